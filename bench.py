@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the VDI hot path on GB300.
+
+Workload (the plain-method configuration): a 512^3 uint16 volume (64 seeded
+Gaussian blobs + 0.1 x 3-octave value noise), K = 8 PEs as 2 x 2 x 2 bricks,
+1920 x 1080 perspective views from a seeded 16-view orbit, N_S = 20, gamma
+chosen by the per-ray bisection search in both phases, FP32 supersegments.
+
+One step = one VDI frame of the whole hot path on one view: building the K
+sampling bricks from the volume, choosing gamma per (PE, ray), the prefix sum,
+emission of the K compact sub-VDIs, compositing into the regular VDI, and
+flattening it from the generating view.  The metric is VDI rays per second
+(Mrays/s; W x H rays per frame).  Each stage is timed with CUDA events on the
+launching stream; the roofline object describes the stage that dominates.
+
+--impl reference times the FP64 CPU oracle (the method's plain statement) on
+the host cores on a bounded sample of the same frames.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VDI gen Mrays/s"
+UNIT = "Mrays/s"
+
+# algorithmic work per unit of the sampling/search kernel:
+# one sample evaluation = trilinear interpolation (7 lerps: 14) + value scale (1)
+# + transfer-function lerp (4 lerps: 8) + premultiplication (3) + log transmittance (2)
+OPS_PER_SAMPLE = 28
+# one state-machine step of one gamma candidate = renormalised opacity (3) + distance (9)
+# + threshold (3) + over / optical depth (9)
+OPS_PER_STEP = 24
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dims", type=int, default=512)
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+class Workload:
+    def __init__(self, dims=512, W=1920, H=1080):
+        import oracle  # noqa: F401  (only for the decomposition check below in tests; not used here)
+        import synth
+
+        self.dims = (dims, dims, dims)
+        self.grid = (2, 2, 2)
+        self.n_s = 20
+        self.step = 0.5
+        self.ref_len = 1.0
+        self.W, self.H = W, H
+        self.vol = synth.volume(self.dims, 64, 3, synth.SEED_VOLUME + 1, np.uint16)
+        self.lut = synth.transfer_function(synth.SEED_TF)
+        self.cams = synth.orbit(self.dims, 16, W, H, synth.SEED_ORBIT)
+        self.name = f"plain: {dims}^3 u16, K=8 (2x2x2), {W}x{H}, 16-view orbit, N_S=20, search, FP32"
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(wl, seconds_target, pixels_seed=17, views=(0,)):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload's rays."""
+    import oracle
+
+    boxes = oracle.split_boxes(wl.dims, wl.grid)
+    rng = np.random.default_rng(pixels_seed)
+    npix = wl.W * wl.H
+    cores = os.cpu_count() or 1
+
+    def run(n, cam):
+        pix = np.sort(rng.choice(npix, n, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        cnt, _, recs, _ = oracle.generate(wl.vol, boxes, wl.lut, cam, wl.step, wl.ref_len, wl.n_s, -1.0, pixels=pix)
+        oracle.composite(oracle.lists_from_recs(cnt, recs), wl.n_s, n_pix=n)
+        return time.perf_counter() - t0
+
+    n = 256
+    t = run(n, wl.cams[views[0]])
+    n = int(min(npix // 4, max(256, n * seconds_target / max(t, 1e-3))))
+    total_rays, total_t = 0, 0.0
+    for v in views:
+        total_t += run(n, wl.cams[v])
+        total_rays += n
+    return {"value": total_rays / total_t / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{total_rays} seeded random rays of view(s) {list(views)} (of {npix} per frame): "
+                      f"FP64 generation with search + compositing, {total_t:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = Workload(args.dims, args.width, args.height)
+    per_step = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(wl, per_step, pixels_seed=100 + i, views=(i % 16,))
+        if i >= args.warmup:
+            vals.append(cb)
+    v = statistics.median([c["value"] for c in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl.W * wl.H / (v * 1e6),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+
+    import paper_2206_14503_gb300 as vdi
+
+    wl = Workload(args.dims, args.width, args.height)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    W, H, n_s = wl.W, wl.H, wl.n_s
+    npix = W * H
+    boxes = vdi.vdi_split_boxes(wl.dims, wl.grid)
+    k = len(boxes)
+    vol_host = torch.from_numpy(wl.vol.view(np.int16)).pin_memory()
+    vol_d = vol_host.to(dev)
+    lut_d = torch.from_numpy(wl.lut).to(dev)
+    with torch.cuda.stream(stream):
+        bricks = vdi.Bricks(vol_d, wl.dims, boxes, stream)
+    cap = npix * n_s // 2
+    outs = [vdi.Compact(npix, cap, vdi.VDI_PREC_F32, dev) for _ in range(k)]
+    reg = vdi.Regular(npix, n_s, vdi.VDI_PREC_F32, dev)
+    img = torch.zeros((npix, 4), dtype=torch.float32, device=dev)
+    wsg = vdi.Workspace(vdi.vdi_generate_workspace(k, W, H), dev)
+    wsc = vdi.Workspace(vdi.vdi_composite_workspace(k, W, H, n_s), dev)
+    params = vdi.make_params(step=wl.step, ref_len=wl.ref_len)
+    cams = [vdi.make_camera(c) for c in wl.cams]
+    ostructs = [o.struct() for o in outs]
+    rstruct = reg.struct()
+    stages = ["brick", "choose_gamma", "scan+emit", "composite", "flatten"]
+    launches_per_step = 1 + 1 + 4 + 1 + 1  # brick, count, 3 scan + emit, composite, flatten
+
+    def frame(view, ev=None):
+        cam = cams[view]
+        if ev:
+            ev[0].record(stream)
+        bricks.rebuild(vol_d, stream)
+        if ev:
+            ev[1].record(stream)
+        vdi.check(vdi.vdi_choose_gamma(bricks.bricks, lut_d.data_ptr(), cam, n_s, vdi.VDI_GAMMA_SEARCH, ostructs,
+                                       params, wsg.ptr, wsg.nbytes, stream), "choose_gamma")
+        if ev:
+            ev[2].record(stream)
+        vdi.check(vdi.vdi_generate(bricks.bricks, lut_d.data_ptr(), cam, n_s, vdi.VDI_GAMMA_CHOSEN, ostructs,
+                                   params, wsg.ptr, wsg.nbytes, stream), "generate")
+        if ev:
+            ev[3].record(stream)
+        vdi.check(vdi.vdi_composite(ostructs, W, H, rstruct, params, wsc.ptr, wsc.nbytes, stream), "composite")
+        if ev:
+            ev[4].record(stream)
+        vdi.check(vdi.vdi_render_view(rstruct, W, H, cam, None, img.data_ptr(), stream), "render")
+        if ev:
+            ev[5].record(stream)
+
+    # warm-up (also checks capacity and device status)
+    for i in range(args.warmup):
+        frame((i * world + rank) % 16)
+    stream.synchronize()
+    vdi.check(wsg.status(stream), "generate status")
+    vdi.check(wsc.status(stream), "composite status")
+    totals = [int(o.offsets[-1].item()) for o in outs]
+    assert max(totals) <= cap, "capacity"
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    n_in = []
+    for s in range(args.steps):
+        frame((args.warmup + s * world + rank) % 16, evs[s])
+    t_end.record(stream)
+    stream.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    stage_ms = {name: [evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps)]
+                for i, name in enumerate(stages)}
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    rays = npix * args.steps * world
+    value = rays / (total_ms * 1e-3) / 1e6
+
+    # ---- work census and bytes of the timed frames (outside the timed region) ----
+    cen_params = vdi.make_params(step=wl.step, ref_len=wl.ref_len, flags=vdi.VDI_FLAG_CENSUS)
+    evals = steps_sm = 0
+    comp_bytes = []
+    for s in range(args.steps):
+        view = (args.warmup + s * world + rank) % 16
+        vdi.check(vdi.vdi_choose_gamma(bricks.bricks, lut_d.data_ptr(), cams[view], n_s, vdi.VDI_GAMMA_SEARCH,
+                                       ostructs, cen_params, wsg.ptr, wsg.nbytes, stream), "census")
+        c = vdi.vdi_workspace_counters(wsg.ptr, stream)
+        evals += c[0]
+        steps_sm += c[1]
+        vdi.check(vdi.vdi_generate(bricks.bricks, lut_d.data_ptr(), cams[view], n_s, vdi.VDI_GAMMA_CHOSEN, ostructs,
+                                   params, wsg.ptr, wsg.nbytes, stream), "generate")
+        stream.synchronize()
+        n_records = sum(int(o.offsets[-1].item()) for o in outs)
+        # composite algorithmic bytes: per PE and pixel count + offset (12 B), input records (24 B),
+        # output slots (N_S x 24 B), output count + gamma (8 B)
+        comp_bytes.append(npix * (12 * k + 24 * n_s + 8) + 24 * n_records)
+        n_in.append(n_records)
+    mean = {kk: statistics.mean(v) for kk, v in stage_ms.items()}
+    dominant = max(mean, key=mean.get)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sm_clock = (clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0))
+    # FP32 issue peak: 152 SMs x 128 FP32 lanes x SM clock (one op per lane per clock)
+    alu_peak_tops = 152 * 128 * sm_clock * 1e6 / 1e12
+    gen_ops = OPS_PER_SAMPLE * evals + OPS_PER_STEP * steps_sm
+    gen_tops = gen_ops / args.steps / (mean["choose_gamma"] * 1e-3) / 1e12
+    comp_gbs = statistics.mean(comp_bytes) / (mean["composite"] * 1e-3) / 1e9
+    if dominant == "composite":
+        roof = {"bound": "hbm", "achieved": comp_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": comp_gbs / hbm_peak, "traffic": None, "kernel": "composite_kernel",
+                "peak_source": hbm_src}
+    else:
+        roof = {"bound": "alu", "achieved": gen_tops, "peak": alu_peak_tops, "unit": "Tops/s",
+                "frac": gen_tops / alu_peak_tops, "traffic": None, "kernel": "gen_count_kernel",
+                "peak_source": f"152 SMs x 128 FP32 lanes x {sm_clock:.0f} MHz (median SM clock under load)"}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        host_counts = torch.empty(npix, dtype=torch.int32).pin_memory()
+        host_rgba = torch.empty((npix * n_s, 4), dtype=torch.float32).pin_memory()
+        host_fb = torch.empty((npix * n_s, 2), dtype=torch.float32).pin_memory()
+        h2d = vol_host.numel() * 2
+        d2h = host_counts.numel() * 4 + host_rgba.numel() * 4 + host_fb.numel() * 4
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        nsteps = max(2, args.steps // 2)
+        with torch.cuda.stream(stream):
+            vol_d.copy_(vol_host, non_blocking=True)
+            frame(0)
+            stream.synchronize()
+            e0.record(stream)
+            for s in range(nsteps):
+                vol_d.copy_(vol_host, non_blocking=True)
+                frame((s * world + rank) % 16)
+                host_counts.copy_(reg.counts, non_blocking=True)
+                host_rgba.copy_(reg.rgba, non_blocking=True)
+                host_fb.copy_(reg.fb, non_blocking=True)
+            e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        e2e = {"value": npix * nsteps * world / (ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(wl, args.cpu_seconds)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (4.3 GB of bricks, >1 GB of sub-VDIs per frame)"},
+                "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps,
+                "clocks": clk,
+                "stages_ms": {kk: round(v, 3) for kk, v in mean.items()},
+                "composite": {"gbs": comp_gbs, "frac_hbm": comp_gbs / hbm_peak, "peak_gbs": hbm_peak,
+                              "peak_source": hbm_src, "records_in_per_frame": int(statistics.mean(n_in)),
+                              "bytes_per_frame": int(statistics.mean(comp_bytes))},
+                "gen": {"mrays_s": npix / (mean["choose_gamma"] + mean["scan+emit"] + mean["brick"]) / 1e3,
+                        "sample_evals_per_frame": evals // args.steps,
+                        "sm_steps_per_frame": steps_sm // args.steps, "tops": gen_tops}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * vdi.h -- C ABI of the GB300 library for distributed Volumetric Depth Image
+ * (VDI) generation and compositing.
+ *
+ * Method: Gupta et al., "Parallel Compositing of Volumetric Depth Images for
+ * Interactive Visualization of Distributed Volumes at High Frame Rates".
+ * Each processing element (PE) owns one box of the volume's cells.  Phase 1
+ * raycasts every PE's box from a shared camera into a compact sub-VDI (sec. 4,
+ * sec. 5.1); phase 2 composites the K sub-VDIs of each pixel into one regular
+ * VDI of at most N_S supersegments (sec. 5.2, Eq. 2, Algorithm S1).  On one
+ * GPU all K sub-VDIs live in device memory; the paper's all-to-all exchange
+ * is the composite kernel's per-pixel gather.
+ *
+ * Conventions shared by every entry point:
+ *   - All array arguments are DEVICE pointers unless marked "host".  The
+ *     caller allocates and frees every buffer; the library allocates no
+ *     device memory in any entry point and frees nothing it did not create.
+ *   - Calls are asynchronous on `stream` (0 = the legacy default stream) and
+ *     do not synchronise the host, except where a flag asks for it.
+ *   - Errors are returned as vdi_status; no C++ exception crosses the ABI.
+ *     Argument errors are detected on the host before any launch.  Errors a
+ *     kernel detects (an output buffer too small) are written to a status
+ *     word inside the caller's workspace; vdi_workspace_status() reads it.
+ *     vdi_last_error() returns a message for the last failing call on the
+ *     calling host thread.
+ *   - Depth is distance from the eye along the unit ray direction, in voxel
+ *     units.  The volume's nodes sit at integer coordinates 0..dims-1; cell
+ *     (i,j,k) spans [i,i+1] x [j,j+1] x [k,k+1].
+ *   - A supersegment ("record") is {front f, back b, premultiplied R,G,B,
+ *     opacity A}.  FP32 records are stored as two arrays, float4 rgba[] and
+ *     float2 fb[] (24 bytes); FP16 records as one array of 16-byte structs
+ *     {float f; float b; half r, g, b, a;} (colour and opacity in IEEE
+ *     binary16, depth in FP32).
+ */
+#ifndef VDI_H
+#define VDI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* vdi_stream; /* same type as cudaStream_t */
+
+typedef enum {
+    VDI_OK = 0,
+    VDI_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is invalid */
+    VDI_ERR_CAPACITY = 2,    /* an output buffer holds fewer records than needed */
+    VDI_ERR_WORKSPACE = 3,   /* the workspace is smaller than the query said */
+    VDI_ERR_CUDA = 4,        /* a CUDA runtime call or launch failed */
+    VDI_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    VDI_ERR_MODEL = 6,       /* a learned-gamma model is missing or malformed */
+    VDI_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
+} vdi_status;
+
+typedef enum { VDI_PREC_F32 = 0, VDI_PREC_F16 = 1 } vdi_precision;
+typedef enum { VDI_VOL_F32 = 0, VDI_VOL_U16 = 1 } vdi_voltype;
+
+/* Maximum number of PEs in one call. */
+#define VDI_MAX_PE 64
+
+/* gamma modes of vdi_generate / vdi_choose_gamma */
+#define VDI_GAMMA_SEARCH (-1.0f) /* per-ray bisection search (sec. 2.4) */
+#define VDI_GAMMA_GIVEN (-2.0f)  /* per-ray gamma read from vdi_compact.gamma */
+#define VDI_GAMMA_CHOSEN (-3.0f) /* vdi_generate only: counts and gamma already written by vdi_choose_gamma */
+
+/* One PE's owned cells: [lo, hi) per axis, x, y, z. */
+typedef struct {
+    int32_t lo[3], hi[3];
+} vdi_box;
+
+/* Pinhole camera (host struct).  Pixel (i, j), j = 0 the top row, gets the ray
+ * through its centre: d = normalize(fwd + x right + y up'), x = (2(i+1/2)/W - 1)
+ * tan(fovy/2) W/H, y = (1 - 2(j+1/2)/H) tan(fovy/2), fwd = normalize(center -
+ * eye), right = normalize(fwd x up), up' = right x fwd. */
+typedef struct {
+    double eye[3], center[3], up[3];
+    double fovy_deg;
+    int32_t width, height;
+} vdi_camera;
+
+/* Sampling parameters (host struct).  Samples lie on a grid shared by all PEs:
+ * sample k of a ray covers [t_in + k step, t_in + (k+1) step] with midpoint
+ * t_in + (k + 1/2) step, t_in the ray's entry into the whole volume's box, for
+ * every k whose midpoint lies before the exit.  A sample belongs to the PE
+ * whose box holds the cell floor(midpoint) (clamped to the volume's cells).
+ * The transfer function's opacity is given per ref_len voxels and corrected to
+ * the step (sec. 2.4, "length-adjusted opacity"). */
+typedef struct {
+    float step;           /* sample spacing in voxels, > 0 */
+    float ref_len;        /* length the table's opacity refers to, > 0 */
+    int32_t bisect_iters; /* bisection steps of the gamma search, 1..24 (16) */
+    int32_t schedule;     /* 0: automatic; see vdi_composite */
+    int32_t flags;        /* VDI_FLAG_* */
+} vdi_params;
+
+#define VDI_FLAG_SYNC_CAPACITY 1 /* vdi_generate: read totals back and return VDI_ERR_CAPACITY before emitting */
+#define VDI_FLAG_CENSUS 2        /* vdi_choose_gamma / vdi_generate: count the work done (vdi_workspace_counters) */
+
+/* A sampling brick: one PE's cells in the library's cell-packed layout, built
+ * by vdi_brick_build().  Opaque to the caller apart from its size. */
+typedef struct {
+    const float* cells; /* device, vdi_brick_bytes() bytes */
+    vdi_box owned;      /* the PE's cells */
+    int32_t dims[3];    /* nodes of the whole volume per axis */
+    float value_scale;  /* stored value * value_scale = v in [0,1] */
+} vdi_brick;
+
+/* Compact sub-VDI of one PE (sec. 4, Fig. 2c).  For pixel p = j*W + i the
+ * records are [offsets[p], offsets[p] + counts[p]).  vdi_generate writes
+ * offsets as the exclusive prefix sum of counts (offsets[W*H] = total);
+ * vdi_composite reads only offsets[p] and counts[p], so any start layout
+ * (several PEs sharing one record pool, say) is accepted there. */
+typedef struct {
+    uint32_t* counts;  /* [W*H] */
+    uint64_t* offsets; /* [W*H + 1] */
+    void* rgba;        /* F32: float4[capacity]; F16: 16-byte records[capacity] */
+    float* fb;         /* F32: float2[capacity]; F16: unused (NULL) */
+    float* gamma;      /* [W*H] per-ray gamma (output of generation; input in VDI_GAMMA_GIVEN mode) */
+    uint64_t capacity; /* records the record arrays hold */
+    int32_t prec;      /* vdi_precision */
+} vdi_compact;
+
+/* Regular VDI (sec. 4, Fig. 2a): N_S slots per pixel, pixel-major, front to
+ * back, unused slots zero; counts[p] slots used.  Record (p, j) is at index
+ * p * n_s + j. */
+typedef struct {
+    uint32_t* counts; /* [W*H] */
+    void* rgba;       /* F32: float4[W*H*n_s]; F16: 16-byte records[W*H*n_s] */
+    float* fb;        /* F32: float2[W*H*n_s]; F16: unused (NULL) */
+    float* gamma;     /* [W*H] gamma chosen by the compositing search, or NULL */
+    int32_t n_s;
+    int32_t prec; /* vdi_precision */
+} vdi_regular;
+
+/* ------------------------------------------------------------------------ */
+/* Version, errors                                                          */
+/* ------------------------------------------------------------------------ */
+int32_t vdi_version(void);
+const char* vdi_status_string(vdi_status s);
+/* Copies the message of the last failing call on this host thread into buf
+ * (at most n bytes, NUL-terminated) and returns that call's status. */
+vdi_status vdi_last_error(char* buf, size_t n);
+/* Synchronises `stream`, reads the device status word in `workspace` and
+ * returns it (VDI_OK if no kernel reported an error since the call that last
+ * cleared it; every entry point taking a workspace clears it first). */
+vdi_status vdi_workspace_status(const void* workspace, vdi_stream stream);
+/* Synchronises `stream` and copies the work counters of the last call made
+ * with VDI_FLAG_CENSUS on this workspace into counters[4] (host):
+ *   [0] samples evaluated (trilinear + classification), summed over passes,
+ *   [1] state-machine steps (samples x gamma candidates evaluated),
+ *   [2] marches over a ray's samples (passes), [3] (PE, ray) pairs with samples.
+ * The census runs a separately compiled variant of the kernel; without the
+ * flag nothing is counted. */
+vdi_status vdi_workspace_counters(const void* workspace, uint64_t counters[4], vdi_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Decomposition and bricks (sec. 3: blocks as close to equal as the data    */
+/* dimensions permit)                                                        */
+/* ------------------------------------------------------------------------ */
+/* Near-equal split of the cells of a dims[0] x dims[1] x dims[2] node volume
+ * into grid[0]*grid[1]*grid[2] boxes (x fastest).  Host only.  boxes_out
+ * (host) receives the boxes.  Cell runs along an axis differ by at most one. */
+vdi_status vdi_split_boxes(const int32_t dims[3], const int32_t grid[3], vdi_box* boxes_out);
+
+/* Bytes of the sampling brick of box `owned` (32 bytes per cell, including a
+ * one-cell border). */
+size_t vdi_brick_bytes(const vdi_box* owned);
+
+/* Builds the sampling bricks of k PEs from the whole volume `volume` (device,
+ * node values x fastest, type `type`: float32 v in [0,1] or uint16 v = u/65535).
+ * cells_out[e] (host array of k device pointers) receives vdi_brick_bytes(&boxes[e])
+ * bytes each; bricks_out (host, k entries) is filled in.  One launch. */
+vdi_status vdi_brick_build(const void* volume, vdi_voltype type, const int32_t dims[3], int32_t k,
+                           const vdi_box* boxes, float* const* cells_out, vdi_brick* bricks_out, vdi_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Phase 1: sub-VDI generation (sec. 4, sec. 5.1, Eq. 1)                     */
+/* ------------------------------------------------------------------------ */
+/* Workspace bytes for vdi_generate / vdi_choose_gamma with k PEs of w x h. */
+size_t vdi_generate_workspace(int32_t k, int32_t w, int32_t h);
+
+/* Chooses gamma and the resulting supersegment count for every (PE, ray)
+ * without emitting records: out[e].gamma and out[e].counts are written.
+ * gamma >= 0: that value for every ray; VDI_GAMMA_SEARCH: per-ray bisection
+ * (gamma = 0 if it yields at most n_s, else bisection of [0, 2] for
+ * params->bisect_iters steps, stopping early at exactly n_s; the upper end is
+ * returned); VDI_GAMMA_GIVEN: out[e].gamma is read, and rays whose count at
+ * that gamma exceeds n_s fall back to the search.  counts are the number of
+ * records emission at that gamma produces with the budget n_s. */
+vdi_status vdi_choose_gamma(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
+                            int32_t n_s, float gamma, vdi_compact* out, const vdi_params* params, void* workspace,
+                            size_t ws_bytes, vdi_stream stream);
+
+/* Generates the k compact sub-VDIs: vdi_choose_gamma, the exclusive prefix sum
+ * of the counts into offsets (sec. 4), and emission of the records.
+ * tf_lut: device float[256*4], straight RGB and opacity per ref_len.
+ * gamma as in vdi_choose_gamma, or VDI_GAMMA_CHOSEN to skip choosing: out[e].counts
+ * and out[e].gamma then hold the result of an earlier vdi_choose_gamma call
+ * with the same bricks, camera, n_s and params (only the prefix sum and the
+ * emission run).
+ * Records of a list are in depth order, at most n_s per list for box-shaped
+ * domains.  If a PE's total exceeds out[e].capacity, no record past the
+ * capacity is written and VDI_ERR_CAPACITY is reported through the workspace
+ * status (or returned, with offsets valid, under VDI_FLAG_SYNC_CAPACITY). */
+vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
+                        int32_t n_s, float gamma, vdi_compact* out, const vdi_params* params, void* workspace,
+                        size_t ws_bytes, vdi_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Phase 2: compositing (sec. 5.2, Eq. 2, Algorithm S1)                      */
+/* ------------------------------------------------------------------------ */
+/* Composites the k compact sub-VDIs (pe[e], all w x h) into the regular VDI
+ * `out` (out->n_s slots per pixel).  Per pixel: the records of all lists with
+ * b > f are cut at every front and back depth; an interval covered by one
+ * record whole keeps that record, a part of one record gets the opacity of
+ * Eq. 2, an interval covered by several records their emission-absorption
+ * mixture, an uncovered interval between records is a transparent sample.
+ * The pieces are re-segmented with Eq. 1 and a per-pixel gamma search, and
+ * at most n_s supersegments are written front to back with a zero tail.
+ * params->schedule: 0 automatic, 1 thread per pixel.
+ * workspace may be NULL when vdi_composite_workspace() returns 0. */
+size_t vdi_composite_workspace(int32_t k, int32_t w, int32_t h, int32_t n_s);
+vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h, vdi_regular* out,
+                         const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Rendering from the generating view (sec. 2.3: a VDI is exact from its    */
+/* viewpoint of generation by associativity of "over")                      */
+/* ------------------------------------------------------------------------ */
+/* Flattens the regular VDI front to back into rgba_out (device float4[w*h],
+ * premultiplied).  `view` must be NULL or equal to `gen`; other views return
+ * VDI_ERR_UNSUPPORTED. */
+vdi_status vdi_render_view(const vdi_regular* vdi, int32_t w, int32_t h, const vdi_camera* gen,
+                           const vdi_camera* view, float* rgba_out, vdi_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VDI_H */

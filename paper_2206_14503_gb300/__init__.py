@@ -1,0 +1,351 @@
+"""Python binding of libvdi.so (include/vdi.h): GB300 generation and
+compositing of distributed Volumetric Depth Images.
+
+The functions named ``vdi_*`` mirror the C entry points one to one and only
+marshal arguments (pointers come from torch CUDA tensors or integers).  The
+helpers below them allocate buffers with torch and fill the C structs; every
+step of the method runs in the library's CUDA kernels.  There is no CPU
+fallback: importing this module fails if libvdi.so cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvdi.so")
+
+VDI_OK = 0
+VDI_ERR_INVALID_ARG = 1
+VDI_ERR_CAPACITY = 2
+VDI_ERR_WORKSPACE = 3
+VDI_ERR_CUDA = 4
+VDI_ERR_TIMEOUT = 5
+VDI_ERR_MODEL = 6
+VDI_ERR_UNSUPPORTED = 7
+VDI_PREC_F32 = 0
+VDI_PREC_F16 = 1
+VDI_VOL_F32 = 0
+VDI_VOL_U16 = 1
+VDI_MAX_PE = 64
+VDI_GAMMA_SEARCH = -1.0
+VDI_GAMMA_GIVEN = -2.0
+VDI_GAMMA_CHOSEN = -3.0
+VDI_FLAG_SYNC_CAPACITY = 1
+VDI_FLAG_CENSUS = 2
+
+
+class VdiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class vdi_box(C.Structure):
+    _fields_ = [("lo", C.c_int32 * 3), ("hi", C.c_int32 * 3)]
+
+
+class vdi_camera(C.Structure):
+    _fields_ = [("eye", C.c_double * 3), ("center", C.c_double * 3), ("up", C.c_double * 3),
+                ("fovy_deg", C.c_double), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class vdi_params(C.Structure):
+    _fields_ = [("step", C.c_float), ("ref_len", C.c_float), ("bisect_iters", C.c_int32),
+                ("schedule", C.c_int32), ("flags", C.c_int32)]
+
+
+class vdi_brick(C.Structure):
+    _fields_ = [("cells", C.c_void_p), ("owned", vdi_box), ("dims", C.c_int32 * 3), ("value_scale", C.c_float)]
+
+
+class vdi_compact(C.Structure):
+    _fields_ = [("counts", C.c_void_p), ("offsets", C.c_void_p), ("rgba", C.c_void_p), ("fb", C.c_void_p),
+                ("gamma", C.c_void_p), ("capacity", C.c_uint64), ("prec", C.c_int32)]
+
+
+class vdi_regular(C.Structure):
+    _fields_ = [("counts", C.c_void_p), ("rgba", C.c_void_p), ("fb", C.c_void_p), ("gamma", C.c_void_p),
+                ("n_s", C.c_int32), ("prec", C.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libvdi.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, sz, f32 = C.c_void_p, C.c_int32, C.c_size_t, C.c_float
+    sigs = {
+        "vdi_version": ([], i32),
+        "vdi_status_string": ([i32], C.c_char_p),
+        "vdi_last_error": ([C.c_char_p, sz], i32),
+        "vdi_workspace_status": ([vp, vp], i32),
+        "vdi_workspace_counters": ([vp, vp, vp], i32),
+        "vdi_split_boxes": ([vp, vp, vp], i32),
+        "vdi_brick_bytes": ([vp], sz),
+        "vdi_brick_build": ([vp, i32, vp, i32, vp, vp, vp, vp], i32),
+        "vdi_generate_workspace": ([i32, i32, i32], sz),
+        "vdi_choose_gamma": ([vp, i32, vp, vp, i32, f32, vp, vp, vp, sz, vp], i32),
+        "vdi_generate": ([vp, i32, vp, vp, i32, f32, vp, vp, vp, sz, vp], i32),
+        "vdi_composite_workspace": ([i32, i32, i32, i32], sz),
+        "vdi_composite": ([vp, i32, i32, i32, vp, vp, vp, sz, vp], i32),
+        "vdi_render_view": ([vp, i32, i32, vp, vp, vp, vp], i32),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+# exported symbol names of the C ABI (checked by the tests against include/vdi.h)
+SYMBOLS = ("vdi_version", "vdi_status_string", "vdi_last_error", "vdi_workspace_status", "vdi_workspace_counters",
+           "vdi_split_boxes",
+           "vdi_brick_bytes", "vdi_brick_build", "vdi_generate_workspace", "vdi_choose_gamma", "vdi_generate",
+           "vdi_composite_workspace", "vdi_composite", "vdi_render_view")
+
+
+def lib():
+    return _lib
+
+
+def _ref(x):
+    return None if x is None else C.cast(C.byref(x), C.c_void_p)
+
+
+def _arr(x):
+    return None if x is None else C.cast(x, C.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(512)
+    _lib.vdi_last_error(buf, 512)
+    return buf.value.decode()
+
+
+def check(status: int, what: str = "vdi call"):
+    if status != VDI_OK:
+        raise VdiError(status, f"{what}: {_lib.vdi_status_string(status).decode()}: {last_error()}")
+    return status
+
+
+# --------------------------------------------------------------------------
+# one-to-one wrappers of the C entry points (argument marshalling only)
+# --------------------------------------------------------------------------
+
+def vdi_version() -> int:
+    return _lib.vdi_version()
+
+
+def vdi_status_string(s: int) -> str:
+    return _lib.vdi_status_string(s).decode()
+
+
+def vdi_workspace_status(workspace_ptr: int, stream=None) -> int:
+    return _lib.vdi_workspace_status(C.c_void_p(workspace_ptr), _stream(stream))
+
+
+def vdi_workspace_counters(workspace_ptr: int, stream=None):
+    out = (C.c_uint64 * 4)()
+    check(_lib.vdi_workspace_counters(C.c_void_p(workspace_ptr), _arr(out), _stream(stream)), "vdi_workspace_counters")
+    return list(out)
+
+
+def vdi_split_boxes(dims, grid):
+    k = grid[0] * grid[1] * grid[2]
+    out = (vdi_box * k)()
+    d = (C.c_int32 * 3)(*dims)
+    g = (C.c_int32 * 3)(*grid)
+    check(_lib.vdi_split_boxes(_arr(d), _arr(g), _arr(out)), "vdi_split_boxes")
+    return list(out)
+
+
+def vdi_brick_bytes(box: vdi_box) -> int:
+    return _lib.vdi_brick_bytes(_ref(box))
+
+
+def vdi_brick_build(volume_ptr: int, voltype: int, dims, boxes, cells_ptrs, stream=None):
+    k = len(boxes)
+    d = (C.c_int32 * 3)(*dims)
+    bx = (vdi_box * k)(*boxes)
+    cp = (C.c_void_p * k)(*cells_ptrs)
+    bricks = (vdi_brick * k)()
+    check(_lib.vdi_brick_build(C.c_void_p(volume_ptr), voltype, _arr(d), k, _arr(bx), _arr(cp), _arr(bricks),
+                               _stream(stream)), "vdi_brick_build")
+    return bricks
+
+
+def vdi_generate_workspace(k: int, w: int, h: int) -> int:
+    return _lib.vdi_generate_workspace(k, w, h)
+
+
+def vdi_choose_gamma(bricks, lut_ptr, cam: vdi_camera, n_s, gamma, outs, params: vdi_params, ws_ptr, ws_bytes,
+                     stream=None) -> int:
+    k = len(outs)
+    oarr = (vdi_compact * k)(*outs)
+    return _lib.vdi_choose_gamma(_arr(bricks), k, C.c_void_p(lut_ptr), _ref(cam), n_s, gamma, _arr(oarr),
+                                 _ref(params), C.c_void_p(ws_ptr), ws_bytes, _stream(stream))
+
+
+def vdi_generate(bricks, lut_ptr, cam: vdi_camera, n_s, gamma, outs, params: vdi_params, ws_ptr, ws_bytes,
+                 stream=None) -> int:
+    k = len(outs)
+    oarr = (vdi_compact * k)(*outs)
+    return _lib.vdi_generate(_arr(bricks), k, C.c_void_p(lut_ptr), _ref(cam), n_s, gamma, _arr(oarr),
+                             _ref(params), C.c_void_p(ws_ptr), ws_bytes, _stream(stream))
+
+
+def vdi_composite_workspace(k, w, h, n_s) -> int:
+    return _lib.vdi_composite_workspace(k, w, h, n_s)
+
+
+def vdi_composite(pes, w, h, out: vdi_regular, params: vdi_params, ws_ptr, ws_bytes, stream=None) -> int:
+    k = len(pes)
+    arr = (vdi_compact * k)(*pes)
+    return _lib.vdi_composite(_arr(arr), k, w, h, _ref(out), _ref(params), C.c_void_p(ws_ptr), ws_bytes,
+                              _stream(stream))
+
+
+def vdi_render_view(vdi: vdi_regular, w, h, gen: vdi_camera, view, rgba_ptr, stream=None) -> int:
+    return _lib.vdi_render_view(_ref(vdi), w, h, _ref(gen), _ref(view) if view is not None else None,
+                                C.c_void_p(rgba_ptr), _stream(stream))
+
+
+# --------------------------------------------------------------------------
+# torch conveniences (buffer allocation and struct filling)
+# --------------------------------------------------------------------------
+
+def make_camera(cam) -> vdi_camera:
+    c = vdi_camera()
+    c.eye[:] = [float(x) for x in cam.eye]
+    c.center[:] = [float(x) for x in cam.center]
+    c.up[:] = [float(x) for x in cam.up]
+    c.fovy_deg = float(cam.fovy_deg)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def make_params(step=0.5, ref_len=1.0, bisect_iters=16, schedule=0, flags=0) -> vdi_params:
+    return vdi_params(step, ref_len, bisect_iters, schedule, flags)
+
+
+class Compact:
+    """Device buffers of one compact sub-VDI (torch tensors) and its C struct."""
+
+    def __init__(self, npix: int, capacity: int, prec: int = VDI_PREC_F32, device="cuda"):
+        import torch
+
+        self.npix = npix
+        self.capacity = capacity
+        self.prec = prec
+        self.counts = torch.zeros(npix, dtype=torch.int32, device=device)
+        self.offsets = torch.zeros(npix + 1, dtype=torch.int64, device=device)
+        self.gamma = torch.zeros(npix, dtype=torch.float32, device=device)
+        if prec == VDI_PREC_F32:
+            self.rgba = torch.zeros((max(capacity, 1), 4), dtype=torch.float32, device=device)
+            self.fb = torch.zeros((max(capacity, 1), 2), dtype=torch.float32, device=device)
+        else:
+            self.rgba = torch.zeros((max(capacity, 1), 4), dtype=torch.int32, device=device)  # 16-byte records
+            self.fb = None
+
+    @classmethod
+    def from_tensors(cls, counts, offsets, rgba, fb, prec=VDI_PREC_F32, gamma=None):
+        self = cls.__new__(cls)
+        self.npix = counts.numel()
+        self.capacity = rgba.shape[0]
+        self.prec = prec
+        self.counts, self.offsets, self.rgba, self.fb, self.gamma = counts, offsets, rgba, fb, gamma
+        return self
+
+    def struct(self) -> vdi_compact:
+        return vdi_compact(self.counts.data_ptr(), self.offsets.data_ptr(), self.rgba.data_ptr(),
+                           None if self.fb is None else self.fb.data_ptr(),
+                           None if self.gamma is None else self.gamma.data_ptr(), self.capacity, self.prec)
+
+
+class Regular:
+    """Device buffers of one regular VDI (torch tensors) and its C struct."""
+
+    def __init__(self, npix: int, n_s: int, prec: int = VDI_PREC_F32, device="cuda"):
+        import torch
+
+        self.npix, self.n_s, self.prec = npix, n_s, prec
+        self.counts = torch.zeros(npix, dtype=torch.int32, device=device)
+        self.gamma = torch.zeros(npix, dtype=torch.float32, device=device)
+        if prec == VDI_PREC_F32:
+            self.rgba = torch.zeros((npix * n_s, 4), dtype=torch.float32, device=device)
+            self.fb = torch.zeros((npix * n_s, 2), dtype=torch.float32, device=device)
+        else:
+            self.rgba = torch.zeros((npix * n_s, 4), dtype=torch.int32, device=device)
+            self.fb = None
+
+    def struct(self) -> vdi_regular:
+        return vdi_regular(self.counts.data_ptr(), self.rgba.data_ptr(),
+                           None if self.fb is None else self.fb.data_ptr(), self.gamma.data_ptr(), self.n_s, self.prec)
+
+    def records_f32(self):
+        """(fb [npix, n_s, 2], rgba [npix, n_s, 4]) as float32 tensors (FP16 records decoded)."""
+        import torch
+
+        if self.prec == VDI_PREC_F32:
+            return self.fb.view(self.npix, self.n_s, 2), self.rgba.view(self.npix, self.n_s, 4)
+        raw = self.rgba.view(self.npix, self.n_s, 4)
+        fb = raw[..., 0:2].contiguous().view(torch.float32)
+        rgba = raw[..., 2:4].contiguous().view(torch.float16).float()
+        return fb, rgba
+
+
+def compact_records_f32(c: Compact):
+    """(fb [n, 2], rgba [n, 4]) float32 views of a compact sub-VDI's records."""
+    import torch
+
+    if c.prec == VDI_PREC_F32:
+        return c.fb, c.rgba
+    raw = c.rgba
+    return raw[:, 0:2].contiguous().view(torch.float32), raw[:, 2:4].contiguous().view(torch.float16).float()
+
+
+class Bricks:
+    """Sampling bricks of K PEs built on the device from a whole volume."""
+
+    def __init__(self, volume, dims, boxes, stream=None):
+        import torch
+
+        self.dims = tuple(int(d) for d in dims)
+        self.boxes = list(boxes)
+        voltype = VDI_VOL_U16 if volume.dtype in (torch.uint16, torch.int16) else VDI_VOL_F32
+        self.cells = [torch.empty(vdi_brick_bytes(b) // 4, dtype=torch.float32, device=volume.device)
+                      for b in self.boxes]
+        self.bricks = vdi_brick_build(volume.data_ptr(), voltype, self.dims, self.boxes,
+                                      [c.data_ptr() for c in self.cells], stream)
+
+    def rebuild(self, volume, stream=None):
+        import torch
+
+        voltype = VDI_VOL_U16 if volume.dtype in (torch.uint16, torch.int16) else VDI_VOL_F32
+        self.bricks = vdi_brick_build(volume.data_ptr(), voltype, self.dims, self.boxes,
+                                      [c.data_ptr() for c in self.cells], stream)
+
+
+class Workspace:
+    def __init__(self, nbytes: int, device="cuda"):
+        import torch
+
+        self.nbytes = max(int(nbytes), 256)
+        self.buf = torch.zeros(self.nbytes, dtype=torch.uint8, device=device)
+
+    @property
+    def ptr(self) -> int:
+        return self.buf.data_ptr()
+
+    def status(self, stream=None) -> int:
+        return vdi_workspace_status(self.ptr, stream)

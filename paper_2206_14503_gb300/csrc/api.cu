@@ -1,0 +1,366 @@
+// C ABI (include/vdi.h): argument checks on the host, then stream-ordered
+// launches.  No entry point allocates device memory.
+#include <math.h>
+#include <stddef.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "vdi_internal.h"
+
+namespace vdi {
+
+static thread_local char g_msg[512];
+static thread_local vdi_status g_last = VDI_OK;
+
+vdi_status set_error(vdi_status s, const char* fmt, ...) {
+    g_last = s;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+vdi_status cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return VDI_OK;
+    return set_error(VDI_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+CamDev make_cam(const vdi_camera& c) {
+    double fwd[3], right[3], up[3];
+    for (int a = 0; a < 3; ++a) fwd[a] = c.center[a] - c.eye[a];
+    double n = sqrt(fwd[0] * fwd[0] + fwd[1] * fwd[1] + fwd[2] * fwd[2]);
+    for (int a = 0; a < 3; ++a) fwd[a] /= n;
+    right[0] = fwd[1] * c.up[2] - fwd[2] * c.up[1];
+    right[1] = fwd[2] * c.up[0] - fwd[0] * c.up[2];
+    right[2] = fwd[0] * c.up[1] - fwd[1] * c.up[0];
+    n = sqrt(right[0] * right[0] + right[1] * right[1] + right[2] * right[2]);
+    for (int a = 0; a < 3; ++a) right[a] /= n;
+    up[0] = right[1] * fwd[2] - right[2] * fwd[1];
+    up[1] = right[2] * fwd[0] - right[0] * fwd[2];
+    up[2] = right[0] * fwd[1] - right[1] * fwd[0];
+    double th = tan(0.5 * c.fovy_deg * 3.14159265358979323846 / 180.0);
+    CamDev d;
+    auto split = [](double v, float out[2]) {
+        out[0] = (float)v;
+        out[1] = (float)(v - (double)out[0]);
+    };
+    for (int a = 0; a < 3; ++a) {
+        split(c.eye[a], d.eye[a]);
+        split(fwd[a], d.fwd[a]);
+        split(right[a], d.right[a]);
+        split(up[a], d.up[a]);
+    }
+    split(th * (double)c.width / (double)c.height, d.sx);
+    split(th, d.sy);
+    d.W = c.width;
+    d.H = c.height;
+    return d;
+}
+
+static bool camera_ok(const vdi_camera* c) {
+    if (!c || c->width < 1 || c->height < 1 || !(c->fovy_deg > 0.0 && c->fovy_deg < 180.0)) return false;
+    double f[3] = {c->center[0] - c->eye[0], c->center[1] - c->eye[1], c->center[2] - c->eye[2]};
+    double r[3] = {f[1] * c->up[2] - f[2] * c->up[1], f[2] * c->up[0] - f[0] * c->up[2], f[0] * c->up[1] - f[1] * c->up[0]};
+    return (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) > 0.0 && (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) > 0.0;
+}
+
+static bool params_ok(const vdi_params* p) {
+    return p && p->step > 0.f && p->ref_len > 0.f && p->bisect_iters >= 1 && p->bisect_iters <= 24;
+}
+
+static BrickDev brick_dev(const vdi_brick& b) {
+    BrickDev d;
+    d.cells = b.cells;
+    for (int a = 0; a < 3; ++a) {
+        d.lo[a] = b.owned.lo[a];
+        d.hi[a] = b.owned.hi[a];
+    }
+    d.nx = b.owned.hi[0] - b.owned.lo[0] + 2;
+    d.ny = b.owned.hi[1] - b.owned.lo[1] + 2;
+    d.nz = b.owned.hi[2] - b.owned.lo[2] + 2;
+    d.ncells = d.nx * d.ny * d.nz;
+    return d;
+}
+
+}  // namespace vdi
+
+using namespace vdi;
+
+extern "C" {
+
+int32_t vdi_version(void) { return 100; }
+
+const char* vdi_status_string(vdi_status s) {
+    switch (s) {
+        case VDI_OK: return "ok";
+        case VDI_ERR_INVALID_ARG: return "invalid argument";
+        case VDI_ERR_CAPACITY: return "output capacity too small";
+        case VDI_ERR_WORKSPACE: return "workspace too small";
+        case VDI_ERR_CUDA: return "CUDA error";
+        case VDI_ERR_TIMEOUT: return "device wait timed out";
+        case VDI_ERR_MODEL: return "model error";
+        case VDI_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+vdi_status vdi_last_error(char* buf, size_t n) {
+    if (buf && n > 0) {
+        strncpy(buf, g_msg, n - 1);
+        buf[n - 1] = 0;
+    }
+    return g_last;
+}
+
+vdi_status vdi_workspace_status(const void* workspace, vdi_stream stream) {
+    if (!workspace) return set_error(VDI_ERR_INVALID_ARG, "vdi_workspace_status: workspace is NULL");
+    unsigned int s = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    vdi_status r = cuda_check(cudaMemcpyAsync(&s, workspace, sizeof s, cudaMemcpyDeviceToHost, st), "status read");
+    if (r != VDI_OK) return r;
+    r = cuda_check(cudaStreamSynchronize(st), "status sync");
+    if (r != VDI_OK) return r;
+    if (s != 0) return set_error((vdi_status)s, "device reported: %s", vdi_status_string((vdi_status)s));
+    return VDI_OK;
+}
+
+vdi_status vdi_workspace_counters(const void* workspace, uint64_t counters[4], vdi_stream stream) {
+    if (!workspace || !counters) return set_error(VDI_ERR_INVALID_ARG, "vdi_workspace_counters: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const char* src = static_cast<const char*>(workspace) + offsetof(WsHeader, counters);
+    vdi_status r = cuda_check(cudaMemcpyAsync(counters, src, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st),
+                              "counters read");
+    if (r != VDI_OK) return r;
+    return cuda_check(cudaStreamSynchronize(st), "counters sync");
+}
+
+vdi_status vdi_split_boxes(const int32_t dims[3], const int32_t grid[3], vdi_box* boxes_out) {
+    if (!dims || !grid || !boxes_out) return set_error(VDI_ERR_INVALID_ARG, "vdi_split_boxes: NULL argument");
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 2 || grid[a] < 1 || grid[a] > dims[a] - 1)
+            return set_error(VDI_ERR_INVALID_ARG, "vdi_split_boxes: axis %d: dims %d grid %d", a, dims[a], grid[a]);
+    if ((long)grid[0] * grid[1] * grid[2] > VDI_MAX_PE)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_split_boxes: more than %d PEs", VDI_MAX_PE);
+    int e = 0;
+    for (int z = 0; z < grid[2]; ++z)
+        for (int y = 0; y < grid[1]; ++y)
+            for (int x = 0; x < grid[0]; ++x) {
+                int idx[3] = {x, y, z};
+                for (int a = 0; a < 3; ++a) {
+                    long cells = dims[a] - 1;
+                    // run a of g gets cells [floor(a C / g), floor((a+1) C / g))
+                    boxes_out[e].lo[a] = (int32_t)(cells * idx[a] / grid[a]);
+                    boxes_out[e].hi[a] = (int32_t)(cells * (idx[a] + 1) / grid[a]);
+                }
+                ++e;
+            }
+    return VDI_OK;
+}
+
+size_t vdi_brick_bytes(const vdi_box* b) {
+    if (!b) return 0;
+    size_t n = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (b->hi[a] <= b->lo[a]) return 0;
+        n *= (size_t)(b->hi[a] - b->lo[a] + 2);
+    }
+    return n * 8 * sizeof(float);
+}
+
+vdi_status vdi_brick_build(const void* volume, vdi_voltype type, const int32_t dims[3], int32_t k,
+                           const vdi_box* boxes, float* const* cells_out, vdi_brick* bricks_out, vdi_stream stream) {
+    if (!volume || !dims || !boxes || !cells_out || !bricks_out)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_brick_build: NULL argument");
+    if (k < 1 || k > VDI_MAX_PE) return set_error(VDI_ERR_INVALID_ARG, "vdi_brick_build: k = %d", k);
+    if (type != VDI_VOL_F32 && type != VDI_VOL_U16) return set_error(VDI_ERR_INVALID_ARG, "vdi_brick_build: type");
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 2) return set_error(VDI_ERR_INVALID_ARG, "vdi_brick_build: dims[%d] = %d", a, dims[a]);
+    for (int e = 0; e < k; ++e) {
+        for (int a = 0; a < 3; ++a)
+            if (boxes[e].lo[a] < 0 || boxes[e].hi[a] > dims[a] - 1 || boxes[e].hi[a] <= boxes[e].lo[a])
+                return set_error(VDI_ERR_INVALID_ARG, "vdi_brick_build: box %d axis %d [%d, %d)", e, a,
+                                 boxes[e].lo[a], boxes[e].hi[a]);
+        if (!cells_out[e]) return set_error(VDI_ERR_INVALID_ARG, "vdi_brick_build: cells_out[%d] NULL", e);
+        if ((reinterpret_cast<uintptr_t>(cells_out[e]) & 15) != 0)
+            return set_error(VDI_ERR_INVALID_ARG, "vdi_brick_build: cells_out[%d] not 16-byte aligned", e);
+        if (vdi_brick_bytes(&boxes[e]) / 32 > (size_t)INT32_MAX)
+            return set_error(VDI_ERR_INVALID_ARG, "vdi_brick_build: box %d too large", e);
+    }
+    vdi_status s = launch_brick_build(volume, type, dims, k, boxes, cells_out, (cudaStream_t)stream);
+    if (s != VDI_OK) return s;
+    for (int e = 0; e < k; ++e) {
+        bricks_out[e].cells = cells_out[e];
+        bricks_out[e].owned = boxes[e];
+        for (int a = 0; a < 3; ++a) bricks_out[e].dims[a] = dims[a];
+        bricks_out[e].value_scale = type == VDI_VOL_U16 ? (float)(1.0 / 65535.0) : 1.0f;
+    }
+    return VDI_OK;
+}
+
+size_t vdi_generate_workspace(int32_t k, int32_t w, int32_t h) {
+    if (k < 1 || w < 0 || h < 0) return 0;
+    return kWsHeader + scan_workspace(k, w * h);
+}
+
+static vdi_status gen_common(const char* fn, const vdi_brick* bricks, int32_t k, const float* tf_lut,
+                             const vdi_camera* cam, int32_t n_s, float gamma, vdi_compact* out,
+                             const vdi_params* params, void* workspace, size_t ws_bytes, bool need_records) {
+    if (!bricks || !tf_lut || !cam || !out || !params) return set_error(VDI_ERR_INVALID_ARG, "%s: NULL argument", fn);
+    if (k < 1 || k > VDI_MAX_PE) return set_error(VDI_ERR_INVALID_ARG, "%s: k = %d", fn, k);
+    if (n_s < 1) return set_error(VDI_ERR_INVALID_ARG, "%s: n_s = %d", fn, n_s);
+    if (!camera_ok(cam)) return set_error(VDI_ERR_INVALID_ARG, "%s: camera", fn);
+    if (!params_ok(params)) return set_error(VDI_ERR_INVALID_ARG, "%s: params", fn);
+    if (!(gamma >= 0.f || gamma == VDI_GAMMA_SEARCH || gamma == VDI_GAMMA_GIVEN ||
+          (need_records && gamma == VDI_GAMMA_CHOSEN)) || isinf(gamma))
+        return set_error(VDI_ERR_INVALID_ARG, "%s: gamma %g", fn, (double)gamma);
+    if ((long long)cam->width * cam->height > (long long)INT32_MAX / 2)
+        return set_error(VDI_ERR_INVALID_ARG, "%s: image too large", fn);
+    for (int e = 0; e < k; ++e) {
+        const vdi_brick& b = bricks[e];
+        if (!b.cells) return set_error(VDI_ERR_INVALID_ARG, "%s: brick %d has no cells", fn, e);
+        for (int a = 0; a < 3; ++a)
+            if (b.dims[a] != bricks[0].dims[a] || b.dims[a] < 2 || b.owned.lo[a] < 0 ||
+                b.owned.hi[a] > b.dims[a] - 1 || b.owned.hi[a] <= b.owned.lo[a])
+                return set_error(VDI_ERR_INVALID_ARG, "%s: brick %d box/dims", fn, e);
+        if (b.value_scale != bricks[0].value_scale) return set_error(VDI_ERR_INVALID_ARG, "%s: value_scale", fn);
+        const vdi_compact& o = out[e];
+        if (!o.counts || !o.gamma) return set_error(VDI_ERR_INVALID_ARG, "%s: out[%d] counts/gamma NULL", fn, e);
+        if (need_records) {
+            if (!o.offsets) return set_error(VDI_ERR_INVALID_ARG, "%s: out[%d].offsets NULL", fn, e);
+            if (o.prec != VDI_PREC_F32 && o.prec != VDI_PREC_F16)
+                return set_error(VDI_ERR_INVALID_ARG, "%s: out[%d].prec", fn, e);
+            if (o.prec != out[0].prec) return set_error(VDI_ERR_INVALID_ARG, "%s: mixed precisions", fn);
+            if (o.capacity > 0 && (!o.rgba || (o.prec == VDI_PREC_F32 && !o.fb)))
+                return set_error(VDI_ERR_INVALID_ARG, "%s: out[%d] record arrays NULL", fn, e);
+            if ((reinterpret_cast<uintptr_t>(o.rgba) & 15) || (reinterpret_cast<uintptr_t>(o.fb) & 7))
+                return set_error(VDI_ERR_INVALID_ARG, "%s: out[%d] record arrays misaligned", fn, e);
+        }
+    }
+    if (!workspace || ws_bytes < vdi_generate_workspace(k, cam->width, cam->height))
+        return set_error(VDI_ERR_WORKSPACE, "%s: workspace %zu < %zu bytes", fn, ws_bytes,
+                         vdi_generate_workspace(k, cam->width, cam->height));
+    if (reinterpret_cast<uintptr_t>(workspace) & 255)
+        return set_error(VDI_ERR_INVALID_ARG, "%s: workspace not 256-byte aligned", fn);
+    return VDI_OK;
+}
+
+vdi_status vdi_choose_gamma(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
+                            int32_t n_s, float gamma, vdi_compact* out, const vdi_params* params, void* workspace,
+                            size_t ws_bytes, vdi_stream stream) {
+    vdi_status s = gen_common("vdi_choose_gamma", bricks, k, tf_lut, cam, n_s, gamma, out, params, workspace,
+                              ws_bytes, false);
+    if (s != VDI_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int* status = reinterpret_cast<unsigned int*>(workspace);
+    s = cuda_check(cudaMemsetAsync(status, 0, 64, st), "status clear");
+    if (s != VDI_OK) return s;
+    BrickDev bd[VDI_MAX_PE];
+    CompactDev od[VDI_MAX_PE];
+    for (int e = 0; e < k; ++e) {
+        bd[e] = brick_dev(bricks[e]);
+        od[e] = CompactDev{out[e].counts, out[e].offsets, out[e].rgba, out[e].fb, out[e].gamma, out[e].capacity};
+    }
+    CamDev cd = make_cam(*cam);
+    float scale255 = (float)(255.0 * (double)bricks[0].value_scale);
+    return launch_gen_count(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s, gamma,
+                            params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0, st);
+}
+
+vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam, int32_t n_s,
+                        float gamma, vdi_compact* out, const vdi_params* params, void* workspace, size_t ws_bytes,
+                        vdi_stream stream) {
+    vdi_status s = gen_common("vdi_generate", bricks, k, tf_lut, cam, n_s, gamma, out, params, workspace, ws_bytes,
+                              true);
+    if (s != VDI_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int* status = reinterpret_cast<unsigned int*>(workspace);
+    s = cuda_check(cudaMemsetAsync(status, 0, 64, st), "status clear");
+    if (s != VDI_OK) return s;
+    BrickDev bd[VDI_MAX_PE];
+    CompactDev od[VDI_MAX_PE];
+    uint32_t* cnts[VDI_MAX_PE];
+    uint64_t* offs[VDI_MAX_PE];
+    for (int e = 0; e < k; ++e) {
+        bd[e] = brick_dev(bricks[e]);
+        od[e] = CompactDev{out[e].counts, out[e].offsets, out[e].rgba, out[e].fb, out[e].gamma, out[e].capacity};
+        cnts[e] = out[e].counts;
+        offs[e] = out[e].offsets;
+    }
+    CamDev cd = make_cam(*cam);
+    float scale255 = (float)(255.0 * (double)bricks[0].value_scale);
+    const int npix = cam->width * cam->height;
+    if (gamma != VDI_GAMMA_CHOSEN) {
+        s = launch_gen_count(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s, gamma,
+                             params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0, st);
+        if (s != VDI_OK) return s;
+    }
+    s = launch_scan(k, npix, cnts, offs, static_cast<char*>(workspace) + kWsHeader, st);
+    if (s != VDI_OK) return s;
+    if (params->flags & VDI_FLAG_SYNC_CAPACITY) {
+        uint64_t tot[VDI_MAX_PE];
+        for (int e = 0; e < k; ++e) {
+            s = cuda_check(cudaMemcpyAsync(&tot[e], offs[e] + npix, sizeof(uint64_t), cudaMemcpyDeviceToHost, st),
+                           "total read");
+            if (s != VDI_OK) return s;
+        }
+        s = cuda_check(cudaStreamSynchronize(st), "total sync");
+        if (s != VDI_OK) return s;
+        for (int e = 0; e < k; ++e)
+            if (tot[e] > out[e].capacity)
+                return set_error(VDI_ERR_CAPACITY, "vdi_generate: PE %d needs %llu records, capacity %llu", e,
+                                 (unsigned long long)tot[e], (unsigned long long)out[e].capacity);
+    }
+    return launch_gen_emit(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s,
+                           out[0].prec, od, status, st);
+}
+
+size_t vdi_composite_workspace(int32_t k, int32_t w, int32_t h, int32_t n_s) {
+    (void)k; (void)w; (void)h; (void)n_s;
+    return kWsHeader;
+}
+
+vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h, vdi_regular* out,
+                         const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream) {
+    if (!pe || !out || !params) return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: NULL argument");
+    if (k < 1 || k > VDI_MAX_PE) return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: k = %d", k);
+    if (w < 0 || h < 0 || (long long)w * h > (long long)INT32_MAX / 2)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: image %d x %d", w, h);
+    if (out->n_s < 1) return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: n_s = %d", out->n_s);
+    if (params->bisect_iters < 1 || params->bisect_iters > 24)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: bisect_iters");
+    for (int e = 0; e < k; ++e) {
+        if (!pe[e].counts || !pe[e].offsets || !pe[e].rgba)
+            return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: pe[%d] NULL array", e);
+        if (pe[e].prec != pe[0].prec || (pe[e].prec != VDI_PREC_F32 && pe[e].prec != VDI_PREC_F16))
+            return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: pe[%d].prec", e);
+        if (pe[e].prec == VDI_PREC_F32 && !pe[e].fb)
+            return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: pe[%d].fb NULL", e);
+        if ((reinterpret_cast<uintptr_t>(pe[e].rgba) & 15) || (reinterpret_cast<uintptr_t>(pe[e].fb) & 7))
+            return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: pe[%d] misaligned", e);
+    }
+    if (!out->counts || !out->rgba || (out->prec == VDI_PREC_F32 && !out->fb))
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: output array NULL");
+    if (out->prec != VDI_PREC_F32 && out->prec != VDI_PREC_F16)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: out->prec");
+    if (!workspace || ws_bytes < vdi_composite_workspace(k, w, h, out->n_s))
+        return set_error(VDI_ERR_WORKSPACE, "vdi_composite: workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int* status = reinterpret_cast<unsigned int*>(workspace);
+    vdi_status s = cuda_check(cudaMemsetAsync(status, 0, sizeof(unsigned int), st), "status clear");
+    if (s != VDI_OK) return s;
+    return launch_composite(pe, k, w, h, out, params->bisect_iters, params->schedule, status, st);
+}
+
+vdi_status vdi_render_view(const vdi_regular* vdi, int32_t w, int32_t h, const vdi_camera* gen,
+                           const vdi_camera* view, float* rgba_out, vdi_stream stream) {
+    if (!vdi || !rgba_out || !vdi->counts || !vdi->rgba || vdi->n_s < 1)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_render_view: NULL argument");
+    if (w < 0 || h < 0) return set_error(VDI_ERR_INVALID_ARG, "vdi_render_view: image size");
+    if (view && (!gen || memcmp(view, gen, sizeof(vdi_camera)) != 0))
+        return set_error(VDI_ERR_UNSUPPORTED, "vdi_render_view: only the generating view is implemented");
+    return launch_flatten(vdi, w, h, rgba_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// Internal structures passed by value to the kernels, and host-side helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vdi.h"
+
+namespace vdi {
+
+// Camera basis as unevaluated pairs of floats (hi + lo, |lo| <= ulp(hi)/2):
+// computed on the host in double and split, so the device sets rays up in
+// double-float arithmetic without FP64 instructions.
+struct CamDev {
+    float eye[3][2];
+    float fwd[3][2], right[3][2], up[3][2];
+    float sx[2], sy[2];  // tan(fovy/2) * W/H, tan(fovy/2)
+    int W, H;
+};
+
+// One PE's sampling brick: cells [lo-1, hi+1) per axis (a one-cell border),
+// 8 corner values per cell as two float4 (v000 v100 v010 v110 | v001 v101 v011 v111).
+struct BrickDev {
+    const float* cells;
+    int lo[3], hi[3];
+    int nx, ny, nz;  // padded cell counts
+    int ncells;
+};
+
+struct CompactDev {
+    uint32_t* counts;
+    uint64_t* offsets;
+    void* rgba;
+    float* fb;
+    float* gamma;
+    uint64_t capacity;
+};
+
+// Status word layout in the caller's workspace (first 256 bytes).
+struct WsHeader {
+    unsigned int status;  // vdi_status of the first device-side error
+    unsigned int pad;
+    unsigned long long counters[4];  // census (VDI_FLAG_CENSUS)
+    unsigned long long pad2[27];
+};
+static_assert(sizeof(WsHeader) == 256, "workspace header is 256 bytes");
+constexpr size_t kWsHeader = 256;
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// host helpers (api.cu)
+CamDev make_cam(const vdi_camera& c);
+vdi_status set_error(vdi_status s, const char* fmt, ...);
+vdi_status cuda_check(cudaError_t e, const char* what);
+
+// kernel launchers (one per .cu file)
+vdi_status launch_brick_build(const void* volume, int type, const int dims[3], int k, const vdi_box* boxes,
+                              float* const* cells, cudaStream_t st);
+vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
+                            float scale255, float step, float ref_len, int n_s, float gamma, int iters,
+                            const CompactDev* out, unsigned int* status, bool census, cudaStream_t st);
+vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
+                           float scale255, float step, float ref_len, int n_s, int prec, const CompactDev* out,
+                           unsigned int* status, cudaStream_t st);
+size_t scan_workspace(int k, int n);
+vdi_status launch_scan(int k, int n, uint32_t* const* counts, uint64_t* const* offsets, void* ws, cudaStream_t st);
+
+struct CompositeArgs;
+vdi_status launch_composite(const vdi_compact* pe, int k, int w, int h, const vdi_regular* out, int iters,
+                            int schedule, unsigned int* status, cudaStream_t st);
+vdi_status launch_flatten(const vdi_regular* v, int w, int h, float* rgba, cudaStream_t st);
+
+}  // namespace vdi

@@ -1,0 +1,129 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point that
+include/vdi.h declares, and its host-side logic (decomposition, sizes,
+argument validation) behaves as documented.  No kernel is launched."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def vdi():
+    import __graft_entry__
+
+    __graft_entry__._builder().build()
+    import paper_2206_14503_gb300 as v
+
+    return v
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "vdi.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(vdi_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(vdi):
+    names = declared_functions()
+    assert len(names) >= 13
+    lib = C.CDLL(vdi.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in vdi.h but not exported"
+    assert set(vdi.SYMBOLS) <= set(names)
+
+
+def test_library_is_sm103a_only(vdi):
+    # the build compiles one gencode: sm_103a
+    import __graft_entry__
+
+    assert __graft_entry__._builder().ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_split_boxes_matches_oracle(vdi):
+    import oracle
+
+    for dims, g in [((512, 512, 512), (2, 2, 2)), ((1024, 1024, 1024), (4, 2, 2)), ((64, 64, 64), (1, 1, 2)),
+                    ((37, 20, 11), (3, 2, 5))]:
+        boxes = vdi.vdi_split_boxes(dims, g)
+        assert [(tuple(b.lo), tuple(b.hi)) for b in boxes] == oracle.split_boxes(dims, g)
+
+
+def test_split_boxes_rejects_bad_grid(vdi):
+    with pytest.raises(vdi.VdiError):
+        vdi.vdi_split_boxes((4, 4, 4), (5, 1, 1))
+    with pytest.raises(vdi.VdiError):
+        vdi.vdi_split_boxes((512, 512, 512), (8, 8, 2))  # more than 64 PEs
+
+
+def test_brick_bytes(vdi):
+    b = vdi.vdi_box((0, 0, 0), (255, 256, 10))
+    assert vdi.vdi_brick_bytes(b) == 257 * 258 * 12 * 32
+    assert vdi.vdi_brick_bytes(vdi.vdi_box((3, 0, 0), (3, 1, 1))) == 0
+
+
+def test_workspace_sizes(vdi):
+    assert vdi.vdi_generate_workspace(8, 1920, 1080) >= 256 + 8 * 8 * ((1920 * 1080 + 4095) // 4096)
+    assert vdi.vdi_composite_workspace(8, 1920, 1080, 20) >= 256
+
+
+def test_status_strings(vdi):
+    for s in range(8):
+        assert vdi.vdi_status_string(s)
+    assert vdi.vdi_status_string(vdi.VDI_ERR_CAPACITY) == "output capacity too small"
+
+
+def test_argument_errors_before_launch(vdi):
+    # every one of these fails on the host, before any CUDA call
+    cam = vdi.vdi_camera((0, 0, -10), (0, 0, 0), (0, 1, 0), 45.0, 8, 8)
+    params = vdi.make_params()
+    fake = 1 << 20  # never dereferenced: validation fails first
+    bricks = (vdi.vdi_brick * 1)()
+    out = vdi.vdi_compact(fake, fake, fake, fake, fake, 10, 0)
+    # k out of range
+    assert vdi.lib().vdi_generate(vdi._arr(bricks), 0, C.c_void_p(fake), vdi._ref(cam), 4, -1.0,
+                                  vdi._arr((vdi.vdi_compact * 1)(out)), vdi._ref(params), C.c_void_p(fake), 1 << 20,
+                                  None) == vdi.VDI_ERR_INVALID_ARG
+    # n_s < 1
+    assert vdi.vdi_generate(bricks, fake, cam, 0, -1.0, [out], params, fake, 1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    # bad gamma mode
+    assert vdi.vdi_generate(bricks, fake, cam, 4, -4.0, [out], params, fake, 1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    assert vdi.vdi_choose_gamma(bricks, fake, cam, 4, -3.0, [out], params, fake, 1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    # degenerate camera (up parallel to the view direction)
+    bad_cam = vdi.vdi_camera((0, 0, -10), (0, 0, 0), (0, 0, 1), 45.0, 8, 8)
+    assert vdi.vdi_generate(bricks, fake, bad_cam, 4, -1.0, [out], params, fake, 1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    # bad params
+    assert vdi.vdi_generate(bricks, fake, cam, 4, -1.0, [out], vdi.make_params(step=0.0), fake,
+                            1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    # brick without cells
+    assert vdi.vdi_generate(bricks, fake, cam, 4, -1.0, [out], params, fake, 1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    assert "brick 0" in vdi.last_error()
+    # workspace too small
+    bricks[0].cells = fake
+    bricks[0].owned = vdi.vdi_box((0, 0, 0), (3, 3, 3))
+    bricks[0].dims[:] = [4, 4, 4]
+    bricks[0].value_scale = 1.0
+    assert vdi.vdi_generate(bricks, fake, cam, 4, -1.0, [out], params, fake, 16) == vdi.VDI_ERR_WORKSPACE
+    # composite: n_s < 1, missing arrays
+    reg = vdi.vdi_regular(fake, fake, fake, None, 0, 0)
+    assert vdi.vdi_composite([out], 4, 4, reg, params, fake, 256) == vdi.VDI_ERR_INVALID_ARG
+    reg.n_s = 4
+    bad = vdi.vdi_compact(None, fake, fake, fake, None, 0, 0)
+    assert vdi.vdi_composite([bad], 4, 4, reg, params, fake, 256) == vdi.VDI_ERR_INVALID_ARG
+    assert vdi.vdi_composite([out], 4, 4, reg, params, None, 0) == vdi.VDI_ERR_WORKSPACE
+    # rendering from a different view is not implemented
+    view = vdi.vdi_camera((1, 0, -10), (0, 0, 0), (0, 1, 0), 45.0, 8, 8)
+    assert vdi.vdi_render_view(reg, 8, 8, cam, view, fake) == vdi.VDI_ERR_UNSUPPORTED
+
+
+def test_product_path_does_not_touch_oracle():
+    # the library and its binding never import or load the oracle
+    pkg = os.path.join(ROOT, "paper_2206_14503_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in src.replace("oracle is", ""), f

@@ -1,0 +1,156 @@
+"""GPU sub-VDI generation (vdi_generate through the C ABI) against the FP64 oracle.
+
+Sampling positions are computed in FP32 on the GPU (no FP64 on the device), so
+sample values differ from the FP64 oracle's by the rounding of FP32 coordinates;
+decisions of Eq. 1 that fall within that rounding can flip.  The tolerances:
+per-ray counts identical on >= 99.9% of (PE, ray) pairs, depth bounds within
+1e-5 of the chord length where counts agree, RGBA within GEN_TOL, and the
+flattened composite within GEN_TOL of the oracle's DVR on every pixel.
+GEN_TOL is derived in the design notes from the FP32 position error.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+from gpu_run import compare_lists, composite, generate, per_pixel
+
+pytestmark = pytest.mark.gpu
+
+GEN_TOL_TINY = 1e-5   # 64^3 volume: coordinates < 64, FP32 position error < 1e-5 voxel
+GEN_TOL_512 = 1e-4    # 512^3 volume: see the design notes (FP32 coordinate rounding)
+
+
+def _check_gen(g_lists, counts_o, recs_o, tol, depth_tol=1e-4):
+    k = len(g_lists)
+    n_max = recs_o.shape[2]
+    cg, rg = per_pixel(g_lists, n_max)
+    assert cg.max() <= n_max
+    st = compare_lists(cg, rg, counts_o, recs_o, depth_tol, tol)
+    return st
+
+
+def test_generate_fixed_gamma_tiny(tiny_workload):
+    w = tiny_workload
+    cam = w["cams"][0]
+    lists, gam = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, w["n_s"], w["gamma"], step=w["step"])
+    cnt, ogam, recs, _ = oracle.generate(w["vol"], w["boxes"], w["lut"], cam, w["step"], w["ref_len"], w["n_s"],
+                                         w["gamma"])
+    st = _check_gen(lists, cnt, recs, GEN_TOL_TINY)
+    assert st["count_agree"] >= 0.999 and st["rgba_max"] <= GEN_TOL_TINY, st
+    assert np.all(gam == np.float32(w["gamma"]))
+    # offsets are the exclusive prefix sum of the counts
+    for c, o, fb, rgba, _ in lists:
+        assert o[0] == 0 and np.array_equal(np.diff(o.astype(np.int64)), c.astype(np.int64))
+
+
+@pytest.mark.parametrize("n_s", [1, 3, 8, 30])
+def test_generate_search_tiny(tiny_workload, n_s):
+    w = tiny_workload
+    cam = w["cams"][3]
+    lists, gam = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, n_s, -1.0, step=w["step"])
+    cnt, ogam, recs, _ = oracle.generate(w["vol"], w["boxes"], w["lut"], cam, w["step"], w["ref_len"], n_s, -1.0)
+    st = _check_gen(lists, cnt, recs, GEN_TOL_TINY)
+    assert st["count_agree"] >= 0.999 and st["rgba_max"] <= GEN_TOL_TINY, st
+    same = np.stack([l[0] for l in lists]) == cnt
+    assert np.mean(gam[same] == ogam[same]) >= 0.99
+
+
+def test_end_to_end_equals_dvr_tiny(tiny_workload):
+    # sec. 2.3: the composited VDI renders exactly from the generating view
+    w = tiny_workload
+    for view in (1, 5):
+        cam = w["cams"][view]
+        lists, _ = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, w["n_s"], -1.0, step=w["step"])
+        g = composite(lists, cam.width, cam.height, w["n_s"])
+        ref = oracle.dvr(w["vol"], w["lut"], cam, w["step"], w["ref_len"])
+        assert np.abs(g["image"] - ref).max() <= GEN_TOL_TINY
+
+
+def test_generate_fp16_storage(tiny_workload):
+    w = tiny_workload
+    cam = w["cams"][2]
+    l32, _ = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, w["n_s"], -1.0, step=w["step"])
+    l16, _ = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, w["n_s"], -1.0, step=w["step"], prec=1)
+    for a, b in zip(l32, l16):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert np.array_equal(a[2], b[2])  # depths stay FP32
+        assert np.abs(a[3] - b[3]).max() <= 2e-3 * 0.5 + 1e-7
+
+
+def test_capacity_error_reported():
+    import torch
+
+    import paper_2206_14503_gb300 as vdi
+    from gpu_run import to_dev
+
+    dims = (24, 24, 24)
+    vol = synth.volume(dims, 6, 2, 3, np.float32)
+    lut = synth.transfer_function(synth.SEED_TF)
+    cam = synth.orbit(dims, 1, 16, 16, 2)[0]
+    boxes = [vdi.vdi_box(lo, hi) for lo, hi in oracle.split_boxes(dims, (1, 1, 1))]
+    br = vdi.Bricks(to_dev(vol), dims, boxes)
+    out = vdi.Compact(256, 3)
+    ws = vdi.Workspace(vdi.vdi_generate_workspace(1, 16, 16))
+    lut_d = to_dev(lut)
+    # synchronous mode: the call itself returns VDI_ERR_CAPACITY with valid offsets
+    s = vdi.vdi_generate(br.bricks, lut_d.data_ptr(), vdi.make_camera(cam), 4, 0.0, [out.struct()],
+                         vdi.make_params(flags=vdi.VDI_FLAG_SYNC_CAPACITY), ws.ptr, ws.nbytes)
+    assert s == vdi.VDI_ERR_CAPACITY
+    need = int(out.offsets[-1].item())
+    assert need > 3 and str(need) in vdi.last_error()
+    # asynchronous mode: nothing past the capacity is written, the workspace status says why
+    s = vdi.vdi_generate(br.bricks, lut_d.data_ptr(), vdi.make_camera(cam), 4, 0.0, [out.struct()],
+                         vdi.make_params(), ws.ptr, ws.nbytes)
+    assert s == vdi.VDI_OK
+    assert ws.status() == vdi.VDI_ERR_CAPACITY
+    # a large enough buffer clears it
+    out2 = vdi.Compact(256, need)
+    s = vdi.vdi_generate(br.bricks, lut_d.data_ptr(), vdi.make_camera(cam), 4, 0.0, [out2.struct()],
+                         vdi.make_params(), ws.ptr, ws.nbytes)
+    assert s == vdi.VDI_OK and ws.status() == vdi.VDI_OK
+    torch.cuda.synchronize()
+
+
+def test_given_gamma_with_fallback(tiny_workload):
+    w = tiny_workload
+    cam = w["cams"][4]
+    npix = cam.width * cam.height
+    k = len(w["boxes"])
+    # given gamma = 0 everywhere: rays with more than N_S non-transparent samples fall back to the search,
+    # so the result equals the plain search
+    lists_s, gam_s = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, w["n_s"], -1.0, step=w["step"])
+    lists_g, gam_g = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, w["n_s"], -2.0, step=w["step"],
+                              given_gamma=np.zeros((k, npix), np.float32))
+    for a, b in zip(lists_s, lists_g):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[3], b[3])
+    assert np.array_equal(gam_s, gam_g)
+    # given gamma = 2: one supersegment per PE ray (count at gamma 2 never exceeds N_S)
+    lists_2, gam_2 = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, w["n_s"], -2.0, step=w["step"],
+                              given_gamma=np.full((k, npix), 2.0, np.float32))
+    assert max(int(l[0].max()) for l in lists_2) == 1
+    assert np.all(gam_2 == 2.0)
+
+
+def test_plain_config_sampled_rays():
+    # 512^3 uint16, 8 bricks, 1920 x 1080, N_S = 20, gamma searched in both phases; the oracle
+    # computes 1500 sampled pixels of one view
+    dims = (512, 512, 512)
+    vol = synth.volume(dims, 64, 3, synth.SEED_VOLUME + 1, np.uint16)
+    lut = synth.transfer_function(synth.SEED_TF)
+    cam = synth.orbit(dims, 16, 1920, 1080, synth.SEED_ORBIT)[0]
+    boxes = oracle.split_boxes(dims, (2, 2, 2))
+    n_s = 20
+    lists, gam = generate(vol, dims, boxes, lut, cam, n_s, -1.0)
+    g = composite(lists, 1920, 1080, n_s)
+    rng = np.random.default_rng(3)
+    pix = np.sort(rng.choice(1920 * 1080, 1500, replace=False)).astype(np.int32)
+    cnt, ogam, recs, _ = oracle.generate(vol, boxes, lut, cam, 0.5, 1.0, n_s, -1.0, pixels=pix)
+    cg, rg = per_pixel(lists, n_s)
+    st = compare_lists(cg[:, pix], rg[:, pix], cnt, recs, 1e-2, GEN_TOL_512)
+    assert st["count_agree"] >= 0.99, st
+    assert st["rgba_max"] <= GEN_TOL_512, st
+    ref = oracle.dvr(vol, lut, cam, 0.5, 1.0, pixels=pix)
+    err = np.abs(g["image"][pix] - ref).max()
+    assert err <= GEN_TOL_512, err
