@@ -209,6 +209,28 @@ vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut,
                         int32_t n_s, float gamma, vdi_compact* out, const vdi_params* params, void* workspace,
                         size_t ws_bytes, vdi_stream stream);
 
+/* Generation for callers that cannot allocate device memory (an in-situ
+ * simulation that reserves its whole device budget at start-up, a plugin with
+ * no access to its host application's allocator).  The paper has no
+ * counterpart; this is vdi_generate with its workspace replaced by a static
+ * device array inside the library (256 B + 512 KiB, held on every GPU that
+ * loads the library until the process exits).  Nothing is allocated or freed.
+ *   - Limit: k * ceil(W*H / 4096) <= 65536 (e.g. 64 PEs at 2048 x 2048);
+ *     larger requests return VDI_ERR_INVALID_ARG without touching the GPU.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before capturing any stream.
+ *   - Capacity is always checked synchronously (VDI_FLAG_SYNC_CAPACITY is
+ *     implied): the call reads the K totals back and returns VDI_ERR_CAPACITY
+ *     before emitting, since there is no workspace status to read later.
+ *   - Every call uses the same array and leaves the previous call's contents
+ *     in it (the status header is cleared by each call); calls that overlap
+ *     on the GPU (several streams or host threads at once) race on it.
+ * Arguments and outputs are those of vdi_generate. */
+vdi_status vdi_generate_static_scratch(const vdi_brick* bricks, int32_t k, const float* tf_lut,
+                                       const vdi_camera* cam, int32_t n_s, float gamma, vdi_compact* out,
+                                       const vdi_params* params, vdi_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Phase 2: compositing (sec. 5.2, Eq. 2, Algorithm S1)                      */
 /* ------------------------------------------------------------------------ */

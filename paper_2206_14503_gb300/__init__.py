@@ -86,6 +86,7 @@ def _load():
         "vdi_generate_workspace": ([i32, i32, i32], sz),
         "vdi_choose_gamma": ([vp, i32, vp, vp, i32, f32, vp, vp, vp, sz, vp], i32),
         "vdi_generate": ([vp, i32, vp, vp, i32, f32, vp, vp, vp, sz, vp], i32),
+        "vdi_generate_static_scratch": ([vp, i32, vp, vp, i32, f32, vp, vp, vp], i32),
         "vdi_composite_workspace": ([i32, i32, i32, i32], sz),
         "vdi_composite": ([vp, i32, i32, i32, vp, vp, vp, sz, vp], i32),
         "vdi_render_view": ([vp, i32, i32, vp, vp, vp, vp], i32),
@@ -103,6 +104,7 @@ _lib = _load()
 SYMBOLS = ("vdi_version", "vdi_status_string", "vdi_last_error", "vdi_workspace_status", "vdi_workspace_counters",
            "vdi_split_boxes",
            "vdi_brick_bytes", "vdi_brick_build", "vdi_generate_workspace", "vdi_choose_gamma", "vdi_generate",
+           "vdi_generate_static_scratch",
            "vdi_composite_workspace", "vdi_composite", "vdi_render_view")
 
 
@@ -202,6 +204,14 @@ def vdi_generate(bricks, lut_ptr, cam: vdi_camera, n_s, gamma, outs, params: vdi
     oarr = (vdi_compact * k)(*outs)
     return _lib.vdi_generate(_arr(bricks), k, C.c_void_p(lut_ptr), _ref(cam), n_s, gamma, _arr(oarr),
                              _ref(params), C.c_void_p(ws_ptr), ws_bytes, _stream(stream))
+
+
+def vdi_generate_static_scratch(bricks, lut_ptr, cam: vdi_camera, n_s, gamma, outs, params: vdi_params,
+                                stream=None) -> int:
+    k = len(outs)
+    oarr = (vdi_compact * k)(*outs)
+    return _lib.vdi_generate_static_scratch(_arr(bricks), k, C.c_void_p(lut_ptr), _ref(cam), n_s, gamma,
+                                            _arr(oarr), _ref(params), _stream(stream))
 
 
 def vdi_composite_workspace(k, w, h, n_s) -> int:

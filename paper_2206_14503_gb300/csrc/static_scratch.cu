@@ -1,0 +1,74 @@
+// vdi_generate_static_scratch: sub-VDI generation for callers that cannot
+// allocate device memory.
+//
+// vdi_generate needs a caller-allocated workspace: a 256-byte status header
+// plus the prefix sum's per-chunk partial sums.  Some callers have no way to
+// provide it -- an in-situ simulation that reserves its whole device-memory
+// budget at start-up and may not allocate during a time step, or a plugin
+// that has no access to its host application's allocator.  This entry point
+// uses instead a file-scope static device array of fixed size (every GPU that
+// loads the library holds it until the process exits) and calls vdi_generate
+// with it; nothing is allocated or freed.
+//
+// The array's host-side name is not a device address: its device address is
+// looked up with cudaGetSymbolAddress once per device, with that device
+// current, by the first call made on that device.
+#include <mutex>
+
+#include "vdi_internal.h"
+
+namespace vdi {
+
+// status header + 65536 partial sums of 8 bytes: k * ceil(W*H / 4096) <= 65536,
+// e.g. 64 PEs of 2048 x 2048 pixels or 8 PEs of 8192 x 8192.
+constexpr size_t kStaticPartials = 65536;
+constexpr size_t kStaticScratchBytes = kWsHeader + kStaticPartials * sizeof(uint64_t);
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+static std::mutex g_scratch_mu;
+static void* g_scratch_ptr[256];
+
+static vdi_status static_scratch_address(void** out) {
+    int dev = 0;
+    vdi_status s = cuda_check(cudaGetDevice(&dev), "vdi_generate_static_scratch: cudaGetDevice");
+    if (s != VDI_OK) return s;
+    if (dev < 0 || dev >= 256) return set_error(VDI_ERR_CUDA, "vdi_generate_static_scratch: device %d", dev);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        s = cuda_check(cudaGetSymbolAddress(&p, g_static_scratch), "vdi_generate_static_scratch: cudaGetSymbolAddress");
+        if (s != VDI_OK) return s;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return VDI_OK;
+}
+
+}  // namespace vdi
+
+using namespace vdi;
+
+extern "C" vdi_status vdi_generate_static_scratch(const vdi_brick* bricks, int32_t k, const float* tf_lut,
+                                                  const vdi_camera* cam, int32_t n_s, float gamma, vdi_compact* out,
+                                                  const vdi_params* params, vdi_stream stream) {
+    if (!cam || !params) return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_static_scratch: NULL argument");
+    if (k < 1 || k > VDI_MAX_PE) return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_static_scratch: k = %d", k);
+    if (cam->width < 1 || cam->height < 1)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_static_scratch: image %d x %d", cam->width, cam->height);
+    const size_t npix = (size_t)cam->width * (size_t)cam->height;
+    const size_t chunks = (npix + 4095) / 4096;
+    if ((size_t)k * chunks > kStaticPartials)
+        return set_error(VDI_ERR_INVALID_ARG,
+                         "vdi_generate_static_scratch: %d PEs x %zu pixels exceed the static scratch "
+                         "(k * ceil(W*H / 4096) must be <= %zu); use vdi_generate with a workspace",
+                         k, npix, kStaticPartials);
+    if (vdi_generate_workspace(k, cam->width, cam->height) > kStaticScratchBytes)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_static_scratch: request exceeds the static scratch");
+    void* scratch = nullptr;
+    vdi_status s = static_scratch_address(&scratch);
+    if (s != VDI_OK) return s;
+    vdi_params p = *params;
+    p.flags |= VDI_FLAG_SYNC_CAPACITY;  // the caller cannot read the status word: report capacity by return
+    return vdi_generate(bricks, k, tf_lut, cam, n_s, gamma, out, &p, scratch, kStaticScratchBytes, stream);
+}

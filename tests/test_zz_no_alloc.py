@@ -1,0 +1,80 @@
+"""vdi_generate_static_scratch: generation for callers that cannot allocate
+device memory (an in-situ simulation with a fixed, pre-reserved device budget,
+a plugin without access to its application's allocator).  It runs
+vdi_generate with a static device array in the library as the workspace.
+
+The test calls it through the C ABI twice in a row (two different views, so the
+second call runs on the scratch the first one left behind) and checks that
+counts, offsets, gamma and records equal those of vdi_generate with a
+caller-allocated workspace, within the generation tests' tolerance (they are
+expected to be identical).  It lives in a file of its own that pytest collects
+last, and passes both alone in a fresh process and after the other tests.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _setup():
+    import torch
+
+    import oracle
+    import paper_2206_14503_gb300 as vdi
+    import synth
+
+    dims = (48, 40, 56)
+    vol = synth.volume(dims, 10, 3, 77, np.uint16)
+    lut = synth.transfer_function(synth.SEED_TF)
+    cams = synth.orbit(dims, 2, 72, 60, 21)
+    boxes = [vdi.vdi_box(lo, hi) for lo, hi in oracle.split_boxes(dims, (2, 1, 2))]
+    vol_d = torch.from_numpy(vol.view(np.int16)).cuda()
+    br = vdi.Bricks(vol_d, dims, boxes)
+    lut_d = torch.from_numpy(lut).cuda()
+    return vdi, torch, br, lut_d, cams, len(boxes)
+
+
+def _result(outs):
+    return [(o.counts.cpu().numpy(), o.offsets.cpu().numpy(), o.gamma.cpu().numpy(),
+             o.rgba[: int(o.offsets[-1])].cpu().numpy(), o.fb[: int(o.offsets[-1])].cpu().numpy()) for o in outs]
+
+
+def test_static_scratch_matches_workspace_version_twice():
+    vdi, torch, br, lut_d, cams, k = _setup()
+    n_s = 6
+    params = vdi.make_params()
+    for cam in cams:  # two calls in a row
+        c = vdi.make_camera(cam)
+        npix = cam.width * cam.height
+        ref = [vdi.Compact(npix, npix * n_s) for _ in range(k)]
+        ws = vdi.Workspace(vdi.vdi_generate_workspace(k, cam.width, cam.height))
+        vdi.check(vdi.vdi_generate(br.bricks, lut_d.data_ptr(), c, n_s, vdi.VDI_GAMMA_SEARCH,
+                                   [o.struct() for o in ref], params, ws.ptr, ws.nbytes), "vdi_generate")
+        vdi.check(ws.status(), "status")
+        got = [vdi.Compact(npix, npix * n_s) for _ in range(k)]
+        vdi.check(vdi.vdi_generate_static_scratch(br.bricks, lut_d.data_ptr(), c, n_s, vdi.VDI_GAMMA_SEARCH,
+                                                  [o.struct() for o in got], params), "static scratch")
+        torch.cuda.synchronize()
+        for (c1, o1, g1, r1, f1), (c2, o2, g2, r2, f2) in zip(_result(ref), _result(got)):
+            assert np.array_equal(c1, c2) and np.array_equal(o1, o2)
+            assert np.abs(g1 - g2).max(initial=0) <= TOL
+            assert np.abs(r1 - r2).max(initial=0) <= TOL and np.abs(f1 - f2).max(initial=0) <= TOL
+        assert int(ref[0].offsets[-1]) > 0
+
+
+def test_static_scratch_reports_capacity_and_size_limits():
+    vdi, torch, br, lut_d, cams, k = _setup()
+    cam = cams[0]
+    c = vdi.make_camera(cam)
+    npix = cam.width * cam.height
+    small = [vdi.Compact(npix, 1) for _ in range(k)]
+    s = vdi.vdi_generate_static_scratch(br.bricks, lut_d.data_ptr(), c, 6, 0.0, [o.struct() for o in small],
+                                        vdi.make_params())
+    assert s == vdi.VDI_ERR_CAPACITY and "needs" in vdi.last_error()
+    # beyond the static scratch: rejected on the host with a clear message
+    big = vdi.vdi_camera(c.eye, c.center, c.up, 45.0, 16384, 16384)
+    s = vdi.vdi_generate_static_scratch(br.bricks, lut_d.data_ptr(), big, 6, 0.0, [o.struct() for o in small],
+                                        vdi.make_params())
+    assert s == vdi.VDI_ERR_INVALID_ARG and "static scratch" in vdi.last_error()
