@@ -47,7 +47,7 @@ OPS_PER_STEP = 24
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dims", type=int, default=512)
@@ -284,7 +284,7 @@ def main():
 
     # ---- work census and bytes of the timed frames (outside the timed region) ----
     cen_params = vdi.make_params(step=wl.step, ref_len=wl.ref_len, flags=vdi.VDI_FLAG_CENSUS)
-    evals = steps_sm = 0
+    evals = steps_sm = passes = pe_rays = 0
     comp_bytes = []
     for s in range(args.steps):
         view = (args.warmup + s * world + rank) % 16
@@ -293,6 +293,8 @@ def main():
         c = vdi.vdi_workspace_counters(wsg.ptr, stream)
         evals += c[0]
         steps_sm += c[1]
+        passes += c[2]
+        pe_rays += c[3]
         vdi.check(vdi.vdi_generate(bricks.bricks, lut_d.data_ptr(), cams[view], n_s, vdi.VDI_GAMMA_CHOSEN, ostructs,
                                    params, wsg.ptr, wsg.nbytes, stream), "generate")
         stream.synchronize()
@@ -375,7 +377,9 @@ def main():
                               "bytes_per_frame": int(statistics.mean(comp_bytes))},
                 "gen": {"mrays_s": npix / (mean["choose_gamma"] + mean["scan+emit"] + mean["brick"]) / 1e3,
                         "sample_evals_per_frame": evals // args.steps,
-                        "sm_steps_per_frame": steps_sm // args.steps, "tops": gen_tops}}
+                        "sm_steps_per_frame": steps_sm // args.steps, "tops": gen_tops,
+                        "marches_per_pe_ray": passes / max(pe_rays, 1),
+                        "pe_rays_per_frame": pe_rays // args.steps}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
