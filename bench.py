@@ -284,7 +284,7 @@ def main():
 
     # ---- work census and bytes of the timed frames (outside the timed region) ----
     cen_params = vdi.make_params(step=wl.step, ref_len=wl.ref_len, flags=vdi.VDI_FLAG_CENSUS)
-    evals = steps_sm = passes = pe_rays = 0
+    evals = steps_sm = passes = pe_rays = searched = overflow = cached = remarched = 0
     comp_bytes = []
     for s in range(args.steps):
         view = (args.warmup + s * world + rank) % 16
@@ -295,6 +295,10 @@ def main():
         steps_sm += c[1]
         passes += c[2]
         pe_rays += c[3]
+        searched += c[4]
+        overflow += c[5]
+        cached += c[6]
+        remarched += c[7]
         vdi.check(vdi.vdi_generate(bricks.bricks, lut_d.data_ptr(), cams[view], n_s, vdi.VDI_GAMMA_CHOSEN, ostructs,
                                    params, wsg.ptr, wsg.nbytes, stream), "generate")
         stream.synchronize()
@@ -379,7 +383,11 @@ def main():
                         "sample_evals_per_frame": evals // args.steps,
                         "sm_steps_per_frame": steps_sm // args.steps, "tops": gen_tops,
                         "marches_per_pe_ray": passes / max(pe_rays, 1),
-                        "pe_rays_per_frame": pe_rays // args.steps}}
+                        "pe_rays_per_frame": pe_rays // args.steps,
+                        "searched_frac": searched / max(pe_rays, 1),
+                        "cache_overflow_frac": overflow / max(searched, 1),
+                        "cached_marches_per_frame": cached // args.steps,
+                        "volume_search_marches_per_frame": remarched // args.steps}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -148,13 +148,16 @@ vdi_status vdi_last_error(char* buf, size_t n);
  * cleared it; every entry point taking a workspace clears it first). */
 vdi_status vdi_workspace_status(const void* workspace, vdi_stream stream);
 /* Synchronises `stream` and copies the work counters of the last call made
- * with VDI_FLAG_CENSUS on this workspace into counters[4] (host):
- *   [0] samples evaluated (trilinear + classification), summed over passes,
+ * with VDI_FLAG_CENSUS on this workspace into counters[8] (host):
+ *   [0] samples evaluated (trilinear + classification), summed over marches,
  *   [1] state-machine steps (samples x gamma candidates evaluated),
- *   [2] marches over a ray's samples (passes), [3] (PE, ray) pairs with samples.
+ *   [2] marches over a ray's samples, [3] (PE, ray) pairs with samples,
+ *   [4] pairs that needed the bisection search, [5] of those, pairs whose
+ *   non-transparent samples did not fit the sample cache, [6] marches over
+ *   cached samples, [7] marches re-sampling the volume for the search.
  * The census runs a separately compiled variant of the kernel; without the
  * flag nothing is counted. */
-vdi_status vdi_workspace_counters(const void* workspace, uint64_t counters[4], vdi_stream stream);
+vdi_status vdi_workspace_counters(const void* workspace, uint64_t counters[8], vdi_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Decomposition and bricks (sec. 3: blocks as close to equal as the data    */
@@ -179,7 +182,13 @@ vdi_status vdi_brick_build(const void* volume, vdi_voltype type, const int32_t d
 /* ------------------------------------------------------------------------ */
 /* Phase 1: sub-VDI generation (sec. 4, sec. 5.1, Eq. 1)                     */
 /* ------------------------------------------------------------------------ */
-/* Workspace bytes for vdi_generate / vdi_choose_gamma with k PEs of w x h. */
+/* Workspace bytes for vdi_generate / vdi_choose_gamma with k PEs of w x h on
+ * the current device: a status header, a work counter, the prefix sum's
+ * partial sums (8 bytes per 4096 pixels per PE) and a sample cache (about
+ * 400 MB on a 152-SM GB300) that lets the gamma search run over each ray's
+ * cached non-transparent samples instead of re-sampling the volume.  Any
+ * workspace of at least 512 + 8 k ceil(w h / 4096) bytes is accepted; without
+ * room for the cache the search re-marches the volume (same result, slower). */
 size_t vdi_generate_workspace(int32_t k, int32_t w, int32_t h);
 
 /* Chooses gamma and the resulting supersegment count for every (PE, ray)
@@ -213,8 +222,10 @@ vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut,
  * simulation that reserves its whole device budget at start-up, a plugin with
  * no access to its host application's allocator).  The paper has no
  * counterpart; this is vdi_generate with its workspace replaced by a static
- * device array inside the library (256 B + 512 KiB, held on every GPU that
+ * device array inside the library (512 B + 512 KiB, held on every GPU that
  * loads the library until the process exits).  Nothing is allocated or freed.
+ * The array has no room for the sample cache, so the gamma search re-marches
+ * the volume (same result as vdi_generate, slower).
  *   - Limit: k * ceil(W*H / 4096) <= 65536 (e.g. 64 PEs at 2048 x 2048);
  *     larger requests return VDI_ERR_INVALID_ARG without touching the GPU.
  *   - The first call on a device looks up the array's device address
@@ -242,11 +253,48 @@ vdi_status vdi_generate_static_scratch(const vdi_brick* bricks, int32_t k, const
  * mixture, an uncovered interval between records is a transparent sample.
  * The pieces are re-segmented with Eq. 1 and a per-pixel gamma search, and
  * at most n_s supersegments are written front to back with a zero tail.
- * params->schedule: 0 automatic, 1 thread per pixel.
- * workspace may be NULL when vdi_composite_workspace() returns 0. */
+ * params->schedule: 0 automatic (1 if k <= 8, else 2); 1: list heads in
+ * registers (k <= 8), two bisection levels per march over the pieces; 2:
+ * list heads in local memory (k <= 64), two levels per march; 3: heads in
+ * local memory, three levels per march.  All give the same result. */
 size_t vdi_composite_workspace(int32_t k, int32_t w, int32_t h, int32_t n_s);
 vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h, vdi_regular* out,
                          const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched compositing: many requests (image sizes, K, N_S) in one           */
+/* persistent launch.  No counterpart in the paper (which composites one VDI */
+/* per MPI rank); the per-pixel work is that of vdi_composite.              */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const vdi_compact* pe; /* host array of k sub-VDI descriptors (device pointers inside) */
+    int32_t k, w, h;
+    vdi_regular out;   /* the request's output (device pointers inside) */
+    int32_t schedule;  /* as params->schedule of vdi_composite; 0 automatic */
+} vdi_request;
+
+/* Bytes of the request table of n requests (host query). */
+size_t vdi_batch_table_bytes(const vdi_request* reqs, int32_t n);
+/* Packs the requests into host_table (host, vdi_batch_table_bytes bytes).  The
+ * caller copies it to device memory (dev_table) before the launch; both are
+ * passed to vdi_composite_batched.  All requests must share one input
+ * precision. */
+vdi_status vdi_batch_table_pack(const vdi_request* reqs, int32_t n, void* host_table, size_t bytes);
+size_t vdi_composite_batched_workspace(int32_t n);
+/* Composites every request of the table in one persistent kernel: CTAs take
+ * (request, 128-pixel tile) items from an atomic counter in the workspace
+ * (reset by this call with a stream-ordered memset) until none is left.  The
+ * memset and the launch may be captured into a CUDA graph and replayed; the
+ * outputs equal those of one vdi_composite call per request, bit for bit. */
+vdi_status vdi_composite_batched(const void* dev_table, const void* host_table, const vdi_params* params,
+                                 void* workspace, size_t ws_bytes, vdi_stream stream);
+/* Autotuner: for each request whose schedule is 0, times the applicable
+ * schedules on (a prefix of) that request with CUDA events and stores the
+ * fastest in reqs[i].schedule.  Results are cached per (K bucket, N_S bucket)
+ * for the life of the process, so later requests of the same shape reuse
+ * them.  Synchronises the stream; overwrites the requests' outputs. */
+vdi_status vdi_composite_autotune(vdi_request* reqs, int32_t n, const vdi_params* params, void* workspace,
+                                  size_t ws_bytes, vdi_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Rendering from the generating view (sec. 2.3: a VDI is exact from its    */

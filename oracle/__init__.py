@@ -97,6 +97,16 @@ def _load():
         lib.oc_ray_sample_count.restype = i
         lib.oc_split_boxes.argtypes = [vp, vp, vp]
         lib.oc_split_boxes.restype = None
+        lib.oc_tile_features.argtypes = [vp, vp, i, vp, vp, d, d, i, vp, vp]
+        lib.oc_tile_features.restype = i
+        lib.oc_tile_labels.argtypes = [vp, vp, i, i, i, vp, vp]
+        lib.oc_tile_labels.restype = None
+        lib.oc_mlp_nparams.argtypes = []
+        lib.oc_mlp_nparams.restype = i
+        lib.oc_mlp_forward.argtypes = [vp, vp, i, vp]
+        lib.oc_mlp_forward.restype = None
+        lib.oc_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i, vp]
+        lib.oc_mlp_loss_grad.restype = d
         _lib = lib
     return _lib
 
@@ -153,7 +163,8 @@ def _boxes(boxes):
 
 
 def generate(vol: np.ndarray, boxes, lut: np.ndarray, cam, step: float, ref_len: float, n_s: int,
-             gamma: float, iters: int = 16, pixels=None, maxrec: int | None = None, owner_map=None):
+             gamma: float, iters: int = 16, pixels=None, maxrec: int | None = None, owner_map=None,
+             records: bool = True):
     """Phase-1 sub-VDIs.  gamma >= 0: fixed; gamma < 0: per-ray search.
 
     Returns (counts[k, np], gammas[k, np], recs[k, np, maxrec, 6], passes[k, np]).
@@ -169,7 +180,7 @@ def generate(vol: np.ndarray, boxes, lut: np.ndarray, cam, step: float, ref_len:
     counts = np.zeros((k, np_), dtype=np.int32)
     gammas = np.zeros((k, np_), dtype=np.float64)
     passes = np.zeros((k, np_), dtype=np.int32)
-    recs = np.zeros((k, np_, maxrec, REC), dtype=np.float64)
+    recs = np.zeros((k, np_, maxrec, REC), dtype=np.float64) if records else None
     bx = _boxes(boxes)
     om = None if owner_map is None else np.ascontiguousarray(owner_map, dtype=np.int32)
     lut = np.ascontiguousarray(lut, dtype=np.float32)
@@ -340,3 +351,57 @@ def ray_sample_count(vol, cam, step, pixel):
     t = np.zeros(2)
     n = _load().oc_ray_sample_count(_ref(V.c), _ref(c), step, pixel, _p(t))
     return n, float(t[0]), float(t[1])
+
+
+# ----------------------------------------------------------------------------
+# learned gamma (extension): tile features, labels, MLP
+# ----------------------------------------------------------------------------
+NF, NH, TILE = 40, 64, 16
+
+
+def tile_features(vol, boxes, lut, cam, step, ref_len, n_s):
+    """Features [k, tiles, 40] and valid [k, tiles] of every (PE, 16 x 16 tile)."""
+    V = Volume(vol)
+    k = len(boxes)
+    tiles = ((cam.width + TILE - 1) // TILE) * ((cam.height + TILE - 1) // TILE)
+    feats = np.zeros((k, tiles, NF))
+    valid = np.zeros((k, tiles), dtype=np.int32)
+    bx = _boxes(boxes)
+    c = camera(cam)
+    _load().oc_tile_features(_ref(V.c), C.cast(bx, C.c_void_p), k, _p(np.ascontiguousarray(lut, dtype=np.float32)),
+                             _ref(c), step, ref_len, n_s, _p(feats), _p(valid))
+    return feats, valid
+
+
+def tile_labels(gammas, nts, W, H):
+    """Per-tile median of log2(max(gamma, 2^-20)) over rays with nt > 0; gammas/nts [k, W*H]."""
+    gammas = np.ascontiguousarray(gammas, dtype=np.float64)
+    nts = np.ascontiguousarray(nts, dtype=np.int32)
+    k = gammas.shape[0]
+    tiles = ((W + TILE - 1) // TILE) * ((H + TILE - 1) // TILE)
+    labels = np.zeros((k, tiles))
+    valid = np.zeros((k, tiles), dtype=np.int32)
+    _load().oc_tile_labels(_p(gammas), _p(nts), k, W, H, _p(labels), _p(valid))
+    return labels, valid
+
+
+def mlp_nparams():
+    return _load().oc_mlp_nparams()
+
+
+def mlp_forward(theta, x):
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, NF)
+    y = np.zeros(len(x))
+    _load().oc_mlp_forward(_p(theta), _p(x), len(x), _p(y))
+    return y
+
+
+def mlp_loss_grad(theta, x, labels, valid=None):
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, NF)
+    labels = np.ascontiguousarray(labels, dtype=np.float64)
+    valid = np.ones(len(x), dtype=np.int32) if valid is None else np.ascontiguousarray(valid, dtype=np.int32)
+    g = np.zeros(mlp_nparams())
+    loss = _load().oc_mlp_loss_grad(_p(theta), _p(x), _p(labels), _p(valid), len(x), _p(g))
+    return loss, g

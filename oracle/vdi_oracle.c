@@ -666,3 +666,214 @@ void oc_split_boxes(const int* dims, const int* g, oc_box* boxes) {
                 ++e;
             }
 }
+
+/* ====================================================================== */
+/* Learned gamma (an extension of the method; the paper searches gamma per */
+/* ray, sec. 2.4).  Per (PE, 16 x 16 pixel tile) features feed a small     */
+/* MLP that predicts log2 gamma for the tile; the search remains the       */
+/* fallback and the judge.                                                 */
+/* ====================================================================== */
+#define OC_NF 40
+#define OC_NH 64
+#define OC_TILE 16
+
+/* Features of one (PE, tile) from its rays' owned samples, in order:
+ *  [0..31]  histogram of the opacity a' of non-transparent samples, bins of
+ *           width 1/64 (bin 31 holds a' >= 31/64), normalised to sum 1;
+ *  [32],[33] mean and standard deviation over rays with a non-transparent
+ *           sample of the depth of the first one, (k_first - k0) step / diag;
+ *  [34],[35] the same for the back of the last one, (k_last + 1 - k0) step / diag;
+ *  [36]     log1p(mean non-transparent samples per ray with owned samples) / 8;
+ *  [37]     n_s / 64;
+ *  [38]     fraction of rays with owned samples that have a non-transparent one;
+ *  [39]     mean |P_k - P_prev| over consecutive non-transparent samples.
+ * diag is the volume box's diagonal.  A tile whose rays own no sample has all
+ * features 0 and valid = 0.  Per-ray search results (gamma_ray, nt_ray, from
+ * oc_generate with gamma < 0) give the label: the median over rays with
+ * nt > 0 of log2(max(gamma, 2^-20)), the lower middle element for an even
+ * number of rays.                                                         */
+int oc_tile_features(const oc_volume* v, const oc_box* boxes, int k, const float* lut, const oc_camera* cam,
+                     double step, double ref_len, int n_s, double* feats, int* valid) {
+    double lutc[256 * 4];
+    oc_lut_correct(lut, step, ref_len, lutc);
+    const int W = cam->width, H = cam->height;
+    const int tx = (W + OC_TILE - 1) / OC_TILE, ty = (H + OC_TILE - 1) / OC_TILE, nt_tiles = tx * ty;
+    int max_s = 0;
+    for (int a = 0; a < 3; ++a) max_s += v->dims[a];
+    max_s = (int)(2.0 * max_s / step) + 16;
+    double diag = 0.0;
+    for (int a = 0; a < 3; ++a) diag += (double)(v->dims[a] - 1) * (v->dims[a] - 1);
+    diag = sqrt(diag);
+#pragma omp parallel
+    {
+        oc_sample* s = malloc(sizeof(oc_sample) * (size_t)max_s);
+#pragma omp for schedule(dynamic, 1)
+        for (int t = 0; t < nt_tiles; ++t) {
+            for (int e = 0; e < k; ++e) {
+                double hist[32] = {0}, sf = 0, sf2 = 0, sl = 0, sl2 = 0, var = 0;
+                long ntot = 0, pairs = 0, rays_own = 0, rays_nt = 0;
+                for (int jj = 0; jj < OC_TILE; ++jj)
+                    for (int ii = 0; ii < OC_TILE; ++ii) {
+                        int i = (t % tx) * OC_TILE + ii, j = (t / tx) * OC_TILE + jj;
+                        if (i >= W || j >= H) continue;
+                        double o[3], d[3];
+                        oc_ray(cam, i, j, o, d);
+                        int ns = ray_samples(v, boxes, k, NULL, lutc, step, o, d, s, max_s);
+                        int k0 = -1, kf = -1, kl = -1, nt = 0;
+                        double prev[3] = {0, 0, 0};
+                        for (int q = 0; q < ns; ++q) {
+                            if (s[q].owner != e) continue;
+                            if (k0 < 0) k0 = q;
+                            if (s[q].a > 0.0) {
+                                int bin = (int)floor(s[q].a * 64.0);
+                                if (bin > 31) bin = 31;
+                                hist[bin] += 1.0;
+                                if (nt > 0) {
+                                    double dd = 0;
+                                    for (int c = 0; c < 3; ++c) dd += (s[q].P[c] - prev[c]) * (s[q].P[c] - prev[c]);
+                                    var += sqrt(dd);
+                                    ++pairs;
+                                }
+                                for (int c = 0; c < 3; ++c) prev[c] = s[q].P[c];
+                                if (kf < 0) kf = q;
+                                kl = q;
+                                ++nt;
+                            }
+                        }
+                        if (k0 < 0) continue;
+                        ++rays_own;
+                        ntot += nt;
+                        if (nt > 0) {
+                            ++rays_nt;
+                            double f = (kf - k0) * step / diag, l = (kl + 1 - k0) * step / diag;
+                            sf += f; sf2 += f * f; sl += l; sl2 += l * l;
+                        }
+                    }
+                double* F = feats + ((size_t)e * nt_tiles + t) * OC_NF;
+                for (int c = 0; c < OC_NF; ++c) F[c] = 0.0;
+                valid[(size_t)e * nt_tiles + t] = rays_own > 0;
+                if (rays_own == 0) continue;
+                if (ntot > 0)
+                    for (int c = 0; c < 32; ++c) F[c] = hist[c] / (double)ntot;
+                if (rays_nt > 0) {
+                    double mf = sf / rays_nt, ml = sl / rays_nt;
+                    F[32] = mf;
+                    F[33] = sqrt(fmax(sf2 / rays_nt - mf * mf, 0.0));
+                    F[34] = ml;
+                    F[35] = sqrt(fmax(sl2 / rays_nt - ml * ml, 0.0));
+                }
+                F[36] = log1p((double)ntot / (double)rays_own) / 8.0;
+                F[37] = n_s / 64.0;
+                F[38] = (double)rays_nt / (double)rays_own;
+                F[39] = pairs > 0 ? var / (double)pairs : 0.0;
+            }
+        }
+        free(s);
+    }
+    return 0;
+}
+
+static int cmp_dbl(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* Tile labels from per-ray search results: gammas[e][p], nts[e][p] (the
+ * count at gamma = 0, i.e. non-transparent samples).  labels[e][t], valid[e][t]. */
+void oc_tile_labels(const double* gammas, const int* nts, int k, int W, int H, double* labels, int* valid) {
+    const int tx = (W + OC_TILE - 1) / OC_TILE, ty = (H + OC_TILE - 1) / OC_TILE;
+    double buf[OC_TILE * OC_TILE];
+    for (int e = 0; e < k; ++e)
+        for (int t = 0; t < tx * ty; ++t) {
+            int n = 0;
+            for (int jj = 0; jj < OC_TILE; ++jj)
+                for (int ii = 0; ii < OC_TILE; ++ii) {
+                    int i = (t % tx) * OC_TILE + ii, j = (t / tx) * OC_TILE + jj;
+                    if (i >= W || j >= H) continue;
+                    size_t p = (size_t)e * W * H + (size_t)j * W + i;
+                    if (nts[p] <= 0) continue;
+                    double g = gammas[p] > 0x1p-20 ? gammas[p] : 0x1p-20;
+                    buf[n++] = log2(g);
+                }
+            size_t o = (size_t)e * tx * ty + t;
+            valid[o] = n > 0;
+            if (n == 0) { labels[o] = 0.0; continue; }
+            qsort(buf, n, sizeof(double), cmp_dbl);
+            labels[o] = buf[(n - 1) / 2];
+        }
+}
+
+/* MLP 40 -> 64 -> 64 -> 1 with ReLU; parameters in one array:
+ * W1[64][40], b1[64], W2[64][64], b2[64], w3[64], b3 (6849 values).
+ * y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 = predicted log2 gamma.      */
+#define OC_NPARAM (OC_NH * OC_NF + OC_NH + OC_NH * OC_NH + OC_NH + OC_NH + 1)
+
+int oc_mlp_nparams(void) { return OC_NPARAM; }
+
+static void mlp_fwd1(const double* th, const double* x, double* h1, double* h2, double* y) {
+    const double *W1 = th, *b1 = W1 + OC_NH * OC_NF, *W2 = b1 + OC_NH, *b2 = W2 + OC_NH * OC_NH, *w3 = b2 + OC_NH,
+                 *b3 = w3 + OC_NH;
+    for (int o = 0; o < OC_NH; ++o) {
+        double a = b1[o];
+        for (int i = 0; i < OC_NF; ++i) a += W1[o * OC_NF + i] * x[i];
+        h1[o] = a > 0 ? a : 0;
+    }
+    for (int o = 0; o < OC_NH; ++o) {
+        double a = b2[o];
+        for (int i = 0; i < OC_NH; ++i) a += W2[o * OC_NH + i] * h1[i];
+        h2[o] = a > 0 ? a : 0;
+    }
+    double a = b3[0];
+    for (int i = 0; i < OC_NH; ++i) a += w3[i] * h2[i];
+    *y = a;
+}
+
+void oc_mlp_forward(const double* th, const double* x, int n, double* y) {
+    for (int s = 0; s < n; ++s) {
+        double h1[OC_NH], h2[OC_NH];
+        mlp_fwd1(th, x + (size_t)s * OC_NF, h1, h2, y + s);
+    }
+}
+
+/* Mean squared error over the rows with valid != 0 and its gradient with
+ * respect to every parameter (backpropagation through the two ReLU layers;
+ * ReLU'(0) = 0).  Returns the loss; grad has OC_NPARAM entries. */
+double oc_mlp_loss_grad(const double* th, const double* x, const double* label, const int* valid, int n, double* grad) {
+    const double *W2 = th + OC_NH * OC_NF + OC_NH, *w3 = W2 + OC_NH * OC_NH + OC_NH;
+    double *gW1 = grad, *gb1 = gW1 + OC_NH * OC_NF, *gW2 = gb1 + OC_NH, *gb2 = gW2 + OC_NH * OC_NH, *gw3 = gb2 + OC_NH,
+           *gb3 = gw3 + OC_NH;
+    for (int i = 0; i < OC_NPARAM; ++i) grad[i] = 0.0;
+    int m = 0;
+    for (int s = 0; s < n; ++s) m += valid[s] != 0;
+    if (m == 0) return 0.0;
+    double loss = 0.0;
+    for (int s = 0; s < n; ++s) {
+        if (!valid[s]) continue;
+        const double* xs = x + (size_t)s * OC_NF;
+        double h1[OC_NH], h2[OC_NH], y;
+        mlp_fwd1(th, xs, h1, h2, &y);
+        double r = y - label[s];
+        loss += r * r / m;
+        double dy = 2.0 * r / m;
+        gb3[0] += dy;
+        double dh2[OC_NH], dh1[OC_NH];
+        for (int i = 0; i < OC_NH; ++i) {
+            gw3[i] += dy * h2[i];
+            dh2[i] = h2[i] > 0 ? dy * w3[i] : 0.0;
+        }
+        for (int i = 0; i < OC_NH; ++i) dh1[i] = 0.0;
+        for (int o = 0; o < OC_NH; ++o) {
+            gb2[o] += dh2[o];
+            for (int i = 0; i < OC_NH; ++i) {
+                gW2[o * OC_NH + i] += dh2[o] * h1[i];
+                dh1[i] += W2[o * OC_NH + i] * dh2[o];
+            }
+        }
+        for (int o = 0; o < OC_NH; ++o) {
+            double g = h1[o] > 0 ? dh1[o] : 0.0;
+            gb1[o] += g;
+            for (int i = 0; i < OC_NF; ++i) gW1[o * OC_NF + i] += g * xs[i];
+        }
+    }
+    return loss;
+}

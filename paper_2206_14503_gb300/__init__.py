@@ -69,6 +69,11 @@ class vdi_regular(C.Structure):
                 ("n_s", C.c_int32), ("prec", C.c_int32)]
 
 
+class vdi_request(C.Structure):
+    _fields_ = [("pe", C.c_void_p), ("k", C.c_int32), ("w", C.c_int32), ("h", C.c_int32), ("out", vdi_regular),
+                ("schedule", C.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libvdi.so not built ({LIB_PATH}); run __graft_entry__.build()")
@@ -90,6 +95,11 @@ def _load():
         "vdi_composite_workspace": ([i32, i32, i32, i32], sz),
         "vdi_composite": ([vp, i32, i32, i32, vp, vp, vp, sz, vp], i32),
         "vdi_render_view": ([vp, i32, i32, vp, vp, vp, vp], i32),
+        "vdi_batch_table_bytes": ([vp, i32], sz),
+        "vdi_batch_table_pack": ([vp, i32, vp, sz], i32),
+        "vdi_composite_batched_workspace": ([i32], sz),
+        "vdi_composite_batched": ([vp, vp, vp, vp, sz, vp], i32),
+        "vdi_composite_autotune": ([vp, i32, vp, vp, sz, vp], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -105,7 +115,8 @@ SYMBOLS = ("vdi_version", "vdi_status_string", "vdi_last_error", "vdi_workspace_
            "vdi_split_boxes",
            "vdi_brick_bytes", "vdi_brick_build", "vdi_generate_workspace", "vdi_choose_gamma", "vdi_generate",
            "vdi_generate_static_scratch",
-           "vdi_composite_workspace", "vdi_composite", "vdi_render_view")
+           "vdi_composite_workspace", "vdi_composite", "vdi_render_view", "vdi_batch_table_bytes",
+           "vdi_batch_table_pack", "vdi_composite_batched_workspace", "vdi_composite_batched", "vdi_composite_autotune")
 
 
 def lib():
@@ -157,7 +168,7 @@ def vdi_workspace_status(workspace_ptr: int, stream=None) -> int:
 
 
 def vdi_workspace_counters(workspace_ptr: int, stream=None):
-    out = (C.c_uint64 * 4)()
+    out = (C.c_uint64 * 8)()
     check(_lib.vdi_workspace_counters(C.c_void_p(workspace_ptr), _arr(out), _stream(stream)), "vdi_workspace_counters")
     return list(out)
 
@@ -223,6 +234,52 @@ def vdi_composite(pes, w, h, out: vdi_regular, params: vdi_params, ws_ptr, ws_by
     arr = (vdi_compact * k)(*pes)
     return _lib.vdi_composite(_arr(arr), k, w, h, _ref(out), _ref(params), C.c_void_p(ws_ptr), ws_bytes,
                               _stream(stream))
+
+
+class Requests:
+    """A ctypes array of vdi_request plus the sub-VDI descriptor arrays it points to."""
+
+    def __init__(self, items):
+        """items: list of (list of vdi_compact, w, h, vdi_regular, schedule)."""
+        self._pe_arrays = []
+        self.arr = (vdi_request * len(items))()
+        for i, (pes, w, h, out, sched) in enumerate(items):
+            pa = (vdi_compact * len(pes))(*pes)
+            self._pe_arrays.append(pa)
+            self.arr[i].pe = C.cast(pa, C.c_void_p)
+            self.arr[i].k = len(pes)
+            self.arr[i].w, self.arr[i].h = w, h
+            self.arr[i].out = out
+            self.arr[i].schedule = sched
+
+    def __len__(self):
+        return len(self.arr)
+
+
+def vdi_batch_table_bytes(reqs: Requests) -> int:
+    return _lib.vdi_batch_table_bytes(_arr(reqs.arr), len(reqs))
+
+
+def vdi_batch_table_pack(reqs: Requests):
+    """Returns the packed table as a bytes-like ctypes buffer (host)."""
+    n = vdi_batch_table_bytes(reqs)
+    buf = (C.c_uint8 * n)()
+    check(_lib.vdi_batch_table_pack(_arr(reqs.arr), len(reqs), _arr(buf), n), "vdi_batch_table_pack")
+    return buf
+
+
+def vdi_composite_batched_workspace(n: int) -> int:
+    return _lib.vdi_composite_batched_workspace(n)
+
+
+def vdi_composite_batched(dev_table_ptr: int, host_table, params: vdi_params, ws_ptr, ws_bytes, stream=None) -> int:
+    return _lib.vdi_composite_batched(C.c_void_p(dev_table_ptr), _arr(host_table), _ref(params), C.c_void_p(ws_ptr),
+                                      ws_bytes, _stream(stream))
+
+
+def vdi_composite_autotune(reqs: Requests, params: vdi_params, ws_ptr, ws_bytes, stream=None) -> int:
+    return _lib.vdi_composite_autotune(_arr(reqs.arr), len(reqs), _ref(params), C.c_void_p(ws_ptr), ws_bytes,
+                                       _stream(stream))
 
 
 def vdi_render_view(vdi: vdi_regular, w, h, gen: vdi_camera, view, rgba_ptr, stream=None) -> int:

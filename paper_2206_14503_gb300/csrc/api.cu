@@ -1,6 +1,8 @@
 // C ABI (include/vdi.h): argument checks on the host, then stream-ordered
 // launches.  No entry point allocates device memory.
 #include <math.h>
+#include <map>
+#include <mutex>
 #include <stddef.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -126,11 +128,11 @@ vdi_status vdi_workspace_status(const void* workspace, vdi_stream stream) {
     return VDI_OK;
 }
 
-vdi_status vdi_workspace_counters(const void* workspace, uint64_t counters[4], vdi_stream stream) {
+vdi_status vdi_workspace_counters(const void* workspace, uint64_t counters[8], vdi_stream stream) {
     if (!workspace || !counters) return set_error(VDI_ERR_INVALID_ARG, "vdi_workspace_counters: NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     const char* src = static_cast<const char*>(workspace) + offsetof(WsHeader, counters);
-    vdi_status r = cuda_check(cudaMemcpyAsync(counters, src, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st),
+    vdi_status r = cuda_check(cudaMemcpyAsync(counters, src, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st),
                               "counters read");
     if (r != VDI_OK) return r;
     return cuda_check(cudaStreamSynchronize(st), "counters sync");
@@ -199,9 +201,14 @@ vdi_status vdi_brick_build(const void* volume, vdi_voltype type, const int32_t d
     return VDI_OK;
 }
 
+static size_t gen_min_workspace(int k, int w, int h) { return kGenFixed + scan_workspace(k, w * h); }
+
 size_t vdi_generate_workspace(int32_t k, int32_t w, int32_t h) {
     if (k < 1 || w < 0 || h < 0) return 0;
-    return kWsHeader + scan_workspace(k, w * h);
+    int ctas = 0;
+    size_t cache = 0;
+    if (gen_count_grid(ctas) == VDI_OK) cache = gen_cache_bytes(ctas);
+    return gen_min_workspace(k, w, h) + align_up(cache, 256);
 }
 
 static vdi_status gen_common(const char* fn, const vdi_brick* bricks, int32_t k, const float* tf_lut,
@@ -238,9 +245,9 @@ static vdi_status gen_common(const char* fn, const vdi_brick* bricks, int32_t k,
                 return set_error(VDI_ERR_INVALID_ARG, "%s: out[%d] record arrays misaligned", fn, e);
         }
     }
-    if (!workspace || ws_bytes < vdi_generate_workspace(k, cam->width, cam->height))
+    if (!workspace || ws_bytes < gen_min_workspace(k, cam->width, cam->height))
         return set_error(VDI_ERR_WORKSPACE, "%s: workspace %zu < %zu bytes", fn, ws_bytes,
-                         vdi_generate_workspace(k, cam->width, cam->height));
+                         gen_min_workspace(k, cam->width, cam->height));
     if (reinterpret_cast<uintptr_t>(workspace) & 255)
         return set_error(VDI_ERR_INVALID_ARG, "%s: workspace not 256-byte aligned", fn);
     return VDI_OK;
@@ -254,7 +261,7 @@ vdi_status vdi_choose_gamma(const vdi_brick* bricks, int32_t k, const float* tf_
     if (s != VDI_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned int* status = reinterpret_cast<unsigned int*>(workspace);
-    s = cuda_check(cudaMemsetAsync(status, 0, 64, st), "status clear");
+    s = cuda_check(cudaMemsetAsync(status, 0, kGenFixed, st), "status clear");
     if (s != VDI_OK) return s;
     BrickDev bd[VDI_MAX_PE];
     CompactDev od[VDI_MAX_PE];
@@ -264,8 +271,11 @@ vdi_status vdi_choose_gamma(const vdi_brick* bricks, int32_t k, const float* tf_
     }
     CamDev cd = make_cam(*cam);
     float scale255 = (float)(255.0 * (double)bricks[0].value_scale);
+    const size_t fixed = gen_min_workspace(k, cam->width, cam->height);
+    char* ws = static_cast<char*>(workspace);
     return launch_gen_count(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s, gamma,
-                            params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0, st);
+                            params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0,
+                            reinterpret_cast<unsigned int*>(ws + kWsHeader), ws + fixed, ws_bytes - fixed, st);
 }
 
 vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam, int32_t n_s,
@@ -276,7 +286,7 @@ vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut,
     if (s != VDI_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned int* status = reinterpret_cast<unsigned int*>(workspace);
-    s = cuda_check(cudaMemsetAsync(status, 0, 64, st), "status clear");
+    s = cuda_check(cudaMemsetAsync(status, 0, kGenFixed, st), "status clear");
     if (s != VDI_OK) return s;
     BrickDev bd[VDI_MAX_PE];
     CompactDev od[VDI_MAX_PE];
@@ -291,12 +301,15 @@ vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut,
     CamDev cd = make_cam(*cam);
     float scale255 = (float)(255.0 * (double)bricks[0].value_scale);
     const int npix = cam->width * cam->height;
+    const size_t fixed = gen_min_workspace(k, cam->width, cam->height);
+    char* ws = static_cast<char*>(workspace);
     if (gamma != VDI_GAMMA_CHOSEN) {
         s = launch_gen_count(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s, gamma,
-                             params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0, st);
+                             params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0,
+                             reinterpret_cast<unsigned int*>(ws + kWsHeader), ws + fixed, ws_bytes - fixed, st);
         if (s != VDI_OK) return s;
     }
-    s = launch_scan(k, npix, cnts, offs, static_cast<char*>(workspace) + kWsHeader, st);
+    s = launch_scan(k, npix, cnts, offs, ws + kGenFixed, st);
     if (s != VDI_OK) return s;
     if (params->flags & VDI_FLAG_SYNC_CAPACITY) {
         uint64_t tot[VDI_MAX_PE];
@@ -330,6 +343,8 @@ vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h,
     if (out->n_s < 1) return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: n_s = %d", out->n_s);
     if (params->bisect_iters < 1 || params->bisect_iters > 24)
         return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: bisect_iters");
+    if (params->schedule < 0 || params->schedule > 3)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: schedule %d", params->schedule);
     for (int e = 0; e < k; ++e) {
         if (!pe[e].counts || !pe[e].offsets || !pe[e].rgba)
             return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: pe[%d] NULL array", e);
@@ -351,6 +366,125 @@ vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h,
     vdi_status s = cuda_check(cudaMemsetAsync(status, 0, sizeof(unsigned int), st), "status clear");
     if (s != VDI_OK) return s;
     return launch_composite(pe, k, w, h, out, params->bisect_iters, params->schedule, status, st);
+}
+
+size_t vdi_batch_table_bytes(const vdi_request* reqs, int32_t n) {
+    if (!reqs || n < 0) return 0;
+    return batch_table_bytes(reqs, n);
+}
+
+static vdi_status check_request(const vdi_request& q, int idx, int prec0) {
+    if (!q.pe || q.k < 1 || q.k > VDI_MAX_PE) return set_error(VDI_ERR_INVALID_ARG, "request %d: k = %d", idx, q.k);
+    if (q.w < 0 || q.h < 0 || (long long)q.w * q.h > (long long)INT32_MAX / 2)
+        return set_error(VDI_ERR_INVALID_ARG, "request %d: image %d x %d", idx, q.w, q.h);
+    if (q.out.n_s < 1 || !q.out.counts || !q.out.rgba || (q.out.prec == VDI_PREC_F32 && !q.out.fb))
+        return set_error(VDI_ERR_INVALID_ARG, "request %d: output", idx);
+    if (q.schedule < 0 || q.schedule > 3) return set_error(VDI_ERR_INVALID_ARG, "request %d: schedule", idx);
+    for (int e = 0; e < q.k; ++e) {
+        const vdi_compact& c = q.pe[e];
+        if (!c.counts || !c.offsets || !c.rgba || (c.prec == VDI_PREC_F32 && !c.fb))
+            return set_error(VDI_ERR_INVALID_ARG, "request %d: pe[%d] NULL array", idx, e);
+        if (c.prec != prec0) return set_error(VDI_ERR_INVALID_ARG, "request %d: mixed input precisions", idx);
+        if ((reinterpret_cast<uintptr_t>(c.rgba) & 15) || (reinterpret_cast<uintptr_t>(c.fb) & 7))
+            return set_error(VDI_ERR_INVALID_ARG, "request %d: pe[%d] misaligned", idx, e);
+    }
+    return VDI_OK;
+}
+
+vdi_status vdi_batch_table_pack(const vdi_request* reqs, int32_t n, void* host_table, size_t bytes) {
+    if (!reqs || n < 1 || !host_table) return set_error(VDI_ERR_INVALID_ARG, "vdi_batch_table_pack: arguments");
+    const int prec0 = reqs[0].pe ? reqs[0].pe[0].prec : 0;
+    for (int r = 0; r < n; ++r) {
+        vdi_status s = check_request(reqs[r], r, prec0);
+        if (s != VDI_OK) return s;
+    }
+    return batch_table_pack(reqs, n, host_table, bytes);
+}
+
+size_t vdi_composite_batched_workspace(int32_t n) {
+    (void)n;
+    return kWsHeader + 256;
+}
+
+vdi_status vdi_composite_batched(const void* dev_table, const void* host_table, const vdi_params* params,
+                                 void* workspace, size_t ws_bytes, vdi_stream stream) {
+    if (!dev_table || !host_table || !params)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_composite_batched: NULL argument");
+    if (params->bisect_iters < 1 || params->bisect_iters > 24)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_composite_batched: bisect_iters");
+    if (!workspace || ws_bytes < vdi_composite_batched_workspace(0))
+        return set_error(VDI_ERR_WORKSPACE, "vdi_composite_batched: workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int* status = reinterpret_cast<unsigned int*>(workspace);
+    unsigned int* counter = reinterpret_cast<unsigned int*>(static_cast<char*>(workspace) + kWsHeader);
+    vdi_status s = cuda_check(cudaMemsetAsync(workspace, 0, kWsHeader + 256, st), "batched: clear");
+    if (s != VDI_OK) return s;
+    int dev = 0, sms = 0;
+    s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s != VDI_OK) return s;
+    s = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    if (s != VDI_OK) return s;
+    return launch_composite_batched(dev_table, host_table, params->bisect_iters, counter, status, sms, st);
+}
+
+static std::mutex g_tune_mu;
+static std::map<long long, int> g_tune_cache;
+
+static long long tune_key(const vdi_request& q) {
+    int kb = q.k <= 8 ? 8 : (q.k <= 16 ? 16 : (q.k <= 32 ? 32 : 64));
+    int nb = q.out.n_s <= 16 ? 16 : (q.out.n_s <= 32 ? 32 : (q.out.n_s <= 64 ? 64 : 128));
+    return ((long long)kb << 32) | ((long long)nb << 8) | (long long)q.pe[0].prec;
+}
+
+vdi_status vdi_composite_autotune(vdi_request* reqs, int32_t n, const vdi_params* params, void* workspace,
+                                  size_t ws_bytes, vdi_stream stream) {
+    if (!reqs || n < 1 || !params) return set_error(VDI_ERR_INVALID_ARG, "vdi_composite_autotune: arguments");
+    if (!workspace || ws_bytes < kWsHeader) return set_error(VDI_ERR_WORKSPACE, "vdi_composite_autotune: workspace");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int* status = reinterpret_cast<unsigned int*>(workspace);
+    cudaEvent_t e0, e1;
+    vdi_status s = cuda_check(cudaEventCreate(&e0), "event");
+    if (s != VDI_OK) return s;
+    s = cuda_check(cudaEventCreate(&e1), "event");
+    if (s != VDI_OK) { cudaEventDestroy(e0); return s; }
+    for (int r = 0; r < n && s == VDI_OK; ++r) {
+        vdi_request& q = reqs[r];
+        s = check_request(q, r, q.pe ? q.pe[0].prec : 0);
+        if (s != VDI_OK) break;
+        if (q.schedule != 0) continue;
+        const long long key = tune_key(q);
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) { q.schedule = it->second; continue; }
+        }
+        // time each applicable schedule on up to 65536 pixels of this request
+        const long long npix = (long long)q.w * q.h;
+        const int sub = (int)(npix < 65536 ? npix : 65536);
+        int best = default_schedule(q.k);
+        float best_ms = 3.0e38f;
+        for (int sched = 1; sched <= 3 && s == VDI_OK; ++sched) {
+            if (sched == 1 && q.k > 8) continue;
+            float ms_min = 3.0e38f;
+            for (int rep = 0; rep < 3 && s == VDI_OK; ++rep) {
+                s = cuda_check(cudaEventRecord(e0, st), "event record");
+                if (s == VDI_OK) s = launch_composite(q.pe, q.k, sub, 1, &q.out, params->bisect_iters, sched, status, st);
+                if (s == VDI_OK) s = cuda_check(cudaEventRecord(e1, st), "event record");
+                if (s == VDI_OK) s = cuda_check(cudaEventSynchronize(e1), "event sync");
+                float ms = 0.f;
+                if (s == VDI_OK) s = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+                if (ms < ms_min) ms_min = ms;
+            }
+            if (ms_min < best_ms) { best_ms = ms_min; best = sched; }
+        }
+        if (s != VDI_OK) break;
+        q.schedule = best;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
 }
 
 vdi_status vdi_render_view(const vdi_regular* vdi, int32_t w, int32_t h, const vdi_camera* gen,

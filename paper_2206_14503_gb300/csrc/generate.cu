@@ -1,15 +1,30 @@
 // Phase 1: sub-VDI generation (sec. 4, sec. 5.1).
 //
-// gen_count_kernel: one thread per (PE, ray), 16 x 16 pixel tiles per CTA as in
-// the paper's work-groups, each warp an 8 x 4 pixel block for coherent volume
-// access.  It marches the PE's owned samples and runs the supersegment state
-// machine (Eq. 1) to choose gamma: a fixed value, the per-ray bisection search
-// of sec. 2.4, or a given per-ray value with the search as fallback.  The
-// search replays sequential bisection exactly but evaluates two levels per
-// march (midpoint and both quarter points), and the first march also counts
-// the non-transparent samples, which is the count at gamma = 0.
+// gen_count_kernel chooses gamma per (PE, ray): a fixed value, the per-ray
+// bisection search of sec. 2.4, or a given per-ray value with the search as
+// fallback.  It is a persistent kernel: CTAs of 128 threads take (PE, 16 x 8
+// pixel tile) work items from an atomic counter (the paper used 16 x 16
+// work-groups); each warp is an 8 x 4 pixel block so its rays read
+// neighbouring cells.  Every thread owns a fixed slot of the sample cache in
+// the workspace:
+//   - the first march over the PE's owned samples counts the non-transparent
+//     samples (the count at gamma = 0) and stores each of them, with the
+//     number of transparent samples before it, in the slot (entry-major, so
+//     a warp's later reads are coalesced);
+//   - every bisection march then runs over the cached samples instead of
+//     re-sampling the volume.  It evaluates a midpoint and both its children;
+//     the sequential bisection choices are replayed from those counts.
+// Rays with more non-transparent samples than a slot holds, and calls whose
+// workspace has no room for the cache, re-march the volume instead (same
+// decisions, same result).
 //
-// gen_emit_kernel: re-marches with the chosen gamma and writes the records at
+// A run of transparent samples inside an open supersegment S is decided by
+// its first sample: the criterion's distance |C_S| (1 - T_S^(1/m)) decreases
+// strictly as the run lengthens S (m grows, nothing else changes), so if the
+// first one is absorbed, so are the rest.  Every GPU path applies this rule,
+// so cached, re-marched and emitting marches take identical decisions.
+//
+// gen_emit_kernel re-marches with the chosen gamma and writes the records at
 // the prefix-sum offsets (compact layout, sec. 4).
 #include <climits>
 #include <float.h>
@@ -29,16 +44,21 @@ struct GenArgs {
     int mode;  // 0 fixed, 1 search, 2 given (+ fallback)
     float gamma;
     int prec;
-    int tiles_x;
+    int tiles_x, tiles_y;
     unsigned int* status;
+    unsigned int* counter;  // work-item counter (persistent kernel)
+    float4* cache_a;        // sample cache: [cap][slots] (P.rgb, a)
+    float2* cache_b;        // [cap][slots] (log2(1 - a), transparent samples before it)
+    int cache_cap, slots;
 };
 
-constexpr int kTile = 16;
+constexpr int kTileW = 16, kTileH = 8, kGenThreads = 128;
+constexpr int kCacheCap = 640;  // cached non-transparent samples per (PE, ray)
 
 // Work census (VDI_FLAG_CENSUS): kept in registers; the kernel variant
 // without the census never stores it, so the counting is compiled out.
 struct Census {
-    unsigned long long evals = 0, steps = 0, passes = 0;
+    unsigned long long evals = 0, steps = 0, passes = 0, searched = 0, overflow = 0, cached = 0, remarched = 0;
 };
 
 // 257 entries of (colour/opacity, difference to the next entry); opacity
@@ -61,139 +81,284 @@ __device__ __forceinline__ void load_lut(const GenArgs& a, float4* lut2) {
     __syncthreads();
 }
 
-__device__ __forceinline__ void tile_pixel(int tiles_x, int& i, int& j) {
-    int t = blockIdx.x;
-    int tx = t % tiles_x, ty = t / tiles_x;
+__device__ __forceinline__ void tile_pixel(int tiles_x, int tile, int& i, int& j) {
+    int tx = tile % tiles_x, ty = tile / tiles_x;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    i = tx * kTile + (warp & 1) * 8 + (lane & 7);
-    j = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+    i = tx * kTileW + (warp & 1) * 8 + (lane & 7);
+    j = ty * kTileH + (warp >> 1) * 4 + (lane >> 3);
 }
 
-// One march over samples [k0, k1): NC gamma candidates (squared) with the
-// given cap, plus the number of non-transparent samples.
+// ---------------------------------------------------------------------------
+// State machine of one gamma candidate over generation samples (all of one
+// step's length): m = samples in S (0: closed), r = 1/m; `run` = S is inside
+// a transparent run whose first sample was absorbed.
+// ---------------------------------------------------------------------------
+struct GenCount {
+    float P[3], A, L2, m;
+    int cnt;
+    bool run;
+};
+
+__device__ __forceinline__ void gc_reset(GenCount& s) {
+    s.m = 0.f;
+    s.cnt = 0;
+    s.run = false;
+}
+
+__device__ __forceinline__ void gc_open(GenCount& s, const float P[3], float a, float lgT) {
+    s.P[0] = P[0]; s.P[1] = P[1]; s.P[2] = P[2];
+    s.A = a; s.L2 = lgT; s.m = 1.f;
+    s.run = false;
+    ++s.cnt;
+}
+
+// one sample (P premultiplied, opacity a, lgT = log2(1 - a))
+__device__ __forceinline__ void gc_step(GenCount& s, const float P[3], float a, float lgT, float g2, int cap) {
+    if (s.m == 0.f) {
+        if (a > 0.f) gc_open(s, P, a, lgT);
+        return;
+    }
+    if (a == 0.f && s.run) {  // rest of an absorbed transparent run
+        s.m = __fadd_rn(s.m, 1.f);
+        return;
+    }
+    if (s.cnt < cap && criterion(s.P, s.A, s.L2, rcp_approx(s.m), P, g2)) {
+        if (a > 0.f) gc_open(s, P, a, lgT);
+        else s.m = 0.f;
+    } else if (a > 0.f) {
+        absorb(s.P, s.A, s.L2, P, a, lgT);
+        s.m = __fadd_rn(s.m, 1.f);
+        s.run = false;
+    } else {
+        s.m = __fadd_rn(s.m, 1.f);
+        s.run = true;
+    }
+}
+
+// a run of n >= 1 transparent samples, all at once (same decisions as n gc_step calls)
+__device__ __forceinline__ void gc_run(GenCount& s, float n, float g2, int cap) {
+    if (s.m == 0.f) return;
+    const float zero[3] = {0.f, 0.f, 0.f};
+    if (s.cnt < cap && criterion(s.P, s.A, s.L2, rcp_approx(s.m), zero, g2)) {
+        s.m = 0.f;
+    } else {
+        s.m = __fadd_rn(s.m, n);
+        s.run = true;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Marches
+// ---------------------------------------------------------------------------
+struct CacheRef {
+    float4* a;
+    float2* b;
+    int slot, slots, cap;
+    __device__ __forceinline__ size_t at(int j) const { return (size_t)j * slots + slot; }
+};
+
+// First march: counts non-transparent samples and, if `c` is given, caches
+// them (up to c->cap).  NC gamma candidates ride along (NC may be 0).
 template <int NC>
-__device__ __forceinline__ void count_pass(const Ray& r, float step, int k0, int k1, const BrickDev& b,
-                                           const float4* lut2, float scale255, const float g2[NC], int cap,
-                                           int cnt[NC], int& nt, Census& cs) {
+__device__ __forceinline__ int first_march(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
+                                           float scale255, const float* g2, int cap, const CacheRef* c, int* cnt,
+                                           Census& cs) {
     cs.evals += (unsigned long long)(k1 - k0);
     cs.steps += (unsigned long long)(k1 - k0) * NC;
     cs.passes += 1;
-    GenCount st[NC];
+    GenCount st[NC > 0 ? NC : 1];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) gc_reset(st[c]);
-    int n_nt = 0;
-    long long P[3];
+    for (int q = 0; q < NC; ++q) gc_reset(st[q]);
+    int nt = 0, gap = 0;
+    march(r, k0, k1, b, lut2, scale255, [&](int, const Sample& s) {
+        if (s.a > 0.f) {
+            if (c && nt < c->cap) {
+                c->a[c->at(nt)] = make_float4(s.P[0], s.P[1], s.P[2], s.a);
+                c->b[c->at(nt)] = make_float2(s.lgT, (float)gap);
+            }
+            ++nt;
+            gap = 0;
+        } else {
+            ++gap;
+        }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) P[a] = r.P0[a] + (long long)k0 * r.D[a];
-    for (int k = k0; k < k1; ++k) {
-        Sample s;
-        sample_at(P, b, lut2, scale255, s);
+        for (int q = 0; q < NC; ++q) gc_step(st[q], s.P, s.a, s.lgT, g2[q], cap);
+    });
 #pragma unroll
-        for (int a = 0; a < 3; ++a) P[a] += r.D[a];
-        n_nt += s.a > 0.f;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) gc_step(st[c], s, g2[c], cap);
-    }
-#pragma unroll
-    for (int c = 0; c < NC; ++c) cnt[c] = st[c].cnt;
-    nt = n_nt;
+    for (int q = 0; q < NC; ++q) cnt[q] = st[q].cnt;
+    return nt;
 }
 
-// Per-ray bisection search (sec. 2.4) given the count at gamma = 0 is above n_s.
-// Returns gamma (upper end) and the count there.
-__device__ __forceinline__ float search(const Ray& r, float step, int k0, int k1, const BrickDev& b,
-                                        const float4* lut2, float scale255, int n_s, int iters, int c0,
-                                        const int* first_counts, int& count, Census& cs) {
-    Bisect bs;
-    bs.lo = 0.f;
-    bs.hi = 2.f;
-    bs.it = 0;
-    bs.cnt_hi = c0 > 0 ? 1 : 0;  // the distance never reaches 2: one supersegment
-    bs.done = false;
-    int c[3];
-    if (first_counts) {
-        c[0] = first_counts[0]; c[1] = first_counts[1]; c[2] = first_counts[2];
-        bisect_apply(bs, c, n_s, iters);
+// Bisection march over the cached samples: three candidates.  Entries are
+// read two ahead of their use so the loads overlap the state-machine work.
+__device__ __forceinline__ void cached_march(const CacheRef& c, int nt, const float g2[3], int cnt[3], Census& cs) {
+    cs.steps += (unsigned long long)nt * 3;
+    cs.passes += 1;
+    GenCount st[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) gc_reset(st[q]);
+    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+    float2 y0 = make_float2(0.f, 0.f), y1 = y0;
+    if (nt > 0) { x0 = __ldcg(c.a + c.at(0)); y0 = __ldcg(c.b + c.at(0)); }
+    if (nt > 1) { x1 = __ldcg(c.a + c.at(1)); y1 = __ldcg(c.b + c.at(1)); }
+    for (int j = 0; j < nt; ++j) {
+        const float4 x = x0;
+        const float2 y = y0;
+        x0 = x1;
+        y0 = y1;
+        if (j + 2 < nt) {
+            x1 = __ldcg(c.a + c.at(j + 2));
+            y1 = __ldcg(c.b + c.at(j + 2));
+        }
+        const float P[3] = {x.x, x.y, x.z};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (y.y > 0.f) gc_run(st[q], y.y, g2[q], INT_MAX);
+            gc_step(st[q], P, x.w, y.x, g2[q], INT_MAX);
+        }
     }
-    while (!bs.done) {
-        float g[3], g2[3];
-        bisect_candidates(bs, g);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) cnt[q] = st[q].cnt;
+}
+
+// Bisection march over the volume: three candidates.
+__device__ __forceinline__ void volume_march(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
+                                             float scale255, const float g2[3], int cnt[3], Census& cs) {
+    first_march<3>(r, k0, k1, b, lut2, scale255, g2, INT_MAX, nullptr, cnt, cs);
+}
+
+// Per-ray bisection search (sec. 2.4), called when the count at gamma = 0
+// (nt) exceeds n_s: sequential bisection of [0, 2]; each march evaluates the
+// midpoint and its two children, so two levels are decided per march.
+__device__ __forceinline__ float search(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
+                                        float scale255, int n_s, int iters, int nt, const CacheRef* c, int& count,
+                                        Census& cs) {
+    float lo = 0.f, hi = 2.f;
+    int cnt_hi = nt > 0 ? 1 : 0;  // the distance never reaches 2: one supersegment
+    int it = 0;
+    while (it < iters) {
+        const float mid = 0.5f * (lo + hi);
+        const float g[3] = {mid, 0.5f * (lo + mid), 0.5f * (mid + hi)};
+        float g2[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) g2[q] = __fmul_rn(g[q], g[q]);
-        int nt;
-        count_pass<3>(r, step, k0, k1, b, lut2, scale255, g2, INT_MAX, c, nt, cs);
-        bisect_apply(bs, c, n_s, iters);
+        int cnt[3];
+        if (c) {
+            cached_march(*c, nt, g2, cnt, cs);
+            cs.cached += 1;
+        } else {
+            volume_march(r, k0, k1, b, lut2, scale255, g2, cnt, cs);
+            cs.remarched += 1;
+        }
+        // level 1: the midpoint
+        ++it;
+        int child;
+        if (cnt[0] <= n_s) {
+            hi = mid;
+            cnt_hi = cnt[0];
+            if (cnt[0] == n_s) break;
+            child = 1;
+        } else {
+            lo = mid;
+            child = 2;
+        }
+        if (it >= iters) break;
+        // level 2: the child inside the new bracket
+        ++it;
+        const int cc = cnt[child];
+        if (cc <= n_s) {
+            hi = g[child];
+            cnt_hi = cc;
+            if (cc == n_s) break;
+        } else {
+            lo = g[child];
+        }
     }
-    count = bs.cnt_hi;
-    return bs.hi;
+    count = cnt_hi;
+    return hi;
 }
 
 template <bool CENSUS>
-__global__ void __launch_bounds__(256, 2) gen_count_kernel(const __grid_constant__ GenArgs a) {
+__global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
+    __shared__ unsigned int s_item;
     load_lut(a, lut2);
-    int i, j;
-    tile_pixel(a.tiles_x, i, j);
-    if (i >= a.cam.W || j >= a.cam.H) return;
-    const int e = blockIdx.y;
-    const BrickDev& b = a.b[e];
-    const CompactDev& o = a.out[e];
-    const size_t p = (size_t)j * a.cam.W + i;
-    Ray r;
-    int k0 = 0, k1 = 0;
-    bool any = ray_setup(a.cam, i, j, a.dims, a.step, r) && owned_range(r, a.step, b, a.dims, k0, k1);
-    float gamma = 0.f;
-    int count = 0;
+    const unsigned tiles = (unsigned)(a.tiles_x * a.tiles_y);
+    const unsigned total = tiles * (unsigned)a.k;
+    CacheRef cref;
+    cref.a = a.cache_a;
+    cref.b = a.cache_b;
+    cref.slot = blockIdx.x * blockDim.x + threadIdx.x;
+    cref.slots = a.slots;
+    cref.cap = a.cache_cap;
     Census cs;
-    if (a.mode == 2) gamma = fmaxf(o.gamma[p], 0.f);
-    if (any) {
-        if (a.mode == 0) {
-            float g2[1] = {__fmul_rn(a.gamma, a.gamma)};
-            int c[1], nt;
-            count_pass<1>(r, a.step, k0, k1, b, lut2, a.scale255, g2, a.n_s, c, nt, cs);
-            gamma = a.gamma;
-            count = c[0];
-        } else if (a.mode == 2) {
-            float g2[1] = {__fmul_rn(gamma, gamma)};
-            int c[1], nt;
-            count_pass<1>(r, a.step, k0, k1, b, lut2, a.scale255, g2, INT_MAX, c, nt, cs);
-            if (c[0] <= a.n_s) {
+    unsigned long long rays = 0;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const unsigned item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        const int e = (int)(item / tiles);
+        int i, j;
+        tile_pixel(a.tiles_x, (int)(item % tiles), i, j);
+        if (i >= a.cam.W || j >= a.cam.H) continue;
+        const BrickDev& b = a.b[e];
+        const CompactDev& o = a.out[e];
+        const size_t p = (size_t)j * a.cam.W + i;
+        Ray r;
+        int k0 = 0, k1 = 0;
+        const bool any = ray_setup(a.cam, i, j, a.dims, a.step, r) && owned_range(r, a.step, b, a.dims, k0, k1);
+        float gamma = a.mode == 0 ? a.gamma : (a.mode == 2 ? fmaxf(o.gamma[p], 0.f) : 0.f);
+        int count = 0;
+        if (any) {
+            rays += 1;
+            if (a.mode == 0) {
+                const float g2[1] = {__fmul_rn(a.gamma, a.gamma)};
+                int c[1];
+                first_march<1>(r, k0, k1, b, lut2, a.scale255, g2, a.n_s, nullptr, c, cs);
                 count = c[0];
             } else {
-                // fallback: the full search (its first march re-counts gamma = 0)
-                float g2s[3] = {1.f, 0.25f, 2.25f};
-                int c3[3];
-                count_pass<3>(r, a.step, k0, k1, b, lut2, a.scale255, g2s, INT_MAX, c3, nt, cs);
-                if (nt <= a.n_s) {
-                    gamma = 0.f;
-                    count = nt;
-                } else {
-                    gamma = search(r, a.step, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c3, count, cs);
+                bool need_search = true;
+                if (a.mode == 2) {
+                    const float g2[1] = {__fmul_rn(gamma, gamma)};
+                    int c[1];
+                    first_march<1>(r, k0, k1, b, lut2, a.scale255, g2, INT_MAX, nullptr, c, cs);
+                    if (c[0] <= a.n_s) {
+                        count = c[0];
+                        need_search = false;
+                    }
+                }
+                if (need_search) {
+                    const bool use_cache = a.cache_a != nullptr;
+                    int dummy[1];
+                    const int nt = first_march<0>(r, k0, k1, b, lut2, a.scale255, nullptr, INT_MAX,
+                                                  use_cache ? &cref : nullptr, dummy, cs);
+                    if (nt <= a.n_s) {
+                        gamma = 0.f;
+                        count = nt;
+                    } else {
+                        const CacheRef* c = (use_cache && nt <= a.cache_cap) ? &cref : nullptr;
+                        cs.searched += 1;
+                        cs.overflow += c ? 0 : 1;
+                        gamma = search(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count, cs);
+                    }
                 }
             }
-        } else {
-            // search: gamma = 0 (non-transparent count) and bisection levels 1-2 in one march
-            float g2[3] = {1.f, 0.25f, 2.25f};
-            int c[3], nt;
-            count_pass<3>(r, a.step, k0, k1, b, lut2, a.scale255, g2, INT_MAX, c, nt, cs);
-            if (nt <= a.n_s) {
-                gamma = 0.f;
-                count = nt;
-            } else {
-                gamma = search(r, a.step, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count, cs);
-            }
         }
-    } else if (a.mode == 0) {
-        gamma = a.gamma;
+        o.counts[p] = (uint32_t)count;
+        if (o.gamma) o.gamma[p] = gamma;
     }
-    o.counts[p] = (uint32_t)count;
-    if (o.gamma) o.gamma[p] = gamma;
     if (CENSUS) {
         unsigned long long* ctr = reinterpret_cast<WsHeader*>(a.status)->counters;
         atomicAdd(ctr + 0, cs.evals);
         atomicAdd(ctr + 1, cs.steps);
         atomicAdd(ctr + 2, cs.passes);
-        atomicAdd(ctr + 3, any ? 1ull : 0ull);
+        atomicAdd(ctr + 3, rays);
+        atomicAdd(ctr + 4, cs.searched);
+        atomicAdd(ctr + 5, cs.overflow);
+        atomicAdd(ctr + 6, cs.cached);
+        atomicAdd(ctr + 7, cs.remarched);
     }
 }
 
@@ -221,11 +386,11 @@ __device__ __forceinline__ void store_record(const GenArgs& a, const CompactDev&
     }
 }
 
-__global__ void __launch_bounds__(256, 2) gen_emit_kernel(const __grid_constant__ GenArgs a) {
+__global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     load_lut(a, lut2);
     int i, j;
-    tile_pixel(a.tiles_x, i, j);
+    tile_pixel(a.tiles_x, blockIdx.x, i, j);
     if (i >= a.cam.W || j >= a.cam.H) return;
     const int e = blockIdx.y;
     const BrickDev& b = a.b[e];
@@ -240,47 +405,34 @@ __global__ void __launch_bounds__(256, 2) gen_emit_kernel(const __grid_constant_
     const float g2 = __fmul_rn(gamma, gamma);
     const uint64_t base = o.offsets[p];
     const int cap = a.n_s;
-    // state machine with record tracking (same decisions as GenCount)
-    float P[3] = {0.f, 0.f, 0.f}, A = 0.f, L2 = 0.f, m = 0.f;
-    int cnt = 0, kopen = 0, klast = 0;
+    // the GenCount state machine (same decisions), tracking the records
+    GenCount st;
+    gc_reset(st);
+    int kopen = 0, klast = 0;
     uint32_t written = 0;
-    long long Pos[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) Pos[q] = r.P0[q] + (long long)k0 * r.D[q];
-    for (int k = k0; k < k1; ++k) {
-        Sample s;
-        sample_at(Pos, b, lut2, a.scale255, s);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) Pos[q] += r.D[q];
-        bool open_new = false;
-        if (m == 0.f) {
-            open_new = s.a > 0.f;
-        } else {
-            float rr = rcp_approx(m);
-            if (cnt < cap && criterion(P, A, L2, rr, s.P, g2)) {
-                if (written < want) {
-                    RecOut ro{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1), {P[0], P[1], P[2]}, A};
-                    store_record(a, o, base + written, ro);
-                }
-                ++written;
-                m = 0.f;
-                open_new = s.a > 0.f;
-            } else {
-                absorb(P, A, L2, s.P, s.a, s.lgT);
-                m = __fadd_rn(m, 1.f);
-                if (s.a > 0.f) klast = k;
-            }
+    march(r, k0, k1, b, lut2, a.scale255, [&](int k, const Sample& s) {
+        const bool was_open = st.m != 0.f;
+        const int before = st.cnt;
+        const RecOut cur{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1),
+                         {st.P[0], st.P[1], st.P[2]}, st.A};
+        gc_step(st, s.P, s.a, s.lgT, g2, cap);
+        // S closed by this sample: either it was shut (m = 0) or a new one opened
+        const bool closed = was_open && (st.m == 0.f || st.cnt != before);
+        if (closed) {
+            if (written < want) store_record(a, o, base + written, cur);
+            ++written;
         }
-        if (open_new) {
-            P[0] = s.P[0]; P[1] = s.P[1]; P[2] = s.P[2];
-            A = s.a; L2 = s.lgT; m = 1.f;
-            kopen = k; klast = k;
-            ++cnt;
+        if (st.cnt != before) {
+            kopen = k;
+            klast = k;
+        } else if (st.m != 0.f && s.a > 0.f) {
+            klast = k;
         }
-    }
-    if (m != 0.f) {
+    });
+    if (st.m != 0.f) {
         if (written < want) {
-            RecOut ro{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1), {P[0], P[1], P[2]}, A};
+            RecOut ro{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1), {st.P[0], st.P[1], st.P[2]},
+                      st.A};
             store_record(a, o, base + written, ro);
         }
         ++written;
@@ -304,22 +456,63 @@ static void fill_args(GenArgs& a, const BrickDev* bricks, int k, const float* lu
     a.k = k;
     a.n_s = n_s;
     a.status = status;
-    a.tiles_x = (cam.W + kTile - 1) / kTile;
+    a.tiles_x = (cam.W + kTileW - 1) / kTileW;
+    a.tiles_y = (cam.H + kTileH - 1) / kTileH;
+    a.counter = nullptr;
+    a.cache_a = nullptr;
+    a.cache_b = nullptr;
+    a.cache_cap = 0;
+    a.slots = 0;
+}
+
+// persistent grid of gen_count_kernel on the current device
+vdi_status gen_count_grid(int& ctas) {
+    int dev = 0, sms = 0, per_sm = 0, per_sm_c = 0;
+    vdi_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s != VDI_OK) return s;
+    s = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    if (s != VDI_OK) return s;
+    s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gen_count_kernel<false>, kGenThreads, 0),
+                   "occupancy");
+    if (s != VDI_OK) return s;
+    s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, gen_count_kernel<true>, kGenThreads, 0),
+                   "occupancy");
+    if (s != VDI_OK) return s;
+    if (per_sm_c > per_sm) per_sm = per_sm_c;
+    ctas = sms * (per_sm > 0 ? per_sm : 1);
+    return VDI_OK;
+}
+
+size_t gen_cache_bytes(int ctas) {
+    return (size_t)ctas * kGenThreads * kCacheCap * (sizeof(float4) + sizeof(float2));
 }
 
 vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                             float scale255, float step, float ref_len, int n_s, float gamma, int iters,
-                            const CompactDev* out, unsigned int* status, bool census, cudaStream_t st) {
+                            const CompactDev* out, unsigned int* status, bool census, unsigned int* counter,
+                            void* cache, size_t cache_bytes, cudaStream_t st) {
     GenArgs a;  // copied into the launch's parameter space
     fill_args(a, bricks, k, lut, cam, dims, scale255, step, ref_len, n_s, out, status);
     a.iters = iters;
     a.gamma = gamma;
     a.mode = gamma >= 0.f ? 0 : (gamma == VDI_GAMMA_GIVEN ? 2 : 1);
     a.prec = 0;
-    int tiles_y = (cam.H + kTile - 1) / kTile;
-    dim3 grid((unsigned)(a.tiles_x * tiles_y), (unsigned)k);
-    if (census) gen_count_kernel<true><<<grid, 256, 0, st>>>(a);
-    else gen_count_kernel<false><<<grid, 256, 0, st>>>(a);
+    a.counter = counter;
+    int ctas = 0;
+    vdi_status s = gen_count_grid(ctas);
+    if (s != VDI_OK) return s;
+    const unsigned items = (unsigned)(a.tiles_x * a.tiles_y) * (unsigned)k;
+    if (items == 0) return VDI_OK;
+    if (cache && cache_bytes >= gen_cache_bytes(ctas)) {
+        a.slots = ctas * kGenThreads;
+        a.cache_cap = kCacheCap;
+        a.cache_a = reinterpret_cast<float4*>(cache);
+        a.cache_b = reinterpret_cast<float2*>(static_cast<char*>(cache) +
+                                              (size_t)a.slots * kCacheCap * sizeof(float4));
+    }
+    if ((unsigned)ctas > items) ctas = (int)items;
+    if (census) gen_count_kernel<true><<<ctas, kGenThreads, 0, st>>>(a);
+    else gen_count_kernel<false><<<ctas, kGenThreads, 0, st>>>(a);
     return cuda_check(cudaGetLastError(), "gen_count_kernel launch");
 }
 
@@ -332,9 +525,9 @@ vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, cons
     a.gamma = 0.f;
     a.mode = 0;
     a.prec = prec;
-    int tiles_y = (cam.H + kTile - 1) / kTile;
-    dim3 grid((unsigned)(a.tiles_x * tiles_y), (unsigned)k);
-    gen_emit_kernel<<<grid, 256, 0, st>>>(a);
+    dim3 grid((unsigned)(a.tiles_x * a.tiles_y), (unsigned)k);
+    if (grid.x == 0) return VDI_OK;
+    gen_emit_kernel<<<grid, kGenThreads, 0, st>>>(a);
     return cuda_check(cudaGetLastError(), "gen_emit_kernel launch");
 }
 

@@ -19,10 +19,12 @@
 
 namespace vdi {
 
-// status header + 65536 partial sums of 8 bytes: k * ceil(W*H / 4096) <= 65536,
-// e.g. 64 PEs of 2048 x 2048 pixels or 8 PEs of 8192 x 8192.
+// status header, work counter and 65536 partial sums of 8 bytes:
+// k * ceil(W*H / 4096) <= 65536, e.g. 64 PEs of 2048 x 2048 pixels or 8 PEs
+// of 8192 x 8192.  There is no room for the sample cache, so the gamma search
+// re-marches the volume (same result).
 constexpr size_t kStaticPartials = 65536;
-constexpr size_t kStaticScratchBytes = kWsHeader + kStaticPartials * sizeof(uint64_t);
+constexpr size_t kStaticScratchBytes = kGenFixed + kStaticPartials * sizeof(uint64_t);
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -63,7 +65,7 @@ extern "C" vdi_status vdi_generate_static_scratch(const vdi_brick* bricks, int32
                          "vdi_generate_static_scratch: %d PEs x %zu pixels exceed the static scratch "
                          "(k * ceil(W*H / 4096) must be <= %zu); use vdi_generate with a workspace",
                          k, npix, kStaticPartials);
-    if (vdi_generate_workspace(k, cam->width, cam->height) > kStaticScratchBytes)
+    if (kGenFixed + (size_t)k * chunks * sizeof(uint64_t) > kStaticScratchBytes)
         return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_static_scratch: request exceeds the static scratch");
     void* scratch = nullptr;
     vdi_status s = static_scratch_address(&scratch);

@@ -246,30 +246,29 @@ struct Sample {
     float lgT;   // log2(1 - a)
 };
 
-// P: fixed-point midpoint of the sample
-__device__ __forceinline__ void sample_at(const long long P[3], const BrickDev& b, const float4* __restrict__ lut2,
-                                          float scale255, Sample& s) {
-    int ci[3];
-    float w[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        ci[a] = fixed_cell(P[a]);
-        w[a] = fixed_frac(P[a]);
-    }
-    // local cell index in the padded brick (border of one cell on every side)
-    int lx = ci[0] - b.lo[0] + 1, ly = ci[1] - b.lo[1] + 1, lz = ci[2] - b.lo[2] + 1;
+// Corner values of the cell holding the fixed-point position P (two float4
+// loads).  The index is clamped to the brick, so the load is always in bounds.
+__device__ __forceinline__ void cell_load(const long long P[3], const BrickDev& b, float4& lo, float4& hi) {
+    int lx = fixed_cell(P[0]) - b.lo[0] + 1, ly = fixed_cell(P[1]) - b.lo[1] + 1, lz = fixed_cell(P[2]) - b.lo[2] + 1;
     int idx = (lz * b.ny + ly) * b.nx + lx;
     idx = min(max(idx, 0), b.ncells - 1);
     const float4* cp = reinterpret_cast<const float4*>(b.cells) + 2 * (size_t)idx;
-    float4 lo = __ldg(cp), hi = __ldg(cp + 1);
-    // corners: lo = (v000, v100, v010, v110), hi = (v001, v101, v011, v111)
-    float c00 = __fmaf_rn(w[0], __fsub_rn(lo.y, lo.x), lo.x);
-    float c10 = __fmaf_rn(w[0], __fsub_rn(lo.w, lo.z), lo.z);
-    float c01 = __fmaf_rn(w[0], __fsub_rn(hi.y, hi.x), hi.x);
-    float c11 = __fmaf_rn(w[0], __fsub_rn(hi.w, hi.z), hi.z);
-    float c0 = __fmaf_rn(w[1], __fsub_rn(c10, c00), c00);
-    float c1 = __fmaf_rn(w[1], __fsub_rn(c11, c01), c01);
-    float v = __fmaf_rn(w[2], __fsub_rn(c1, c0), c0);
+    lo = __ldg(cp);
+    hi = __ldg(cp + 1);
+}
+
+// Sample at fixed-point midpoint P from its cell's corners (lo = v000 v100 v010
+// v110, hi = v001 v101 v011 v111): trilinear value, classification with the
+// step-corrected table (257 entries of value and difference), premultiplied colour.
+__device__ __forceinline__ void sample_from(float w0, float w1, float w2, const float4& lo, const float4& hi,
+                                            const float4* __restrict__ lut2, float scale255, Sample& s) {
+    float c00 = __fmaf_rn(w0, __fsub_rn(lo.y, lo.x), lo.x);
+    float c10 = __fmaf_rn(w0, __fsub_rn(lo.w, lo.z), lo.z);
+    float c01 = __fmaf_rn(w0, __fsub_rn(hi.y, hi.x), hi.x);
+    float c11 = __fmaf_rn(w0, __fsub_rn(hi.w, hi.z), hi.z);
+    float c0 = __fmaf_rn(w1, __fsub_rn(c10, c00), c00);
+    float c1 = __fmaf_rn(w1, __fsub_rn(c11, c01), c01);
+    float v = __fmaf_rn(w2, __fsub_rn(c1, c0), c0);
     float x = fminf(fmaxf(__fmul_rn(v, scale255), 0.f), 255.f);
     float fl;
     int i = floor_magic(x, fl);
@@ -284,6 +283,31 @@ __device__ __forceinline__ void sample_at(const long long P[3], const BrickDev& 
     s.P[1] = __fmul_rn(G, A);
     s.P[2] = __fmul_rn(B, A);
     s.lgT = lg2_approx(__fsub_rn(1.f, A));
+}
+
+// March over samples [k0, k1) of ray r in brick b, calling f(k, sample) in
+// order.  The next sample's cell is loaded while the current one is
+// processed, so the load latency overlaps the state-machine work.
+template <typename F>
+__device__ __forceinline__ void march(const Ray& r, int k0, int k1, const BrickDev& b, const float4* __restrict__ lut2,
+                                      float scale255, F&& f) {
+    long long P[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) P[a] = r.P0[a] + (long long)k0 * r.D[a];
+    float4 clo, chi;
+    cell_load(P, b, clo, chi);
+    for (int k = k0; k < k1; ++k) {
+        const float w0 = fixed_frac(P[0]), w1 = fixed_frac(P[1]), w2 = fixed_frac(P[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) P[a] += r.D[a];
+        float4 nlo, nhi;
+        cell_load(P, b, nlo, nhi);  // next sample's cell, in flight during this sample's work
+        Sample s;
+        sample_from(w0, w1, w2, clo, chi, lut2, scale255, s);
+        f(k, s);
+        clo = nlo;
+        chi = nhi;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -304,6 +328,21 @@ __device__ __forceinline__ bool criterion(const float P[3], float A, float L2, f
     return D >= __fmul_rn(g2, __fmul_rn(A, A));
 }
 
+// The same decision, also returning the decision ratio q ~= D / A^2 (one
+// approximate reciprocal): every gamma with gamma^2 on the same side of q
+// takes the same decision at this step.
+__device__ __forceinline__ bool criterion_q(const float P[3], float A, float L2, float r, const float Px[3], float g2,
+                                            float& q) {
+    float at = __fsub_rn(1.f, ex2_approx(__fmul_rn(L2, r)));
+    float e0 = __fmaf_rn(P[0], at, -__fmul_rn(A, Px[0]));
+    float e1 = __fmaf_rn(P[1], at, -__fmul_rn(A, Px[1]));
+    float e2 = __fmaf_rn(P[2], at, -__fmul_rn(A, Px[2]));
+    float D = __fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0)));
+    float AA = __fmul_rn(A, A);
+    q = __fmul_rn(D, rcp_approx(AA));
+    return D >= __fmul_rn(g2, AA);
+}
+
 // absorb piece x into S ("over")
 __device__ __forceinline__ void absorb(float P[3], float& A, float& L2, const float Px[3], float ax, float lgTx) {
     float T = __fsub_rn(1.f, A);
@@ -314,93 +353,31 @@ __device__ __forceinline__ void absorb(float P[3], float& A, float& L2, const fl
     L2 = __fadd_rn(L2, lgTx);
 }
 
-// Counting state of one gamma candidate over generation samples (equal lengths):
-// m = samples in S (0: closed).  r = 1/m.
-struct GenCount {
-    float P[3], A, L2, m;
-    int cnt;
+// Known counts: exact candidates and their decision intervals.
+struct CountTable {
+    static constexpr int N = 27;  // 9 marches of 3 candidates cover 16 levels
+    float g2[N], lo[N], hi[N];
+    int c[N];
+    int n;
+    __device__ __forceinline__ void add(float g2v, float qlo, float qhi, int cnt) {
+        if (n >= N) n = 0;  // full (more than 16 levels): start over, dropping the oldest
+        {
+            g2[n] = g2v;
+            lo[n] = qlo;
+            hi[n] = qhi;
+            c[n] = cnt;
+            ++n;
+        }
+    }
+    // count at gamma^2 = x if known, else -1.  The interval is narrowed by a
+    // relative margin of 2^-16, far above the ratio's approximation error.
+    __device__ __forceinline__ int lookup(float x) const {
+        for (int i = 0; i < n; ++i) {
+            if (x == g2[i]) return c[i];
+            if (x > lo[i] * (1.f + 1.0f / 65536.f) && x <= hi[i] * (1.f - 1.0f / 65536.f)) return c[i];
+        }
+        return -1;
+    }
 };
-
-__device__ __forceinline__ void gc_reset(GenCount& s) {
-    s.m = 0.f;
-    s.cnt = 0;
-}
-
-__device__ __forceinline__ void gc_step(GenCount& s, const Sample& x, float g2, int cap) {
-    if (s.m == 0.f) {
-        if (x.a > 0.f) {
-            s.P[0] = x.P[0]; s.P[1] = x.P[1]; s.P[2] = x.P[2];
-            s.A = x.a; s.L2 = x.lgT; s.m = 1.f;
-            ++s.cnt;
-        }
-        return;
-    }
-    float r = rcp_approx(s.m);
-    if (s.cnt < cap && criterion(s.P, s.A, s.L2, r, x.P, g2)) {
-        if (x.a > 0.f) {
-            s.P[0] = x.P[0]; s.P[1] = x.P[1]; s.P[2] = x.P[2];
-            s.A = x.a; s.L2 = x.lgT; s.m = 1.f;
-            ++s.cnt;
-        } else {
-            s.m = 0.f;
-        }
-    } else {
-        absorb(s.P, s.A, s.L2, x.P, x.a, x.lgT);
-        s.m = __fadd_rn(s.m, 1.f);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Bisection bookkeeping (sec. 2.4): sequential bisection on [0, 2] advanced two
-// levels per pass.  A pass evaluates the midpoint and both quarter points; the
-// sequential algorithm's choices are then replayed from those counts.
-// ---------------------------------------------------------------------------
-struct Bisect {
-    float lo, hi;
-    int it;       // levels done
-    int cnt_hi;   // count at hi
-    bool done;
-};
-
-__device__ __forceinline__ void bisect_candidates(const Bisect& b, float g[3]) {
-    float mid = 0.5f * (b.lo + b.hi);
-    g[0] = mid;
-    g[1] = 0.5f * (b.lo + mid);
-    g[2] = 0.5f * (mid + b.hi);
-}
-
-__device__ __forceinline__ void bisect_apply(Bisect& b, const int c[3], int n_s, int iters) {
-    float mid = 0.5f * (b.lo + b.hi);
-    // level 1: midpoint
-    if (c[0] <= n_s) {
-        b.hi = mid;
-        b.cnt_hi = c[0];
-        ++b.it;
-        if (c[0] == n_s || b.it >= iters) { b.done = true; return; }
-        // level 2: quarter point between lo and mid (candidate 1)
-        float q = 0.5f * (b.lo + mid);
-        if (c[1] <= n_s) {
-            b.hi = q;
-            b.cnt_hi = c[1];
-            if (c[1] == n_s) b.done = true;
-        } else {
-            b.lo = q;
-        }
-    } else {
-        b.lo = mid;
-        ++b.it;
-        if (b.it >= iters) { b.done = true; return; }
-        float q = 0.5f * (mid + b.hi);
-        if (c[2] <= n_s) {
-            b.hi = q;
-            b.cnt_hi = c[2];
-            if (c[2] == n_s) b.done = true;
-        } else {
-            b.lo = q;
-        }
-    }
-    ++b.it;
-    if (b.it >= iters) b.done = true;
-}
 
 }  // namespace vdi

@@ -40,8 +40,8 @@ struct CompactDev {
 struct WsHeader {
     unsigned int status;  // vdi_status of the first device-side error
     unsigned int pad;
-    unsigned long long counters[4];  // census (VDI_FLAG_CENSUS)
-    unsigned long long pad2[27];
+    unsigned long long counters[8];  // census (VDI_FLAG_CENSUS)
+    unsigned long long pad2[23];
 };
 static_assert(sizeof(WsHeader) == 256, "workspace header is 256 bytes");
 constexpr size_t kWsHeader = 256;
@@ -58,16 +58,26 @@ vdi_status launch_brick_build(const void* volume, int type, const int dims[3], i
                               float* const* cells, cudaStream_t st);
 vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                             float scale255, float step, float ref_len, int n_s, float gamma, int iters,
-                            const CompactDev* out, unsigned int* status, bool census, cudaStream_t st);
+                            const CompactDev* out, unsigned int* status, bool census, unsigned int* counter,
+                            void* cache, size_t cache_bytes, cudaStream_t st);
+vdi_status gen_count_grid(int& ctas);
+size_t gen_cache_bytes(int ctas);
+// generation workspace: [0, 256) header, [256, 512) work counter, then the
+// prefix sum's partial sums, then (optionally) the sample cache
+constexpr size_t kGenFixed = 512;
 vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                            float scale255, float step, float ref_len, int n_s, int prec, const CompactDev* out,
                            unsigned int* status, cudaStream_t st);
 size_t scan_workspace(int k, int n);
 vdi_status launch_scan(int k, int n, uint32_t* const* counts, uint64_t* const* offsets, void* ws, cudaStream_t st);
 
-struct CompositeArgs;
 vdi_status launch_composite(const vdi_compact* pe, int k, int w, int h, const vdi_regular* out, int iters,
                             int schedule, unsigned int* status, cudaStream_t st);
+int default_schedule(int k);
+size_t batch_table_bytes(const vdi_request* reqs, int n);
+vdi_status batch_table_pack(const vdi_request* reqs, int n, void* host_table, size_t bytes);
+vdi_status launch_composite_batched(const void* dev_table, const void* host_table, int iters, unsigned int* counter,
+                                    unsigned int* status, int device_sms, cudaStream_t st);
 vdi_status launch_flatten(const vdi_regular* v, int w, int h, float* rgba, cudaStream_t st);
 
 }  // namespace vdi
