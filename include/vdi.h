@@ -297,6 +297,77 @@ vdi_status vdi_composite_autotune(vdi_request* reqs, int32_t n, const vdi_params
                                   size_t ws_bytes, vdi_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* Learned gamma.  No counterpart in the paper, which searches gamma per ray */
+/* (sec. 2.4); the search stays as the fallback and as the source of the     */
+/* training labels.  A small MLP predicts log2 gamma per (PE, 16 x 16 tile)  */
+/* from features of the tile's rays.                                          */
+/* ------------------------------------------------------------------------ */
+#define VDI_NFEAT 40       /* features per (PE, tile) */
+#define VDI_GAMMA_TILE 16  /* tile edge in pixels; tiles are row-major, ceil(W/16) per row */
+
+/* Model: one caller-allocated device buffer of vdi_model_bytes() bytes holding
+ * the FP32 master parameters (vdi_model_nparams() = 6849: W1[64][40], b1[64],
+ * W2[64][64], b2[64], w3[64], b3), their BF16 copy used by inference, the Adam
+ * moments, the Adam step count and the init seed. */
+size_t vdi_model_bytes(void);
+int32_t vdi_model_nparams(void);
+/* He-uniform weights from a counter-based generator (seed), zero biases and moments. */
+vdi_status vdi_model_init(void* model, uint64_t seed, vdi_stream stream);
+/* Checkpoint: synchronous copy of the whole buffer to / from a file
+ * ("VDIMLP01" header, version, parameter count, size).  Training resumed from
+ * a checkpoint continues bit for bit. */
+vdi_status vdi_model_save(const void* model, const char* path, vdi_stream stream);
+vdi_status vdi_model_load(void* model, const char* path, vdi_stream stream);
+
+/* Features of every (PE, tile) from the owned samples of the tile's rays at
+ * even pixel offsets (8 x 8 rays): [0..31] histogram of the opacity of
+ * non-transparent samples (bins of 1/64, the last open), normalised; [32],
+ * [33] mean and standard deviation of the first non-transparent sample's
+ * depth from the PE's first sample, over the volume diagonal; [34], [35] the
+ * same for the back of the last one; [36] log1p(mean non-transparent samples
+ * per ray with samples) / 8; [37] n_s / 64; [38] fraction of those rays with a
+ * non-transparent sample; [39] mean |P_k - P_prev| of consecutive
+ * non-transparent samples.  feats: device float[k][tiles][40]; valid: device
+ * uint8[k][tiles], 0 for tiles whose rays own no sample (features all 0). */
+vdi_status vdi_tile_features(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
+                             int32_t n_s, const vdi_params* params, float* feats, uint8_t* valid, vdi_stream stream);
+/* Training labels from a searched generation (searched[e].counts, .gamma):
+ * per tile, the lower median over rays with a supersegment of
+ * log2(max(gamma, 2^-20)).  labels: float[k][tiles]; valid: uint8[k][tiles]. */
+vdi_status vdi_tile_labels(const vdi_compact* searched, int32_t k, int32_t w, int32_t h, float* labels,
+                           uint8_t* valid, vdi_stream stream);
+/* Inference on the tensor cores: log2_gamma[r] = MLP(feats[r]) - offset, n rows. */
+vdi_status vdi_mlp_infer(const void* model, const float* feats, int32_t n, float offset, float* log2_gamma,
+                         vdi_stream stream);
+/* Training (FP32 arithmetic, BF16-rounded weights).  Loss: mean squared error
+ * of the prediction over the rows with valid != 0.  vdi_mlp_grad writes the
+ * gradient (device float[6849]) and the loss (device float); vdi_mlp_train_step
+ * also applies one Adam step (beta 0.9, 0.999, eps 1e-8, learning rate lr).
+ * Deterministic (per-block partial sums in the workspace, fixed-order reduction). */
+size_t vdi_mlp_train_workspace(int32_t n);
+vdi_status vdi_mlp_grad(const void* model, const float* feats, const float* labels, const uint8_t* valid, int32_t n,
+                        float* grad, float* loss, void* workspace, size_t ws_bytes, vdi_stream stream);
+vdi_status vdi_mlp_train_step(void* model, const float* feats, const float* labels, const uint8_t* valid, int32_t n,
+                              float lr, float* loss, void* workspace, size_t ws_bytes, vdi_stream stream);
+/* Learned gamma for generation: tile features, inference, then per ray one
+ * march over the volume that counts at the tile's prediction gp =
+ * 2^(output - offset) and caches the ray's non-transparent samples.  The
+ * prediction then brackets a short search over the cached samples: log2 gamma
+ * in [log2 gp - 4, log2 gp] when gp is feasible (count <= n_s), else
+ * [log2 gp, log2 gp + 4] when its top is; six bisection levels (three cached
+ * marches) give the smallest feasible gamma found.  Rays with no feasible
+ * gamma in the bracket, or too many non-transparent samples for the cache, run
+ * the full bisection search; rays with at most n_s non-transparent samples
+ * take gamma = 0 as in the search.  Writes out[e].gamma and out[e].counts like
+ * vdi_choose_gamma; follow with vdi_generate(..., VDI_GAMMA_CHOSEN, ...) to
+ * emit.  The supersegment counts differ from the full search's only through
+ * the bracket's resolution (a factor 2^(1/16) in gamma). */
+size_t vdi_learned_workspace(int32_t k, int32_t w, int32_t h);
+vdi_status vdi_choose_gamma_learned(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
+                                    int32_t n_s, const void* model, float offset, vdi_compact* out,
+                                    const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* Rendering from the generating view (sec. 2.3: a VDI is exact from its    */
 /* viewpoint of generation by associativity of "over")                      */
 /* ------------------------------------------------------------------------ */

@@ -677,7 +677,8 @@ void oc_split_boxes(const int* dims, const int* g, oc_box* boxes) {
 #define OC_NH 64
 #define OC_TILE 16
 
-/* Features of one (PE, tile) from its rays' owned samples, in order:
+/* Features of one (PE, tile) from the owned samples of the tile's rays at
+ * even pixel offsets (8 x 8 of its 16 x 16 rays), in order:
  *  [0..31]  histogram of the opacity a' of non-transparent samples, bins of
  *           width 1/64 (bin 31 holds a' >= 31/64), normalised to sum 1;
  *  [32],[33] mean and standard deviation over rays with a non-transparent
@@ -712,8 +713,8 @@ int oc_tile_features(const oc_volume* v, const oc_box* boxes, int k, const float
             for (int e = 0; e < k; ++e) {
                 double hist[32] = {0}, sf = 0, sf2 = 0, sl = 0, sl2 = 0, var = 0;
                 long ntot = 0, pairs = 0, rays_own = 0, rays_nt = 0;
-                for (int jj = 0; jj < OC_TILE; ++jj)
-                    for (int ii = 0; ii < OC_TILE; ++ii) {
+                for (int jj = 0; jj < OC_TILE; jj += 2)
+                    for (int ii = 0; ii < OC_TILE; ii += 2) {
                         int i = (t % tx) * OC_TILE + ii, j = (t / tx) * OC_TILE + jj;
                         if (i >= W || j >= H) continue;
                         double o[3], d[3];

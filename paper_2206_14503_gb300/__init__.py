@@ -100,6 +100,19 @@ def _load():
         "vdi_composite_batched_workspace": ([i32], sz),
         "vdi_composite_batched": ([vp, vp, vp, vp, sz, vp], i32),
         "vdi_composite_autotune": ([vp, i32, vp, vp, sz, vp], i32),
+        "vdi_model_bytes": ([], sz),
+        "vdi_model_nparams": ([], i32),
+        "vdi_model_init": ([vp, C.c_uint64, vp], i32),
+        "vdi_model_save": ([vp, C.c_char_p, vp], i32),
+        "vdi_model_load": ([vp, C.c_char_p, vp], i32),
+        "vdi_tile_features": ([vp, i32, vp, vp, i32, vp, vp, vp, vp], i32),
+        "vdi_tile_labels": ([vp, i32, i32, i32, vp, vp, vp], i32),
+        "vdi_mlp_infer": ([vp, vp, i32, f32, vp, vp], i32),
+        "vdi_mlp_train_workspace": ([i32], sz),
+        "vdi_mlp_grad": ([vp, vp, vp, vp, i32, vp, vp, vp, sz, vp], i32),
+        "vdi_mlp_train_step": ([vp, vp, vp, vp, i32, f32, vp, vp, sz, vp], i32),
+        "vdi_learned_workspace": ([i32, i32, i32], sz),
+        "vdi_choose_gamma_learned": ([vp, i32, vp, vp, i32, vp, f32, vp, vp, vp, sz, vp], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -116,7 +129,10 @@ SYMBOLS = ("vdi_version", "vdi_status_string", "vdi_last_error", "vdi_workspace_
            "vdi_brick_bytes", "vdi_brick_build", "vdi_generate_workspace", "vdi_choose_gamma", "vdi_generate",
            "vdi_generate_static_scratch",
            "vdi_composite_workspace", "vdi_composite", "vdi_render_view", "vdi_batch_table_bytes",
-           "vdi_batch_table_pack", "vdi_composite_batched_workspace", "vdi_composite_batched", "vdi_composite_autotune")
+           "vdi_batch_table_pack", "vdi_composite_batched_workspace", "vdi_composite_batched", "vdi_composite_autotune",
+           "vdi_model_bytes", "vdi_model_nparams", "vdi_model_init", "vdi_model_save", "vdi_model_load",
+           "vdi_tile_features", "vdi_tile_labels", "vdi_mlp_infer", "vdi_mlp_train_workspace", "vdi_mlp_grad",
+           "vdi_mlp_train_step", "vdi_learned_workspace", "vdi_choose_gamma_learned")
 
 
 def lib():
@@ -280,6 +296,78 @@ def vdi_composite_batched(dev_table_ptr: int, host_table, params: vdi_params, ws
 def vdi_composite_autotune(reqs: Requests, params: vdi_params, ws_ptr, ws_bytes, stream=None) -> int:
     return _lib.vdi_composite_autotune(_arr(reqs.arr), len(reqs), _ref(params), C.c_void_p(ws_ptr), ws_bytes,
                                        _stream(stream))
+
+
+# ---- learned gamma ----
+VDI_NFEAT = 40
+VDI_GAMMA_TILE = 16
+
+
+def vdi_model_bytes() -> int:
+    return _lib.vdi_model_bytes()
+
+
+def vdi_model_nparams() -> int:
+    return _lib.vdi_model_nparams()
+
+
+def vdi_model_init(model_ptr: int, seed: int, stream=None) -> int:
+    return _lib.vdi_model_init(C.c_void_p(model_ptr), seed, _stream(stream))
+
+
+def vdi_model_save(model_ptr: int, path: str, stream=None) -> int:
+    return _lib.vdi_model_save(C.c_void_p(model_ptr), path.encode(), _stream(stream))
+
+
+def vdi_model_load(model_ptr: int, path: str, stream=None) -> int:
+    return _lib.vdi_model_load(C.c_void_p(model_ptr), path.encode(), _stream(stream))
+
+
+def vdi_tile_features(bricks, lut_ptr, cam: vdi_camera, n_s, params: vdi_params, feats_ptr, valid_ptr,
+                      stream=None) -> int:
+    return _lib.vdi_tile_features(_arr(bricks), len(bricks), C.c_void_p(lut_ptr), _ref(cam), n_s, _ref(params),
+                                  C.c_void_p(feats_ptr), C.c_void_p(valid_ptr), _stream(stream))
+
+
+def vdi_tile_labels(searched, w, h, labels_ptr, valid_ptr, stream=None) -> int:
+    arr = (vdi_compact * len(searched))(*searched)
+    return _lib.vdi_tile_labels(_arr(arr), len(searched), w, h, C.c_void_p(labels_ptr), C.c_void_p(valid_ptr),
+                                _stream(stream))
+
+
+def vdi_mlp_infer(model_ptr, feats_ptr, n, offset, out_ptr, stream=None) -> int:
+    return _lib.vdi_mlp_infer(C.c_void_p(model_ptr), C.c_void_p(feats_ptr), n, offset, C.c_void_p(out_ptr),
+                              _stream(stream))
+
+
+def vdi_mlp_train_workspace(n) -> int:
+    return _lib.vdi_mlp_train_workspace(n)
+
+
+def vdi_mlp_grad(model_ptr, feats_ptr, labels_ptr, valid_ptr, n, grad_ptr, loss_ptr, ws_ptr, ws_bytes,
+                 stream=None) -> int:
+    return _lib.vdi_mlp_grad(C.c_void_p(model_ptr), C.c_void_p(feats_ptr), C.c_void_p(labels_ptr),
+                             C.c_void_p(valid_ptr), n, C.c_void_p(grad_ptr), C.c_void_p(loss_ptr), C.c_void_p(ws_ptr),
+                             ws_bytes, _stream(stream))
+
+
+def vdi_mlp_train_step(model_ptr, feats_ptr, labels_ptr, valid_ptr, n, lr, loss_ptr, ws_ptr, ws_bytes,
+                       stream=None) -> int:
+    return _lib.vdi_mlp_train_step(C.c_void_p(model_ptr), C.c_void_p(feats_ptr), C.c_void_p(labels_ptr),
+                                   C.c_void_p(valid_ptr), n, lr, C.c_void_p(loss_ptr), C.c_void_p(ws_ptr), ws_bytes,
+                                   _stream(stream))
+
+
+def vdi_learned_workspace(k, w, h) -> int:
+    return _lib.vdi_learned_workspace(k, w, h)
+
+
+def vdi_choose_gamma_learned(bricks, lut_ptr, cam: vdi_camera, n_s, model_ptr, offset, outs, params: vdi_params,
+                             ws_ptr, ws_bytes, stream=None) -> int:
+    oarr = (vdi_compact * len(outs))(*outs)
+    return _lib.vdi_choose_gamma_learned(_arr(bricks), len(outs), C.c_void_p(lut_ptr), _ref(cam), n_s,
+                                         C.c_void_p(model_ptr), offset, _arr(oarr), _ref(params), C.c_void_p(ws_ptr),
+                                         ws_bytes, _stream(stream))
 
 
 def vdi_render_view(vdi: vdi_regular, w, h, gen: vdi_camera, view, rgba_ptr, stream=None) -> int:

@@ -487,6 +487,143 @@ vdi_status vdi_composite_autotune(vdi_request* reqs, int32_t n, const vdi_params
     return s;
 }
 
+size_t vdi_model_bytes(void) { return model_bytes(); }
+int32_t vdi_model_nparams(void) { return model_nparams(); }
+
+vdi_status vdi_model_init(void* model, uint64_t seed, vdi_stream stream) {
+    if (!model) return set_error(VDI_ERR_INVALID_ARG, "vdi_model_init: NULL model");
+    return launch_model_init(model, seed, (cudaStream_t)stream);
+}
+
+vdi_status vdi_model_save(const void* model, const char* path, vdi_stream stream) {
+    if (!model || !path) return set_error(VDI_ERR_INVALID_ARG, "vdi_model_save: NULL argument");
+    return model_save(model, path, (cudaStream_t)stream);
+}
+
+vdi_status vdi_model_load(void* model, const char* path, vdi_stream stream) {
+    if (!model || !path) return set_error(VDI_ERR_INVALID_ARG, "vdi_model_load: NULL argument");
+    return model_load(model, path, (cudaStream_t)stream);
+}
+
+static vdi_status bricks_ok(const char* fn, const vdi_brick* bricks, int k) {
+    if (!bricks || k < 1 || k > VDI_MAX_PE) return set_error(VDI_ERR_INVALID_ARG, "%s: bricks / k", fn);
+    for (int e = 0; e < k; ++e) {
+        const vdi_brick& b = bricks[e];
+        if (!b.cells) return set_error(VDI_ERR_INVALID_ARG, "%s: brick %d has no cells", fn, e);
+        for (int a = 0; a < 3; ++a)
+            if (b.dims[a] != bricks[0].dims[a] || b.dims[a] < 2 || b.owned.lo[a] < 0 ||
+                b.owned.hi[a] > b.dims[a] - 1 || b.owned.hi[a] <= b.owned.lo[a])
+                return set_error(VDI_ERR_INVALID_ARG, "%s: brick %d box/dims", fn, e);
+    }
+    return VDI_OK;
+}
+
+vdi_status vdi_tile_features(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
+                             int32_t n_s, const vdi_params* params, float* feats, uint8_t* valid, vdi_stream stream) {
+    vdi_status s = bricks_ok("vdi_tile_features", bricks, k);
+    if (s != VDI_OK) return s;
+    if (!tf_lut || !camera_ok(cam) || !params_ok(params) || !feats || !valid || n_s < 1)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_tile_features: arguments");
+    BrickDev bd[VDI_MAX_PE];
+    for (int e = 0; e < k; ++e) bd[e] = brick_dev(bricks[e]);
+    CamDev cd = make_cam(*cam);
+    return launch_tile_features(bd, k, tf_lut, cd, bricks[0].dims, (float)(255.0 * (double)bricks[0].value_scale),
+                                params->step, params->ref_len, n_s, feats, valid, (cudaStream_t)stream);
+}
+
+vdi_status vdi_tile_labels(const vdi_compact* searched, int32_t k, int32_t w, int32_t h, float* labels,
+                           uint8_t* valid, vdi_stream stream) {
+    if (!searched || k < 1 || k > VDI_MAX_PE || w < 1 || h < 1 || !labels || !valid)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_tile_labels: arguments");
+    for (int e = 0; e < k; ++e)
+        if (!searched[e].counts || !searched[e].gamma)
+            return set_error(VDI_ERR_INVALID_ARG, "vdi_tile_labels: searched[%d] counts/gamma NULL", e);
+    return launch_tile_labels(searched, k, w, h, labels, valid, (cudaStream_t)stream);
+}
+
+vdi_status vdi_mlp_infer(const void* model, const float* feats, int32_t n, float offset, float* log2_gamma,
+                         vdi_stream stream) {
+    if (!model || n < 0 || (n > 0 && (!feats || !log2_gamma)))
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_mlp_infer: arguments");
+    return launch_mlp_infer(model, feats, n, offset, log2_gamma, (cudaStream_t)stream);
+}
+
+size_t vdi_mlp_train_workspace(int32_t n) { return n < 0 ? 0 : train_workspace(n); }
+
+vdi_status vdi_mlp_grad(const void* model, const float* feats, const float* labels, const uint8_t* valid, int32_t n,
+                        float* grad, float* loss, void* workspace, size_t ws_bytes, vdi_stream stream) {
+    if (!model || n < 1 || !feats || !labels || !valid || !grad)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_mlp_grad: arguments");
+    if (!workspace || ws_bytes < train_workspace(n)) return set_error(VDI_ERR_WORKSPACE, "vdi_mlp_grad: workspace");
+    return launch_mlp_grad(model, feats, labels, valid, n, grad, loss, workspace, (cudaStream_t)stream);
+}
+
+vdi_status vdi_mlp_train_step(void* model, const float* feats, const float* labels, const uint8_t* valid, int32_t n,
+                              float lr, float* loss, void* workspace, size_t ws_bytes, vdi_stream stream) {
+    if (!model || n < 1 || !feats || !labels || !valid || !(lr > 0.f))
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_mlp_train_step: arguments");
+    if (!workspace || ws_bytes < train_workspace(n))
+        return set_error(VDI_ERR_WORKSPACE, "vdi_mlp_train_step: workspace");
+    return launch_train_step(model, feats, labels, valid, n, lr, loss, workspace, (cudaStream_t)stream);
+}
+
+static size_t learned_extra(int k, int w, int h) {
+    size_t tiles = (size_t)((w + VDI_GAMMA_TILE - 1) / VDI_GAMMA_TILE) * ((h + VDI_GAMMA_TILE - 1) / VDI_GAMMA_TILE);
+    size_t n = (size_t)k * tiles;
+    return align_up(n * VDI_NFEAT * 4, 256) + align_up(n * 4, 256) + align_up(n, 256);
+}
+
+size_t vdi_learned_workspace(int32_t k, int32_t w, int32_t h) {
+    if (k < 1 || w < 1 || h < 1) return 0;
+    return learned_extra(k, w, h) + vdi_generate_workspace(k, w, h);
+}
+
+vdi_status vdi_choose_gamma_learned(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
+                                    int32_t n_s, const void* model, float offset, vdi_compact* out,
+                                    const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream) {
+    if (!model) return set_error(VDI_ERR_MODEL, "vdi_choose_gamma_learned: NULL model");
+    if (!cam || cam->width < 1 || cam->height < 1) return set_error(VDI_ERR_INVALID_ARG, "vdi_choose_gamma_learned: camera");
+    const size_t extra = learned_extra(k, cam->width, cam->height);
+    if (!workspace || ws_bytes < extra) return set_error(VDI_ERR_WORKSPACE, "vdi_choose_gamma_learned: workspace");
+    vdi_status s = gen_common("vdi_choose_gamma_learned", bricks, k, tf_lut, cam, n_s, VDI_GAMMA_GIVEN, out, params,
+                              static_cast<char*>(workspace) + extra, ws_bytes - extra, false);
+    if (s != VDI_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tiles = ((cam->width + VDI_GAMMA_TILE - 1) / VDI_GAMMA_TILE) *
+                      ((cam->height + VDI_GAMMA_TILE - 1) / VDI_GAMMA_TILE);
+    const size_t n = (size_t)k * tiles;
+    char* ws = static_cast<char*>(workspace);
+    float* feats = reinterpret_cast<float*>(ws);
+    float* pred = reinterpret_cast<float*>(ws + align_up(n * VDI_NFEAT * 4, 256));
+    unsigned char* valid = reinterpret_cast<unsigned char*>(ws + align_up(n * VDI_NFEAT * 4, 256) + align_up(n * 4, 256));
+    BrickDev bd[VDI_MAX_PE];
+    CompactDev od[VDI_MAX_PE];
+    float* gam[VDI_MAX_PE];
+    for (int e = 0; e < k; ++e) {
+        bd[e] = brick_dev(bricks[e]);
+        od[e] = CompactDev{out[e].counts, out[e].offsets, out[e].rgba, out[e].fb, out[e].gamma, out[e].capacity};
+        gam[e] = out[e].gamma;
+    }
+    CamDev cd = make_cam(*cam);
+    const float scale255 = (float)(255.0 * (double)bricks[0].value_scale);
+    s = launch_tile_features(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s, feats,
+                             valid, st);
+    if (s != VDI_OK) return s;
+    s = launch_mlp_infer(model, feats, (int)n, offset, pred, st);
+    if (s != VDI_OK) return s;
+    s = launch_gamma_expand(gam, k, cam->width, cam->height, pred, st);
+    if (s != VDI_OK) return s;
+    char* gws = ws + extra;
+    const size_t gbytes = ws_bytes - extra;
+    unsigned int* status = reinterpret_cast<unsigned int*>(gws);
+    s = cuda_check(cudaMemsetAsync(status, 0, kGenFixed, st), "status clear");
+    if (s != VDI_OK) return s;
+    const size_t fixed = gen_min_workspace(k, cam->width, cam->height);
+    return launch_gen_count(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s,
+                            kGammaLearnedBracket, params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0,
+                            reinterpret_cast<unsigned int*>(gws + kWsHeader), gws + fixed, gbytes - fixed, st);
+}
+
 vdi_status vdi_render_view(const vdi_regular* vdi, int32_t w, int32_t h, const vdi_camera* gen,
                            const vdi_camera* view, float* rgba_out, vdi_stream stream) {
     if (!vdi || !rgba_out || !vdi->counts || !vdi->rgba || vdi->n_s < 1)

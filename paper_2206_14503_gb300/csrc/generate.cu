@@ -41,7 +41,7 @@ struct GenArgs {
     const float* lut;  // 256 x 4, straight colour + opacity per ref_len
     float scale255, step, ref_len;
     int k, n_s, iters;
-    int mode;  // 0 fixed, 1 search, 2 given (+ fallback)
+    int mode;  // 0 fixed, 1 search, 2 given (+ fallback), 3 learned bracket (+ fallback)
     float gamma;
     int prec;
     int tiles_x, tiles_y;
@@ -221,6 +221,10 @@ __device__ __forceinline__ void cached_march(const CacheRef& c, int nt, const fl
     for (int q = 0; q < 3; ++q) cnt[q] = st[q].cnt;
 }
 
+__device__ __noinline__ void cached_march_call(const CacheRef& c, int nt, const float g2[3], int cnt[3], Census& cs) {
+    cached_march(c, nt, g2, cnt, cs);
+}
+
 // Bisection march over the volume: three candidates.
 __device__ __forceinline__ void volume_march(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
                                              float scale255, const float g2[3], int cnt[3], Census& cs) {
@@ -278,7 +282,118 @@ __device__ __forceinline__ float search(const Ray& r, int k0, int k1, const Bric
     return hi;
 }
 
-template <bool CENSUS>
+// Learned-gamma refinement over the cached samples.  The prediction gp (count
+// cp there) brackets the search: if gp is feasible (cp <= n_s) the bracket is
+// log2 gamma in [log2 gp - 4, log2 gp], else [log2 gp, log2 gp + 4] once its
+// top is found feasible; six levels of bisection in log2 gamma follow, two
+// per cached march.  Returns false when the bracket holds no feasible gamma
+// (the caller then runs the full search).  The result is the smallest
+// feasible gamma found, within a factor 2^(1/16) of the bracket's threshold.
+__device__ __forceinline__ bool bracket_refine(const CacheRef& c, int nt, float gp, int cp, int n_s, float& gamma,
+                                               int& count, Census& cs) {
+    constexpr float R = 4.f;
+    constexpr int kLevels = 6;
+    const float lg = log2f(fmaxf(gp, 0x1p-30f));
+    float lo, hi, ghi;
+    int cnt_hi, it = 0;
+    if (cp <= n_s) {
+        hi = lg;
+        ghi = gp;
+        cnt_hi = cp;
+        lo = lg - R;
+    } else {
+        // the bracket's top, its midpoint and left quarter in one march
+        const float x[3] = {lg + R, lg + 0.5f * R, lg + 0.25f * R};
+        float g[3], g2[3];
+        int cc[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            g[q] = exp2f(x[q]);
+            g2[q] = __fmul_rn(g[q], g[q]);
+        }
+        cached_march_call(c, nt, g2, cc, cs);
+        cs.cached += 1;
+        if (cc[0] > n_s) return false;
+        lo = lg;
+        hi = x[0];
+        ghi = g[0];
+        cnt_hi = cc[0];
+        ++it;
+        if (cc[1] <= n_s) {
+            hi = x[1];
+            ghi = g[1];
+            cnt_hi = cc[1];
+            if (cc[1] != n_s) {
+                ++it;
+                if (cc[2] <= n_s) {
+                    hi = x[2];
+                    ghi = g[2];
+                    cnt_hi = cc[2];
+                } else {
+                    lo = x[2];
+                }
+            } else {
+                it = kLevels;
+            }
+        } else {
+            lo = x[1];
+        }
+    }
+    while (it < kLevels && cnt_hi != n_s) {
+        const float mid = 0.5f * (lo + hi);
+        const float x[3] = {mid, 0.5f * (lo + mid), 0.5f * (mid + hi)};
+        float g[3], g2[3];
+        int cc[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            g[q] = exp2f(x[q]);
+            g2[q] = __fmul_rn(g[q], g[q]);
+        }
+        cached_march_call(c, nt, g2, cc, cs);
+        cs.cached += 1;
+        ++it;
+        int child;
+        if (cc[0] <= n_s) {
+            hi = mid;
+            ghi = g[0];
+            cnt_hi = cc[0];
+            if (cc[0] == n_s) break;
+            child = 1;
+        } else {
+            lo = mid;
+            child = 2;
+        }
+        if (it >= kLevels) break;
+        ++it;
+        if (cc[child] <= n_s) {
+            hi = x[child];
+            ghi = g[child];
+            cnt_hi = cc[child];
+        } else {
+            lo = x[child];
+        }
+    }
+    gamma = ghi;
+    count = cnt_hi;
+    return true;
+}
+
+// Out-of-line copies for the learned instantiation, whose extra refinement
+// path would otherwise spill.
+__device__ __noinline__ bool bracket_refine_call(const CacheRef& c, int nt, float gp, int cp, int n_s, float& gamma,
+                                                    int& count, Census& cs) {
+    return bracket_refine(c, nt, gp, cp, n_s, gamma, count, cs);
+}
+
+__device__ __noinline__ float search_call(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
+                                             float scale255, int n_s, int iters, int nt, const CacheRef* c,
+                                             int& count, Census& cs) {
+    return search(r, k0, k1, b, lut2, scale255, n_s, iters, nt, c, count, cs);
+}
+
+// The learned-gamma refinement (mode 3) is compiled only into the LEARNED
+// instantiation so that the search kernel keeps its register budget.
+template <bool CENSUS, bool LEARNED>
 __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     __shared__ unsigned int s_item;
@@ -293,6 +408,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
     cref.cap = a.cache_cap;
     Census cs;
     unsigned long long rays = 0;
+    const int mode = LEARNED ? 3 : a.mode;
     while (true) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
         __syncthreads();
@@ -309,31 +425,39 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
         Ray r;
         int k0 = 0, k1 = 0;
         const bool any = ray_setup(a.cam, i, j, a.dims, a.step, r) && owned_range(r, a.step, b, a.dims, k0, k1);
-        float gamma = a.mode == 0 ? a.gamma : (a.mode == 2 ? fmaxf(o.gamma[p], 0.f) : 0.f);
+        float gamma = mode == 0 ? a.gamma : (mode >= 2 ? fmaxf(o.gamma[p], 0.f) : 0.f);
         int count = 0;
         if (any) {
             rays += 1;
-            if (a.mode == 0) {
+            if (mode == 0) {
                 const float g2[1] = {__fmul_rn(a.gamma, a.gamma)};
                 int c[1];
                 first_march<1>(r, k0, k1, b, lut2, a.scale255, g2, a.n_s, nullptr, c, cs);
                 count = c[0];
             } else {
-                bool need_search = true;
-                if (a.mode == 2) {
+                const bool use_cache = a.cache_a != nullptr;
+                int nt;
+                bool searched = true;
+                if (mode >= 2) {
+                    // one march: count at the given gamma, non-transparent count, cache
                     const float g2[1] = {__fmul_rn(gamma, gamma)};
                     int c[1];
-                    first_march<1>(r, k0, k1, b, lut2, a.scale255, g2, INT_MAX, nullptr, c, cs);
-                    if (c[0] <= a.n_s) {
-                        count = c[0];
-                        need_search = false;
+                    nt = first_march<1>(r, k0, k1, b, lut2, a.scale255, g2, INT_MAX, use_cache ? &cref : nullptr, c,
+                                        cs);
+                    if (mode == 2) {
+                        if (c[0] <= a.n_s) {
+                            count = c[0];
+                            searched = false;
+                        }
+                    } else if (LEARNED && nt > a.n_s && use_cache && nt <= a.cache_cap) {
+                        searched = !bracket_refine_call(cref, nt, gamma, c[0], a.n_s, gamma, count, cs);
                     }
-                }
-                if (need_search) {
-                    const bool use_cache = a.cache_a != nullptr;
+                } else {
                     int dummy[1];
-                    const int nt = first_march<0>(r, k0, k1, b, lut2, a.scale255, nullptr, INT_MAX,
-                                                  use_cache ? &cref : nullptr, dummy, cs);
+                    nt = first_march<0>(r, k0, k1, b, lut2, a.scale255, nullptr, INT_MAX, use_cache ? &cref : nullptr,
+                                        dummy, cs);
+                }
+                if (searched) {
                     if (nt <= a.n_s) {
                         gamma = 0.f;
                         count = nt;
@@ -341,7 +465,8 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
                         const CacheRef* c = (use_cache && nt <= a.cache_cap) ? &cref : nullptr;
                         cs.searched += 1;
                         cs.overflow += c ? 0 : 1;
-                        gamma = search(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count, cs);
+                        gamma = LEARNED ? search_call(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count, cs)
+                                        : search(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count, cs);
                     }
                 }
             }
@@ -472,13 +597,14 @@ vdi_status gen_count_grid(int& ctas) {
     if (s != VDI_OK) return s;
     s = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     if (s != VDI_OK) return s;
-    s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gen_count_kernel<false>, kGenThreads, 0),
-                   "occupancy");
-    if (s != VDI_OK) return s;
-    s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, gen_count_kernel<true>, kGenThreads, 0),
-                   "occupancy");
-    if (s != VDI_OK) return s;
-    if (per_sm_c > per_sm) per_sm = per_sm_c;
+    void (*const kernels[4])(GenArgs) = {gen_count_kernel<false, false>, gen_count_kernel<true, false>,
+                                         gen_count_kernel<false, true>, gen_count_kernel<true, true>};
+    for (int q = 0; q < 4; ++q) {
+        s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, kernels[q], kGenThreads, 0),
+                       "occupancy");
+        if (s != VDI_OK) return s;
+        if (per_sm_c > per_sm) per_sm = per_sm_c;
+    }
     ctas = sms * (per_sm > 0 ? per_sm : 1);
     return VDI_OK;
 }
@@ -495,7 +621,7 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
     fill_args(a, bricks, k, lut, cam, dims, scale255, step, ref_len, n_s, out, status);
     a.iters = iters;
     a.gamma = gamma;
-    a.mode = gamma >= 0.f ? 0 : (gamma == VDI_GAMMA_GIVEN ? 2 : 1);
+    a.mode = gamma >= 0.f ? 0 : (gamma == VDI_GAMMA_GIVEN ? 2 : (gamma == kGammaLearnedBracket ? 3 : 1));
     a.prec = 0;
     a.counter = counter;
     int ctas = 0;
@@ -511,8 +637,11 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
                                               (size_t)a.slots * kCacheCap * sizeof(float4));
     }
     if ((unsigned)ctas > items) ctas = (int)items;
-    if (census) gen_count_kernel<true><<<ctas, kGenThreads, 0, st>>>(a);
-    else gen_count_kernel<false><<<ctas, kGenThreads, 0, st>>>(a);
+    const bool learned = a.mode == 3;
+    if (census && learned) gen_count_kernel<true, true><<<ctas, kGenThreads, 0, st>>>(a);
+    else if (census) gen_count_kernel<true, false><<<ctas, kGenThreads, 0, st>>>(a);
+    else if (learned) gen_count_kernel<false, true><<<ctas, kGenThreads, 0, st>>>(a);
+    else gen_count_kernel<false, false><<<ctas, kGenThreads, 0, st>>>(a);
     return cuda_check(cudaGetLastError(), "gen_count_kernel launch");
 }
 

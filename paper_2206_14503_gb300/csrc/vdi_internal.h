@@ -65,6 +65,9 @@ size_t gen_cache_bytes(int ctas);
 // generation workspace: [0, 256) header, [256, 512) work counter, then the
 // prefix sum's partial sums, then (optionally) the sample cache
 constexpr size_t kGenFixed = 512;
+// internal gamma mode of launch_gen_count: per-ray predicted gamma in out.gamma,
+// refined by a short bracketed search over the sample cache (learned path)
+constexpr float kGammaLearnedBracket = -5.0f;
 vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                            float scale255, float step, float ref_len, int n_s, int prec, const CompactDev* out,
                            unsigned int* status, cudaStream_t st);
@@ -79,5 +82,24 @@ vdi_status batch_table_pack(const vdi_request* reqs, int n, void* host_table, si
 vdi_status launch_composite_batched(const void* dev_table, const void* host_table, int iters, unsigned int* counter,
                                     unsigned int* status, int device_sms, cudaStream_t st);
 vdi_status launch_flatten(const vdi_regular* v, int w, int h, float* rgba, cudaStream_t st);
+
+// learned gamma (learned.cu)
+size_t model_bytes();
+int model_nparams();
+vdi_status launch_model_init(void* model, unsigned long long seed, cudaStream_t st);
+vdi_status launch_tile_features(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
+                                float scale255, float step, float ref_len, int n_s, float* feats,
+                                unsigned char* valid, cudaStream_t st);
+vdi_status launch_tile_labels(const vdi_compact* searched, int k, int w, int h, float* labels, unsigned char* valid,
+                              cudaStream_t st);
+vdi_status launch_mlp_infer(const void* model, const float* feats, int n, float offset, float* out, cudaStream_t st);
+vdi_status launch_gamma_expand(float* const* gammas, int k, int w, int h, const float* pred, cudaStream_t st);
+size_t train_workspace(int n);
+vdi_status launch_mlp_grad(const void* model, const float* x, const float* y, const unsigned char* valid, int n,
+                           float* grad, float* loss, void* ws, cudaStream_t st);
+vdi_status launch_train_step(void* model, const float* x, const float* y, const unsigned char* valid, int n, float lr,
+                             float* loss, void* ws, cudaStream_t st);
+vdi_status model_save(const void* model, const char* path, cudaStream_t st);
+vdi_status model_load(void* model, const char* path, cudaStream_t st);
 
 }  // namespace vdi
