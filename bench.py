@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-scale", action="store_true", help="skip the 2048^2 K=32 dense compositing runs")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-request batched compositing run")
     return ap.parse_args()
 
 
@@ -234,6 +236,128 @@ def learned_eval(vdi, torch, stream, views=3, warmup=1):
             "mrays_s_search": npix / ms_s / 1e3, "mrays_s_learned": npix / ms_l / 1e3}
 
 
+def _comp_census(vdi, counters):
+    pix = max(counters[0], 1)
+    return {"sweeps_per_pixel": counters[2] / pix, "pieces_per_sweep": counters[3] / max(counters[2], 1),
+            "searched_frac": counters[1] / pix, "cand_steps_per_pixel": counters[4] / pix,
+            "records_in_per_pixel": counters[5] / pix, "table_hits_per_searched_pixel": counters[6] / max(counters[1], 1)}
+
+
+def scale_eval(vdi, torch, stream, hbm_peak, warmup=1, steps=3):
+    """Compositing only, 2048 x 2048, K = 32, N_S = 32, dense lists: FP32 records, then FP16 colour storage."""
+    from synth import gpu_lists
+
+    W = H = 2048
+    K, NS = 32, 32
+    npix = W * H
+    torch.cuda.empty_cache()
+    if torch.cuda.mem_get_info()[0] < 125e9:
+        return {"skipped": "needs 125 GB of free device memory"}
+    seed = 0x5CA1E
+    pes = []
+    for e in range(K):
+        c, o, fb, rgba = gpu_lists.dense_set(seed, 0, e, npix, NS)
+        pes.append(vdi.Compact.from_tensors(c, o, rgba, fb, vdi.VDI_PREC_F32))
+    ws = vdi.Workspace(vdi.vdi_composite_workspace(K, W, H, NS))
+    res = {"workload": "2048x2048, K=32, N_S=32, dense lists (32 records per PE and pixel), compositing only"}
+    for prec in (vdi.VDI_PREC_F32, vdi.VDI_PREC_F16):
+        if prec == vdi.VDI_PREC_F16:
+            for e in range(K):
+                rec = gpu_lists.pack_f16(pes[e].fb, pes[e].rgba)
+                pes[e] = vdi.Compact.from_tensors(pes[e].counts, pes[e].offsets, rec, None, prec)
+            torch.cuda.empty_cache()
+        out = vdi.Regular(npix, NS, prec)
+        structs = [p.struct() for p in pes]
+        params = vdi.make_params()
+        for _ in range(warmup):
+            vdi.check(vdi.vdi_composite(structs, W, H, out.struct(), params, ws.ptr, ws.nbytes, stream), "scale")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            vdi.check(vdi.vdi_composite(structs, W, H, out.struct(), params, ws.ptr, ws.nbytes, stream), "scale")
+        e1.record(stream)
+        stream.synchronize()
+        vdi.check(ws.status(stream), "scale status")
+        ms = e0.elapsed_time(e1) / steps
+        rec = 24 if prec == vdi.VDI_PREC_F32 else 16
+        nbytes = npix * (12 * K + rec * NS + 8) + rec * npix * K * NS
+        vdi.check(vdi.vdi_composite(structs, W, H, out.struct(), vdi.make_params(flags=vdi.VDI_FLAG_CENSUS),
+                                    ws.ptr, ws.nbytes, stream), "scale census")
+        cen = _comp_census(vdi, vdi.vdi_workspace_counters(ws.ptr, stream))
+        name = "fp32" if prec == vdi.VDI_PREC_F32 else "fp16"
+        res[name] = {"ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak,
+                     "bytes": nbytes, "mpix_s": npix / (ms * 1e-3) / 1e6, "census": cen}
+        del out
+    del pes
+    torch.cuda.empty_cache()
+    return res
+
+
+def batched_eval(vdi, torch, stream, hbm_peak, warmup=1, steps=3, runs=1 << 22):
+    """64 requests of the seeded request table in one persistent launch, captured in a CUDA graph."""
+    import synth
+    from synth import gpu_lists
+
+    table = synth.requests(64)
+    torch.cuda.empty_cache()
+    need = 12e9 + sum(w * h * (k * 12 + n_s * 24 + 8) for w, h, k, n_s in table)
+    if torch.cuda.mem_get_info()[0] < need + 20e9:
+        return {"skipped": f"needs {(need + 20e9) / 1e9:.0f} GB of free device memory"}
+    pool_fb, pool_rgba = gpu_lists.pool(synth.SEED_REQUESTS, runs)
+    keep, items = [], []
+    n_rec = 0
+    nbytes = 0
+    for r, (w, h, k, n_s) in enumerate(table):
+        pix = torch.arange(w * h, dtype=torch.int64, device="cuda")
+        pes = []
+        for e in range(k):
+            n, first = gpu_lists.pool_picks(synth.SEED_REQUESTS, r, e, pix, n_s, runs)
+            n_rec += int(n.sum().item())
+            pes.append(vdi.Compact.from_tensors(n, first, pool_rgba, pool_fb, vdi.VDI_PREC_F32))
+        out = vdi.Regular(w * h, n_s)
+        keep.append((pes, out))
+        items.append(([p.struct() for p in pes], w, h, out.struct(), 0))
+        nbytes += w * h * (12 * k + 24 * n_s + 8)
+    nbytes += 24 * n_rec
+    R = vdi.Requests(items)
+    tws = vdi.Workspace(vdi.vdi_composite_workspace(64, 1 << 20, 1, 64))
+    t0 = time.time()
+    vdi.check(vdi.vdi_composite_autotune(R, vdi.make_params(), tws.ptr, tws.nbytes, stream), "autotune")
+    tune_s = time.time() - t0
+    host = vdi.vdi_batch_table_pack(R)
+    dev_t = torch.frombuffer(bytearray(host), dtype=torch.uint8).cuda()
+    ws = vdi.Workspace(vdi.vdi_composite_batched_workspace(host))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            vdi.check(vdi.vdi_composite_batched(dev_t.data_ptr(), host, vdi.make_params(), ws.ptr, ws.nbytes,
+                                                stream), "batched capture")
+        for _ in range(warmup):
+            g.replay()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            g.replay()
+        e1.record(stream)
+    stream.synchronize()
+    vdi.check(ws.status(stream), "batched status")
+    ms = e0.elapsed_time(e1) / steps
+    npix = sum(w * h for w, h, _, _ in table)
+    scheds = [R.arr[i].schedule for i in range(len(R))]
+    res = {"workload": "64 requests: W~U{256..1920}, H~U{256..1080}, K~U{2..32}, N_S~U{8..64}, lengths~U{0..N_S}, "
+                       "lists = windows into a pool of 4.19 M sorted 64-record runs (6.4 GB, reuse distance >> L2)",
+           "ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak,
+           "bytes": nbytes, "pixels": npix, "records_in": n_rec, "mpix_s": npix / (ms * 1e-3) / 1e6,
+           "autotune_s": tune_s, "schedules": {str(s): scheds.count(s) for s in sorted(set(scheds))}}
+    del keep, pool_fb, pool_rgba, g
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -279,6 +403,9 @@ def main():
     wl = Workload(args.dims, args.width, args.height)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
+    # every torch operation (allocation, zeroing, input generation) runs on the
+    # stream the library's calls are issued on, so that all work is ordered
+    torch.cuda.set_stream(stream)
     W, H, n_s = wl.W, wl.H, wl.n_s
     npix = W * H
     boxes = vdi.vdi_split_boxes(wl.dims, wl.grid)
@@ -316,12 +443,32 @@ def main():
                                    params, wsg.ptr, wsg.nbytes, stream), "generate")
         if ev:
             ev[3].record(stream)
-        vdi.check(vdi.vdi_composite(ostructs, W, H, rstruct, params, wsc.ptr, wsc.nbytes, stream), "composite")
+        vdi.check(vdi.vdi_composite(ostructs, W, H, rstruct, params_c, wsc.ptr, wsc.nbytes, stream), "composite")
         if ev:
             ev[4].record(stream)
         vdi.check(vdi.vdi_render_view(rstruct, W, H, cam, None, img.data_ptr(), stream), "render")
         if ev:
             ev[5].record(stream)
+
+    # the compositing schedule: autotuned on the first view's sub-VDIs (outside the timed region)
+    params_c = params
+    frame(0)
+    req = vdi.Requests([(ostructs, W, H, rstruct, 0)])
+    vdi.check(vdi.vdi_composite_autotune(req, params, wsc.ptr, wsc.nbytes, stream), "autotune")
+    comp_schedule = int(req.arr[0].schedule)
+    params_c = vdi.make_params(step=wl.step, ref_len=wl.ref_len, schedule=comp_schedule)
+    sched_ms = {}
+    for sched in (1, 2, 3, vdi.VDI_SCHED_STAGED):
+        p_s = vdi.make_params(step=wl.step, ref_len=wl.ref_len, schedule=sched)
+        ea = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event(enable_timing=True)
+        vdi.check(vdi.vdi_composite(ostructs, W, H, rstruct, p_s, wsc.ptr, wsc.nbytes, stream), "schedule sweep")
+        ea.record(stream)
+        for _ in range(3):
+            vdi.check(vdi.vdi_composite(ostructs, W, H, rstruct, p_s, wsc.ptr, wsc.nbytes, stream), "schedule sweep")
+        eb.record(stream)
+        stream.synchronize()
+        sched_ms[str(sched)] = round(ea.elapsed_time(eb) / 3, 3)
 
     # warm-up (also checks capacity and device status)
     for i in range(args.warmup):
@@ -364,6 +511,7 @@ def main():
     cen_params = vdi.make_params(step=wl.step, ref_len=wl.ref_len, flags=vdi.VDI_FLAG_CENSUS)
     evals = steps_sm = passes = pe_rays = searched = overflow = cached = remarched = 0
     comp_bytes = []
+    comp_ctr = None
     for s in range(args.steps):
         view = (args.warmup + s * world + rank) % 16
         vdi.check(vdi.vdi_choose_gamma(bricks.bricks, lut_d.data_ptr(), cams[view], n_s, vdi.VDI_GAMMA_SEARCH,
@@ -379,6 +527,10 @@ def main():
         remarched += c[7]
         vdi.check(vdi.vdi_generate(bricks.bricks, lut_d.data_ptr(), cams[view], n_s, vdi.VDI_GAMMA_CHOSEN, ostructs,
                                    params, wsg.ptr, wsg.nbytes, stream), "generate")
+        cen_c = vdi.make_params(step=wl.step, ref_len=wl.ref_len, schedule=comp_schedule, flags=vdi.VDI_FLAG_CENSUS)
+        vdi.check(vdi.vdi_composite(ostructs, W, H, rstruct, cen_c, wsc.ptr, wsc.nbytes, stream), "census")
+        cc = vdi.vdi_workspace_counters(wsc.ptr, stream)
+        comp_ctr = cc if comp_ctr is None else [a + b for a, b in zip(comp_ctr, cc)]
         stream.synchronize()
         n_records = sum(int(o.offsets[-1].item()) for o in outs)
         # composite algorithmic bytes: per PE and pixel count + offset (12 B), input records (24 B),
@@ -444,6 +596,15 @@ def main():
     learned = None
     if not args.no_learned and rank == 0:
         learned = learned_eval(vdi, torch, stream)
+    scale = batched = None
+    if rank == 0 and not (args.no_scale and args.no_batched):
+        # free the frame's buffers first
+        del outs, reg, img, bricks, vol_d, wsg, wsc, ostructs
+        torch.cuda.empty_cache()
+        if not args.no_scale:
+            scale = scale_eval(vdi, torch, stream, hbm_peak)
+        if not args.no_batched:
+            batched = batched_eval(vdi, torch, stream, hbm_peak)
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -460,7 +621,10 @@ def main():
                 "stages_ms": {kk: round(v, 3) for kk, v in mean.items()},
                 "composite": {"gbs": comp_gbs, "frac_hbm": comp_gbs / hbm_peak, "peak_gbs": hbm_peak,
                               "peak_source": hbm_src, "records_in_per_frame": int(statistics.mean(n_in)),
-                              "bytes_per_frame": int(statistics.mean(comp_bytes))},
+                              "bytes_per_frame": int(statistics.mean(comp_bytes)),
+                              "census": _comp_census(vdi, comp_ctr), "schedule": comp_schedule,
+                              "schedule_ms": sched_ms},
+                "composite_scale": scale, "composite_batched": batched,
                 "gen": {"mrays_s": npix / (mean["choose_gamma"] + mean["scan+emit"] + mean["brick"]) / 1e3,
                         "sample_evals_per_frame": evals // args.steps,
                         "sm_steps_per_frame": steps_sm // args.steps, "tops": gen_tops,

@@ -97,7 +97,7 @@ typedef struct {
 } vdi_params;
 
 #define VDI_FLAG_SYNC_CAPACITY 1 /* vdi_generate: read totals back and return VDI_ERR_CAPACITY before emitting */
-#define VDI_FLAG_CENSUS 2        /* vdi_choose_gamma / vdi_generate: count the work done (vdi_workspace_counters) */
+#define VDI_FLAG_CENSUS 2        /* vdi_choose_gamma / vdi_generate / vdi_composite: count the work done (vdi_workspace_counters) */
 
 /* A sampling brick: one PE's cells in the library's cell-packed layout, built
  * by vdi_brick_build().  Opaque to the caller apart from its size. */
@@ -155,6 +155,12 @@ vdi_status vdi_workspace_status(const void* workspace, vdi_stream stream);
  *   [4] pairs that needed the bisection search, [5] of those, pairs whose
  *   non-transparent samples did not fit the sample cache, [6] marches over
  *   cached samples, [7] marches re-sampling the volume for the search.
+ * After vdi_composite with the flag the counters are instead:
+ *   [0] pixels, [1] pixels that needed the search, [2] sweeps over a
+ *   pixel's pieces (search marches plus the emitting sweep), [3] pieces
+ *   visited over those sweeps, [4] state-machine steps (pieces x gamma
+ *   candidates), [5] input records, [6] bisection levels answered by the
+ *   decision intervals of earlier marches, [7] unused.
  * The census runs a separately compiled variant of the kernel; without the
  * flag nothing is counted. */
 vdi_status vdi_workspace_counters(const void* workspace, uint64_t counters[8], vdi_stream stream);
@@ -253,10 +259,26 @@ vdi_status vdi_generate_static_scratch(const vdi_brick* bricks, int32_t k, const
  * mixture, an uncovered interval between records is a transparent sample.
  * The pieces are re-segmented with Eq. 1 and a per-pixel gamma search, and
  * at most n_s supersegments are written front to back with a zero tail.
- * params->schedule: 0 automatic (1 if k <= 8, else 2); 1: list heads in
- * registers (k <= 8), two bisection levels per march over the pieces; 2:
- * list heads in local memory (k <= 64), two levels per march; 3: heads in
- * local memory, three levels per march.  All give the same result. */
+ * params->schedule (all give the same result, bit for bit):
+ *   0 automatic (VDI_SCHED_STAGED);
+ *   VDI_SCHED_STAGED (4): a warp builds the pieces of 32 pixels, one pixel at
+ *     a time with all its lanes (coalesced loads of the K lists, a stable
+ *     merge of their bounds, an exact prefix scan of the records' terms) into
+ *     a piece buffer in the workspace; then each lane runs the search and the
+ *     emission of one pixel over its buffered pieces.  Pixels with more than
+ *     1024 records, or more pieces than the buffer's rows, take schedule 2 in
+ *     a second launch;
+ *   1, 2, 3 (direct): each thread sweeps its pixel's K lists on every march;
+ *     1: list heads in registers (k <= 8), two bisection levels per march;
+ *     2: heads in shared memory under a winner tree, two levels per march;
+ *     3: as 2 with three levels per march.
+ * Workspace: vdi_composite_workspace bytes give the staged path its full
+ * piece buffer (2048 rows per column); a smaller workspace gives fewer rows
+ * (at least 256 bytes plus one row are needed for the staged path; the direct
+ * schedules need 256 bytes).  Colours must be non-negative (premultiplied,
+ * at most A); a record's extinction -log2(1 - A) / (b - f) is clamped at
+ * 2^56 per unit depth. */
+#define VDI_SCHED_STAGED 4
 size_t vdi_composite_workspace(int32_t k, int32_t w, int32_t h, int32_t n_s);
 vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h, vdi_regular* out,
                          const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream);
@@ -280,19 +302,27 @@ size_t vdi_batch_table_bytes(const vdi_request* reqs, int32_t n);
  * passed to vdi_composite_batched.  All requests must share one input
  * precision. */
 vdi_status vdi_batch_table_pack(const vdi_request* reqs, int32_t n, void* host_table, size_t bytes);
-size_t vdi_composite_batched_workspace(int32_t n);
-/* Composites every request of the table in one persistent kernel: CTAs take
- * (request, 128-pixel tile) items from an atomic counter in the workspace
- * (reset by this call with a stream-ordered memset) until none is left.  The
- * memset and the launch may be captured into a CUDA graph and replayed; the
- * outputs equal those of one vdi_composite call per request, bit for bit. */
+/* Workspace bytes for a packed table (host_table from vdi_batch_table_pack). */
+size_t vdi_composite_batched_workspace(const void* host_table);
+/* Composites every request of the table in one persistent kernel: warps take
+ * (request, 32-pixel batch) items from an atomic counter in the workspace
+ * (reset by this call with a stream-ordered memset) until none is left and
+ * run the staged schedule on them; requests with a direct schedule (1-3, run
+ * as 2) and the pixels the stage cannot hold follow in a second launch over
+ * the list the first one left in the workspace.  The memset and the launches
+ * may be captured into a CUDA graph and replayed; the outputs equal those of
+ * one vdi_composite call per request, bit for bit. */
 vdi_status vdi_composite_batched(const void* dev_table, const void* host_table, const vdi_params* params,
                                  void* workspace, size_t ws_bytes, vdi_stream stream);
 /* Autotuner: for each request whose schedule is 0, times the applicable
- * schedules on (a prefix of) that request with CUDA events and stores the
- * fastest in reqs[i].schedule.  Results are cached per (K bucket, N_S bucket)
- * for the life of the process, so later requests of the same shape reuse
- * them.  Synchronises the stream; overwrites the requests' outputs. */
+ * schedules (1 when k <= 8, 2, 3, and VDI_SCHED_STAGED when the workspace
+ * holds vdi_composite_workspace(k, m, 1, n_s) bytes, m = min(w h, 2^20)) on
+ * the first m of the request's pixels with CUDA events and stores the
+ * fastest in
+ * reqs[i].schedule.  Results are cached per (K bucket, N_S bucket, input
+ * precision) for the life of the process, so later requests of the same
+ * shape reuse them.  Synchronises the stream; overwrites the requests'
+ * outputs. */
 vdi_status vdi_composite_autotune(vdi_request* reqs, int32_t n, const vdi_params* params, void* workspace,
                                   size_t ws_bytes, vdi_stream stream);
 

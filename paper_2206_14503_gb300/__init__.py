@@ -33,6 +33,7 @@ VDI_GAMMA_GIVEN = -2.0
 VDI_GAMMA_CHOSEN = -3.0
 VDI_FLAG_SYNC_CAPACITY = 1
 VDI_FLAG_CENSUS = 2
+VDI_SCHED_STAGED = 4
 
 
 class VdiError(RuntimeError):
@@ -97,7 +98,7 @@ def _load():
         "vdi_render_view": ([vp, i32, i32, vp, vp, vp, vp], i32),
         "vdi_batch_table_bytes": ([vp, i32], sz),
         "vdi_batch_table_pack": ([vp, i32, vp, sz], i32),
-        "vdi_composite_batched_workspace": ([i32], sz),
+        "vdi_composite_batched_workspace": ([vp], sz),
         "vdi_composite_batched": ([vp, vp, vp, vp, sz, vp], i32),
         "vdi_composite_autotune": ([vp, i32, vp, vp, sz, vp], i32),
         "vdi_model_bytes": ([], sz),
@@ -284,8 +285,9 @@ def vdi_batch_table_pack(reqs: Requests):
     return buf
 
 
-def vdi_composite_batched_workspace(n: int) -> int:
-    return _lib.vdi_composite_batched_workspace(n)
+def vdi_composite_batched_workspace(host_table) -> int:
+    """Workspace bytes for a table packed by vdi_batch_table_pack."""
+    return _lib.vdi_composite_batched_workspace(_arr(host_table))
 
 
 def vdi_composite_batched(dev_table_ptr: int, host_table, params: vdi_params, ws_ptr, ws_bytes, stream=None) -> int:

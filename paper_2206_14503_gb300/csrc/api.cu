@@ -330,8 +330,9 @@ vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut,
 }
 
 size_t vdi_composite_workspace(int32_t k, int32_t w, int32_t h, int32_t n_s) {
-    (void)k; (void)w; (void)h; (void)n_s;
-    return kWsHeader;
+    (void)k; (void)n_s;
+    if (w < 0 || h < 0) return 0;
+    return composite_workspace_bytes(w, h);
 }
 
 vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h, vdi_regular* out,
@@ -343,7 +344,7 @@ vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h,
     if (out->n_s < 1) return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: n_s = %d", out->n_s);
     if (params->bisect_iters < 1 || params->bisect_iters > 24)
         return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: bisect_iters");
-    if (params->schedule < 0 || params->schedule > 3)
+    if (params->schedule < 0 || params->schedule > VDI_SCHED_STAGED)
         return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: schedule %d", params->schedule);
     for (int e = 0; e < k; ++e) {
         if (!pe[e].counts || !pe[e].offsets || !pe[e].rgba)
@@ -359,13 +360,19 @@ vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h,
         return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: output array NULL");
     if (out->prec != VDI_PREC_F32 && out->prec != VDI_PREC_F16)
         return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: out->prec");
-    if (!workspace || ws_bytes < vdi_composite_workspace(k, w, h, out->n_s))
-        return set_error(VDI_ERR_WORKSPACE, "vdi_composite: workspace too small");
+    if (!workspace || ws_bytes < kWsHeader) return set_error(VDI_ERR_WORKSPACE, "vdi_composite: workspace too small");
     cudaStream_t st = (cudaStream_t)stream;
     unsigned int* status = reinterpret_cast<unsigned int*>(workspace);
-    vdi_status s = cuda_check(cudaMemsetAsync(status, 0, sizeof(unsigned int), st), "status clear");
+    const bool census = (params->flags & VDI_FLAG_CENSUS) != 0;
+    vdi_status s = cuda_check(cudaMemsetAsync(status, 0, census ? kWsHeader : sizeof(unsigned int), st),
+                              "status clear");
     if (s != VDI_OK) return s;
-    return launch_composite(pe, k, w, h, out, params->bisect_iters, params->schedule, status, st);
+    s = launch_composite(pe, k, w, h, out, params->bisect_iters, params->schedule, status, workspace, ws_bytes, st,
+                         census);
+    if (s == VDI_ERR_CUDA && (params->schedule == 0 || params->schedule == VDI_SCHED_STAGED) &&
+        ws_bytes < composite_workspace_bytes(1, 1))
+        return set_error(VDI_ERR_WORKSPACE, "vdi_composite: workspace too small for the staged schedule");
+    return s;
 }
 
 size_t vdi_batch_table_bytes(const vdi_request* reqs, int32_t n) {
@@ -379,7 +386,8 @@ static vdi_status check_request(const vdi_request& q, int idx, int prec0) {
         return set_error(VDI_ERR_INVALID_ARG, "request %d: image %d x %d", idx, q.w, q.h);
     if (q.out.n_s < 1 || !q.out.counts || !q.out.rgba || (q.out.prec == VDI_PREC_F32 && !q.out.fb))
         return set_error(VDI_ERR_INVALID_ARG, "request %d: output", idx);
-    if (q.schedule < 0 || q.schedule > 3) return set_error(VDI_ERR_INVALID_ARG, "request %d: schedule", idx);
+    if (q.schedule < 0 || q.schedule > VDI_SCHED_STAGED)
+        return set_error(VDI_ERR_INVALID_ARG, "request %d: schedule", idx);
     for (int e = 0; e < q.k; ++e) {
         const vdi_compact& c = q.pe[e];
         if (!c.counts || !c.offsets || !c.rgba || (c.prec == VDI_PREC_F32 && !c.fb))
@@ -401,9 +409,9 @@ vdi_status vdi_batch_table_pack(const vdi_request* reqs, int32_t n, void* host_t
     return batch_table_pack(reqs, n, host_table, bytes);
 }
 
-size_t vdi_composite_batched_workspace(int32_t n) {
-    (void)n;
-    return kWsHeader + 256;
+size_t vdi_composite_batched_workspace(const void* host_table) {
+    if (!host_table) return 0;
+    return batched_workspace_bytes(host_table);
 }
 
 vdi_status vdi_composite_batched(const void* dev_table, const void* host_table, const vdi_params* params,
@@ -412,19 +420,13 @@ vdi_status vdi_composite_batched(const void* dev_table, const void* host_table, 
         return set_error(VDI_ERR_INVALID_ARG, "vdi_composite_batched: NULL argument");
     if (params->bisect_iters < 1 || params->bisect_iters > 24)
         return set_error(VDI_ERR_INVALID_ARG, "vdi_composite_batched: bisect_iters");
-    if (!workspace || ws_bytes < vdi_composite_batched_workspace(0))
+    if (!workspace || ws_bytes < batched_workspace_bytes(host_table))
         return set_error(VDI_ERR_WORKSPACE, "vdi_composite_batched: workspace too small");
     cudaStream_t st = (cudaStream_t)stream;
     unsigned int* status = reinterpret_cast<unsigned int*>(workspace);
-    unsigned int* counter = reinterpret_cast<unsigned int*>(static_cast<char*>(workspace) + kWsHeader);
-    vdi_status s = cuda_check(cudaMemsetAsync(workspace, 0, kWsHeader + 256, st), "batched: clear");
+    vdi_status s = cuda_check(cudaMemsetAsync(workspace, 0, kWsHeader, st), "batched: clear");
     if (s != VDI_OK) return s;
-    int dev = 0, sms = 0;
-    s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
-    if (s != VDI_OK) return s;
-    s = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    if (s != VDI_OK) return s;
-    return launch_composite_batched(dev_table, host_table, params->bisect_iters, counter, status, sms, st);
+    return launch_composite_batched(dev_table, host_table, params->bisect_iters, status, workspace, ws_bytes, st);
 }
 
 static std::mutex g_tune_mu;
@@ -458,17 +460,21 @@ vdi_status vdi_composite_autotune(vdi_request* reqs, int32_t n, const vdi_params
             auto it = g_tune_cache.find(key);
             if (it != g_tune_cache.end()) { q.schedule = it->second; continue; }
         }
-        // time each applicable schedule on up to 65536 pixels of this request
+        // time each applicable schedule on up to 2^20 pixels of this request
         const long long npix = (long long)q.w * q.h;
-        const int sub = (int)(npix < 65536 ? npix : 65536);
+        const int sub = (int)(npix < (1 << 20) ? npix : (1 << 20));
         int best = default_schedule(q.k);
         float best_ms = 3.0e38f;
-        for (int sched = 1; sched <= 3 && s == VDI_OK; ++sched) {
+        const bool staged_fits = ws_bytes >= composite_workspace_bytes(sub, 1);
+        for (int sched = 1; sched <= VDI_SCHED_STAGED && s == VDI_OK; ++sched) {
             if (sched == 1 && q.k > 8) continue;
+            if (sched == VDI_SCHED_STAGED && !staged_fits) continue;
             float ms_min = 3.0e38f;
             for (int rep = 0; rep < 3 && s == VDI_OK; ++rep) {
                 s = cuda_check(cudaEventRecord(e0, st), "event record");
-                if (s == VDI_OK) s = launch_composite(q.pe, q.k, sub, 1, &q.out, params->bisect_iters, sched, status, st);
+                if (s == VDI_OK)
+                    s = launch_composite(q.pe, q.k, sub, 1, &q.out, params->bisect_iters, sched, status, workspace,
+                                         ws_bytes, st);
                 if (s == VDI_OK) s = cuda_check(cudaEventRecord(e1, st), "event record");
                 if (s == VDI_OK) s = cuda_check(cudaEventSynchronize(e1), "event sync");
                 float ms = 0.f;

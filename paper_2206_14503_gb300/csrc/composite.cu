@@ -88,24 +88,211 @@ __device__ __forceinline__ float4 load_rgba(const PeIn& pe, uint64_t idx) {
     return make_float4(a.x, a.y, b2.x, b2.y);
 }
 
-// Sweep state: one head per PE.  KMAX <= 16: unrolled, in registers;
-// larger: runtime loops, in local memory.
+// ---------------------------------------------------------------------------
+// Piece sweep
+// ---------------------------------------------------------------------------
+// The pieces of a pixel are the intervals between consecutive distinct record
+// bounds of its K lists.  A sweep keeps one head per PE (its current record)
+// and processes the bounds in depth order as events: a record's front starts
+// it, its back ends it and moves the head to the PE's next record with b > f.
+// The emission-absorption mixture of the active records is kept as exact
+// running sums, updated once per event: the extinction mu = -log2(1 - A) / l
+// and mu times the unpremultiplied colour of every non-opaque record are
+// summed in 128-bit fixed point (64 integer and 64 fraction bits; a record's
+// terms are computed the same way at its start and at its end, so the sum of
+// the active records is exact however many events came before).  Opaque
+// records (A >= 1) are counted, with their colours summed.
+
+struct U128 {
+    unsigned long long hi, lo;
+};
+
+__device__ __forceinline__ void u128_add(U128& s, const U128& x) {
+    const unsigned long long lo = s.lo + x.lo;
+    s.hi += x.hi + (lo < s.lo ? 1ull : 0ull);
+    s.lo = lo;
+}
+
+__device__ __forceinline__ void u128_sub(U128& s, const U128& x) {
+    const unsigned long long lo = s.lo - x.lo;
+    s.hi -= x.hi + (s.lo < x.lo ? 1ull : 0ull);
+    s.lo = lo;
+}
+
+// v in [0, 2^56] as fixed point: exact for v >= 2^-41 (the 24-bit significand
+// fits in the 64 fraction bits), truncated below
+__device__ __forceinline__ U128 to_fixed(float v) {
+    const float ip = truncf(v);
+    U128 r;
+    r.hi = __float2ull_rz(ip);
+    r.lo = __float2ull_rz(__fmul_rn(__fsub_rn(v, ip), 18446744073709551616.f));
+    return r;
+}
+
+__device__ __forceinline__ float from_fixed(const U128& s) {
+    return __fmaf_rn(__ull2float_rn(s.lo), 5.421010862427522e-20f, __ull2float_rn(s.hi));
+}
+
+// Clamp of a record's extinction terms (per unit depth): a record shorter than
+// ~3e-16 depth units with non-zero opacity is treated as having mu = 2^56, so
+// that 64 PEs' sums stay below 2^64.
+constexpr float kMuMax = 72057594037927936.f;  // 2^56
+
+// A record's terms: extinction mu = -log2(1 - A) / (b - f) and mu times the
+// unpremultiplied colour (non-opaque records), or its colour (opaque records).
+struct Contrib {
+    U128 M, MC[3], OC[3];
+    int op;  // 1 if opaque
+};
+
+__device__ __forceinline__ void u128_zero(U128& x) { x.hi = x.lo = 0ull; }
+
+__device__ __forceinline__ Contrib contrib(const float4& c, float f, float b) {
+    Contrib r;
+    u128_zero(r.M);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        u128_zero(r.MC[q]);
+        u128_zero(r.OC[q]);
+    }
+    r.op = 0;
+    const float col[3] = {c.x, c.y, c.z};
+    if (c.w >= 1.f) {
+        r.op = 1;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) r.OC[q] = to_fixed(fminf(fmaxf(col[q], 0.f), kMuMax));
+    } else if (c.w > 0.f) {
+        const float ia = rcp_approx(c.w);
+        const float mu =
+            fminf(__fmul_rn(-lg2_approx(__fsub_rn(1.f, c.w)), rcp_approx(__fsub_rn(b, f))), kMuMax);
+        r.M = to_fixed(mu);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) r.MC[q] = to_fixed(fminf(fmaxf(__fmul_rn(mu, __fmul_rn(col[q], ia)), 0.f), kMuMax));
+    }
+    return r;
+}
+
+// Sums over the active records.
+struct MixSums {
+    U128 M, MC[3], OC[3];
+    int nop, nact;
+};
+
+__device__ __forceinline__ void sums_reset(MixSums& m) {
+    u128_zero(m.M);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        u128_zero(m.MC[q]);
+        u128_zero(m.OC[q]);
+    }
+    m.nop = m.nact = 0;
+}
+
+// OPQ = false: the caller knows that no record is opaque (the OC sums stay 0)
+template <bool ADD, bool OPQ = true>
+__device__ __forceinline__ void sums_update(MixSums& m, const Contrib& x) {
+    if (ADD) {
+        u128_add(m.M, x.M);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            u128_add(m.MC[q], x.MC[q]);
+            if (OPQ) u128_add(m.OC[q], x.OC[q]);
+        }
+        m.nop += x.op;
+        ++m.nact;
+    } else {
+        u128_sub(m.M, x.M);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            u128_sub(m.MC[q], x.MC[q]);
+            if (OPQ) u128_sub(m.OC[q], x.OC[q]);
+        }
+        m.nop -= x.op;
+        --m.nact;
+    }
+}
+
+// The piece [t, t1] of an active set with sums m; `whole` when exactly one
+// record is active and it spans [t, t1] (its colour and opacity are wc).
+__device__ __forceinline__ void piece_from(const MixSums& m, bool whole, const float4& wc, float t, float t1,
+                                           Piece& x) {
+    x.f = t;
+    x.b = t1;
+    if (whole) {
+        // one record covering the piece exactly: the record itself
+        x.P[0] = wc.x;
+        x.P[1] = wc.y;
+        x.P[2] = wc.z;
+        x.a = wc.w;
+        x.lgT = lg2_approx(__fsub_rn(1.f, wc.w));
+        return;
+    }
+    if (m.nop > 0) {
+        // opaque records: the mean of their colours
+        const float inv = 1.f / (float)m.nop;
+        x.a = 1.f;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) x.P[q] = __fmul_rn(from_fixed(m.OC[q]), inv);
+        x.lgT = -INFINITY;
+        return;
+    }
+    const float M = m.nact > 0 ? from_fixed(m.M) : 0.f;
+    if (M > 0.f) {
+        // emission-absorption mixture (Eq. 2 when one record covers the piece in part)
+        x.lgT = -__fmul_rn(M, __fsub_rn(t1, t));
+        x.a = __fsub_rn(1.f, ex2_approx(x.lgT));
+        const float s = __fmul_rn(x.a, rcp_approx(M));
+#pragma unroll
+        for (int q = 0; q < 3; ++q) x.P[q] = __fmul_rn(from_fixed(m.MC[q]), s);
+    } else {
+        // a gap, or only fully transparent records
+        x.P[0] = x.P[1] = x.P[2] = 0.f;
+        x.a = 0.f;
+        x.lgT = 0.f;
+    }
+}
+
+// Direct sweeps: the sums plus the record started last (for the whole-record case).
+struct Mix {
+    MixSums s;
+    float lt_f, lt_b;  // bounds of the record started last
+    float4 lt_c;       // and its premultiplied colour and opacity
+};
+
+__device__ __forceinline__ void mix_reset(Mix& m) {
+    sums_reset(m.s);
+    m.lt_f = m.lt_b = -1.f;
+    m.lt_c = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ void mix_piece(const Mix& m, float t, float t1, Piece& x) {
+    piece_from(m.s, m.s.nact == 1 && m.lt_f == t && m.lt_b == t1, m.lt_c, t, t1, x);
+}
+
+__device__ __forceinline__ void mix_start(Mix& m, const float4& c, float f, float b) {
+    sums_update<true>(m.s, contrib(c, f, b));
+    m.lt_f = f;
+    m.lt_b = b;
+    m.lt_c = c;
+}
+
+__device__ __forceinline__ void mix_end(Mix& m, const float4& c, float f, float b) {
+    sums_update<false>(m.s, contrib(c, f, b));
+}
+
+constexpr float kNoEvent = 3.0e38f;
+
+// Heads in registers (K <= KMAX, fully unrolled; KMAX <= 8).
 template <int KMAX>
-struct Heads {
+struct RegHeads {
     uint64_t cur[KMAX];
     uint32_t rem[KMAX];
     float hf[KMAX], hb[KMAX];
 };
 
-#define VDI_UNROLL_K _Pragma("unroll")
-template <int KMAX>
-struct Unroll {
-    static constexpr int N = KMAX <= 16 ? KMAX : 1;
-};
-
 // advance PE e's head to its next record with b > f (records with b <= f are ignored)
 template <int KMAX, int PREC>
-__device__ __forceinline__ void next_valid(const PeIn* pe, Heads<KMAX>& h, int e) {
+__device__ __forceinline__ void reg_next_valid(const PeIn* pe, RegHeads<KMAX>& h, int e) {
     while (h.rem[e] > 0) {
         float f, b;
         load_fb<PREC>(pe[e], h.cur[e], f, b);
@@ -119,99 +306,276 @@ __device__ __forceinline__ void next_valid(const PeIn* pe, Heads<KMAX>& h, int e
     }
 }
 
-// Calls visit(piece) for every piece of one pixel in depth order.
+
+struct ActiveRec {
+    uint64_t cur;
+    float f, b;
+    int e;
+};
+
+// The piece [t, t1] covered by the n active records ar: the opaque records'
+// colour sum if any is opaque, else the extinction sums (each in exact fixed
+// point, as the running sums of the other sweeps).
+template <int PREC>
+__device__ __forceinline__ void mixture_piece(const PeIn* pe, const ActiveRec* ar, int n, float t, float t1,
+                                              Piece& x) {
+    MixSums m;
+    sums_reset(m);
+    m.nact = n;
+    for (int i = 0; i < n; ++i) {
+        const float4 c = load_rgba<PREC>(pe[ar[i].e], ar[i].cur);
+        if (c.w >= 1.f) ++m.nop;
+    }
+    if (m.nop > 0) {
+        for (int i = 0; i < n; ++i) {
+            const float4 c = load_rgba<PREC>(pe[ar[i].e], ar[i].cur);
+            if (c.w >= 1.f) {
+                const float col[3] = {c.x, c.y, c.z};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) u128_add(m.OC[q], to_fixed(fminf(fmaxf(col[q], 0.f), kMuMax)));
+            }
+        }
+    } else {
+        for (int i = 0; i < n; ++i) {
+            const Contrib c = contrib(load_rgba<PREC>(pe[ar[i].e], ar[i].cur), ar[i].f, ar[i].b);
+            u128_add(m.M, c.M);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) u128_add(m.MC[q], c.MC[q]);
+        }
+    }
+    piece_from(m, false, make_float4(0.f, 0.f, 0.f, 0.f), t, t1, x);
+}
+
+// Calls visit(piece) for every piece of one pixel in depth order; returns the
+// number of pieces.  The heads' bounds give each piece; the mixture sums of a
+// piece covered by several records (or part of one) are summed from its
+// active records (exactly, so the result equals the running sums of the other
+// sweeps), which costs nothing for the common piece that is a whole record
+// or a gap.
 template <int KMAX, int PREC, typename V>
-__device__ __forceinline__ void sweep(const PeIn* pe, int k, const uint32_t* cnt0, const uint64_t* off0, V& visit) {
-    Heads<KMAX> h;
-    float t = 3.0e38f;
-#pragma unroll Unroll<KMAX>::N
+__device__ __forceinline__ int sweep_reg(const PeIn* pe, int k, const uint32_t* cnt0, const uint64_t* off0, V& visit) {
+    RegHeads<KMAX> h;
+    float t = kNoEvent;
+#pragma unroll
     for (int e = 0; e < KMAX; ++e) {
+        h.rem[e] = 0;
         if (e < k) {
             h.cur[e] = off0[e];
             h.rem[e] = cnt0[e];
-            next_valid<KMAX, PREC>(pe, h, e);
+            reg_next_valid<KMAX, PREC>(pe, h, e);
             if (h.rem[e] > 0) t = fminf(t, h.hf[e]);
         }
     }
+    int npieces = 0;
     while (true) {
-        float t1 = 3.0e38f;
-        int nact = 0, last = -1;
-#pragma unroll Unroll<KMAX>::N
+        float t1 = kNoEvent;
+        int nact = 0, last = 0;
+        unsigned act = 0u;
+#pragma unroll
         for (int e = 0; e < KMAX; ++e) {
             if (e < k && h.rem[e] > 0) {
                 if (h.hf[e] <= t) {
                     ++nact;
                     last = e;
+                    act |= 1u << e;
                     t1 = fminf(t1, h.hb[e]);
                 } else {
                     t1 = fminf(t1, h.hf[e]);
                 }
             }
         }
-        if (t1 >= 3.0e38f) break;
+        if (t1 >= kNoEvent) break;
         Piece x;
-        x.f = t;
-        x.b = t1;
         if (nact == 0) {
+            x.f = t;
+            x.b = t1;
             x.P[0] = x.P[1] = x.P[2] = 0.f;
             x.a = 0.f;
             x.lgT = 0.f;
-        } else if (nact == 1 && h.hf[last] == t && h.hb[last] == t1) {
-            float4 c = load_rgba<PREC>(pe[last], h.cur[last]);
-            x.P[0] = c.x; x.P[1] = c.y; x.P[2] = c.z;
-            x.a = c.w;
-            x.lgT = lg2_approx(__fsub_rn(1.f, c.w));
         } else {
-            // emission-absorption mixture over [t, t1]; extinction in log2 units
-            float M = 0.f, MC[3] = {0.f, 0.f, 0.f}, OC[3] = {0.f, 0.f, 0.f};
-            int nop = 0;
-            const float dt = __fsub_rn(t1, t);
-#pragma unroll Unroll<KMAX>::N
+            float lf = 0.f, lb = 0.f;
+            uint64_t lc = 0;
+#pragma unroll
             for (int e = 0; e < KMAX; ++e) {
-                if (e < k && h.rem[e] > 0 && h.hf[e] <= t) {
-                    float4 c = load_rgba<PREC>(pe[e], h.cur[e]);
-                    if (c.w >= 1.f) {
-                        ++nop;
-                        OC[0] += c.x; OC[1] += c.y; OC[2] += c.z;
-                    } else if (c.w > 0.f) {
-                        float ia = rcp_approx(c.w);
-                        float mu = __fmul_rn(-lg2_approx(__fsub_rn(1.f, c.w)), rcp_approx(__fsub_rn(h.hb[e], h.hf[e])));
-                        M = __fadd_rn(M, mu);
-                        MC[0] = __fmaf_rn(mu, __fmul_rn(c.x, ia), MC[0]);
-                        MC[1] = __fmaf_rn(mu, __fmul_rn(c.y, ia), MC[1]);
-                        MC[2] = __fmaf_rn(mu, __fmul_rn(c.z, ia), MC[2]);
-                    }
+                if (e == last) {
+                    lf = h.hf[e];
+                    lb = h.hb[e];
+                    lc = h.cur[e];
                 }
             }
-            if (nop > 0) {
-                float inv = 1.f / (float)nop;
-                x.a = 1.f;
-                x.P[0] = OC[0] * inv; x.P[1] = OC[1] * inv; x.P[2] = OC[2] * inv;
-                x.lgT = -INFINITY;
-            } else if (M > 0.f) {
-                x.lgT = -__fmul_rn(M, dt);
-                x.a = __fsub_rn(1.f, ex2_approx(x.lgT));
-                float s = __fmul_rn(x.a, rcp_approx(M));
-                x.P[0] = __fmul_rn(MC[0], s); x.P[1] = __fmul_rn(MC[1], s); x.P[2] = __fmul_rn(MC[2], s);
+            if (nact == 1 && lf == t && lb == t1) {
+                MixSums m;
+                sums_reset(m);
+                piece_from(m, true, load_rgba<PREC>(pe[last], lc), t, t1, x);
             } else {
-                x.P[0] = x.P[1] = x.P[2] = 0.f;
-                x.a = 0.f;
-                x.lgT = 0.f;
+                ActiveRec ar[KMAX];
+                int na = 0;
+#pragma unroll
+                for (int e = 0; e < KMAX; ++e) {
+                    if ((act >> e) & 1u) {
+                        ar[na].cur = h.cur[e];
+                        ar[na].f = h.hf[e];
+                        ar[na].b = h.hb[e];
+                        ar[na].e = e;
+                        ++na;
+                    }
+                }
+                mixture_piece<PREC>(pe, ar, na, t, t1, x);
             }
         }
         visit(x);
-        // advance heads that end at t1
-#pragma unroll Unroll<KMAX>::N
+        ++npieces;
+        // advance the heads that end at t1
+#pragma unroll
         for (int e = 0; e < KMAX; ++e) {
-            if (e < k && h.rem[e] > 0 && h.hf[e] <= t && h.hb[e] <= t1) {
+            if (((act >> e) & 1u) && h.hb[e] <= t1) {
                 ++h.cur[e];
                 --h.rem[e];
-                next_valid<KMAX, PREC>(pe, h, e);
+                reg_next_valid<KMAX, PREC>(pe, h, e);
             }
         }
         t = t1;
     }
+    return npieces;
 }
+
+// Heads in shared memory with a winner tree over P leaves (K <= P <= 64), one
+// lane's arrays interleaved with its warp's other lanes (element i of lane l
+// at word i * 32 + l), so that every access is free of bank conflicts.
+template <int P>
+struct SmemHeads {
+    float* key;      // next event depth of each head (kNoEvent when exhausted)
+    float* oth;      // the other bound of the head's record
+    uint32_t* pos;   // record index within the PE's list; top bit: record active
+    uint32_t* node;  // node[n], 1 <= n < P: winning head of the subtree n
+    __device__ __forceinline__ float& K(int i) const { return key[i * 32]; }
+    __device__ __forceinline__ float& O(int i) const { return oth[i * 32]; }
+    __device__ __forceinline__ uint32_t& S(int i) const { return pos[i * 32]; }
+    __device__ __forceinline__ uint32_t& N(int i) const { return node[i * 32]; }
+};
+
+constexpr uint32_t kActive = 0x80000000u;
+
+// words of dynamic shared memory per thread for P leaves
+template <int P>
+constexpr int smem_words_per_thread() {
+    return 4 * P;
+}
+
+template <int P>
+__device__ __forceinline__ SmemHeads<P> smem_heads(uint32_t* smem) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t* base = smem + (size_t)warp * (4 * P * 32) + lane;
+    SmemHeads<P> h;
+    h.key = reinterpret_cast<float*>(base);
+    h.oth = reinterpret_cast<float*>(base + P * 32);
+    h.pos = base + 2 * P * 32;
+    h.node = base + 3 * P * 32;
+    return h;
+}
+
+template <int P>
+__device__ __forceinline__ int tree_winner_of(const SmemHeads<P>& h, int n) {
+    return n >= P ? n - P : (int)h.N(n);
+}
+
+// recompute the winners on the path from leaf e to the root
+template <int P>
+__device__ __forceinline__ void tree_update(const SmemHeads<P>& h, int e) {
+    int c = P + e;
+    int w = e;
+    float kw = h.K(e);
+#pragma unroll
+    for (int lev = 0; lev < 6; ++lev) {
+        if ((P >> lev) <= 1) break;
+        const int ws = tree_winner_of(h, c ^ 1);
+        const float ks = h.K(ws);
+        if (ks < kw || (ks == kw && ws < w)) {
+            w = ws;
+            kw = ks;
+        }
+        c >>= 1;
+        h.N(c) = (uint32_t)w;
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void tree_build(const SmemHeads<P>& h) {
+    for (int n = P - 1; n >= 1; --n) {
+        const int a = tree_winner_of(h, 2 * n), b = tree_winner_of(h, 2 * n + 1);
+        const float ka = h.K(a), kb = h.K(b);
+        h.N(n) = (uint32_t)((kb < ka || (kb == ka && b < a)) ? b : a);
+    }
+}
+
+// move head e to its first record at or after index j with b > f
+template <int P, int PREC>
+__device__ __forceinline__ void smem_seek(const SmemHeads<P>& h, const PeIn& pe, uint32_t p, int e, uint32_t j) {
+    const uint32_t cnt = __ldg(pe.counts + p);
+    const uint64_t base = __ldg(pe.offsets + p);
+    while (j < cnt) {
+        float f, b;
+        load_fb<PREC>(pe, base + j, f, b);
+        if (b > f) {
+            h.K(e) = f;
+            h.O(e) = b;
+            h.S(e) = j;
+            return;
+        }
+        ++j;
+    }
+    h.K(e) = kNoEvent;
+    h.S(e) = j;
+}
+
+template <int P, int PREC, typename V>
+__device__ __forceinline__ int sweep_smem(const PeIn* pe, int k, uint32_t p, const SmemHeads<P>& h, V& visit) {
+    for (int e = 0; e < P; ++e) {
+        if (e < k) smem_seek<P, PREC>(h, pe[e], p, e, 0u);
+        else h.K(e) = kNoEvent;
+    }
+    tree_build<P>(h);
+    Mix m;
+    mix_reset(m);
+    int npieces = 0;
+    float t = h.K(h.N(1));
+    while (t < kNoEvent) {
+        // events at depth t, in ascending PE order (the tree breaks ties by index)
+        float t1;
+        while (true) {
+            const int e = (int)h.N(1);
+            t1 = h.K(e);
+            if (t1 != t) break;
+            const uint32_t s = h.S(e);
+            const uint32_t j = s & ~kActive;
+            const float4 c = load_rgba<PREC>(pe[e], __ldg(pe[e].offsets + p) + j);
+            if (!(s & kActive)) {
+                const float b = h.O(e);
+                mix_start(m, c, t, b);
+                h.K(e) = b;
+                h.O(e) = t;
+                h.S(e) = s | kActive;
+            } else {
+                mix_end(m, c, h.O(e), t);
+                smem_seek<P, PREC>(h, pe[e], p, e, j + 1);
+            }
+            tree_update<P>(h, e);
+        }
+        if (t1 >= kNoEvent) break;
+        Piece x;
+        mix_piece(m, t, t1, x);
+        visit(x);
+        ++npieces;
+        t = t1;
+    }
+    return npieces;
+}
+
+// Work census of the compositing kernels (VDI_FLAG_CENSUS).
+struct CompCensus {
+    unsigned long long pixels = 0, searched = 0, sweeps = 0, pieces = 0, cand_steps = 0, records = 0,
+                       table_hits = 0;
+};
 
 // Counting state of one gamma candidate over pieces of arbitrary length.
 struct CompCount {
@@ -399,20 +763,52 @@ __device__ __forceinline__ void tree_candidates(float lo, float hi, float g[(1 <
     }
 }
 
-// The whole per-pixel composite: search, emission, zero tail.
-template <int KMAX, int NLEV, int PREC>
-__device__ __forceinline__ void composite_pixel(const PeIn* pe, int k, const OutDev& out, int iters,
-                                                unsigned int* status, uint32_t p) {
-    constexpr int NC = (1 << NLEV) - 1;
-    uint32_t cnt0[KMAX];
-    uint64_t off0[KMAX];
-#pragma unroll Unroll<KMAX>::N
-    for (int e = 0; e < KMAX; ++e) {
-        if (e < k) {
-            cnt0[e] = __ldg(pe[e].counts + p);
-            off0[e] = __ldg(pe[e].offsets + p);
+// One pixel's sweeps: heads in registers (KMAX > 0, K <= KMAX) or in shared
+// memory with P leaves (KMAX == 0, K <= P).
+template <int KMAX, int P, int PREC>
+struct Sweeper {
+    const PeIn* pe;
+    int k;
+    uint32_t p;
+    uint32_t cnt0[KMAX > 0 ? KMAX : 1];
+    uint64_t off0[KMAX > 0 ? KMAX : 1];
+    SmemHeads<P> sh;
+
+    __device__ __forceinline__ void init(const PeIn* pe_, int k_, uint32_t p_, uint32_t* smem) {
+        pe = pe_;
+        k = k_;
+        p = p_;
+        if constexpr (KMAX > 0) {
+#pragma unroll
+            for (int e = 0; e < KMAX; ++e) {
+                if (e < k) {
+                    cnt0[e] = __ldg(pe[e].counts + p);
+                    off0[e] = __ldg(pe[e].offsets + p);
+                }
+            }
+        } else {
+            sh = smem_heads<P>(smem);
         }
     }
+    __device__ __forceinline__ unsigned long long records() const {
+        unsigned long long n = 0;
+        for (int e = 0; e < k; ++e) n += __ldg(pe[e].counts + p);
+        return n;
+    }
+    template <typename V>
+    __device__ __forceinline__ int run(V& v) {
+        if constexpr (KMAX > 0) return sweep_reg<KMAX, PREC>(pe, k, cnt0, off0, v);
+        else return sweep_smem<P, PREC>(pe, k, p, sh, v);
+    }
+};
+
+// The whole per-pixel composite: search, emission, zero tail.
+// The whole per-pixel composite over the pieces that sw.run(visit) produces:
+// search, emission, zero tail.
+template <int NLEV, bool CENSUS, typename SW>
+__device__ __forceinline__ void composite_search_emit(SW& sw, const OutDev& out, int iters, unsigned int* status,
+                                                      uint32_t p, CompCensus* cs) {
+    constexpr int NC = (1 << NLEV) - 1;
     // search (sec. 2.4 applied to the pieces, sec. 5.2): sequential bisection;
     // a midpoint's count comes from the table of earlier marches when one of
     // their decision intervals holds it, else from a march over the NLEV-level
@@ -428,12 +824,20 @@ __device__ __forceinline__ void composite_pixel(const PeIn* pe, int k, const Out
         tree_candidates<NLEV>(0.f, 2.f, g);
 #pragma unroll
         for (int q = 0; q < NC; ++q) v.g2[q] = __fmul_rn(g[q], g[q]);
-        sweep<KMAX, PREC>(pe, k, cnt0, off0, v);
+        {
+            const int np = sw.run(v);
+            if (CENSUS) {
+                cs->sweeps += 1;
+                cs->pieces += (unsigned long long)np;
+                cs->cand_steps += (unsigned long long)np * NC;
+            }
+        }
 #pragma unroll
         for (int q = 0; q < NC; ++q) t.add(v.g2[q], v.st[q].qlo, v.st[q].qhi, v.st[q].cnt);
         if (v.nt <= out.n_s) {
             count = v.nt;
         } else {
+            if (CENSUS) cs->searched += 1;
             float lo = 0.f, hi = 2.f;
             int cnt_hi = 1;  // the distance never reaches 2: one supersegment
             for (int it = 0; it < iters; ++it) {
@@ -444,10 +848,17 @@ __device__ __forceinline__ void composite_pixel(const PeIn* pe, int k, const Out
                     v.reset();
 #pragma unroll
                     for (int q = 0; q < NC; ++q) v.g2[q] = __fmul_rn(g[q], g[q]);
-                    sweep<KMAX, PREC>(pe, k, cnt0, off0, v);
+                    const int np = sw.run(v);
+                    if (CENSUS) {
+                        cs->sweeps += 1;
+                        cs->pieces += (unsigned long long)np;
+                        cs->cand_steps += (unsigned long long)np * NC;
+                    }
 #pragma unroll
                     for (int q = 0; q < NC; ++q) t.add(v.g2[q], v.st[q].qlo, v.st[q].qhi, v.st[q].cnt);
                     c = v.st[0].cnt;
+                } else if (CENSUS) {
+                    cs->table_hits += 1;
                 }
                 if (c <= out.n_s) {
                     hi = mid;
@@ -470,7 +881,13 @@ __device__ __forceinline__ void composite_pixel(const PeIn* pe, int k, const Out
     em.written = 0;
     em.base = (size_t)p * out.n_s;
     em.out = &out;
-    sweep<KMAX, PREC>(pe, k, cnt0, off0, em);
+    {
+        const int np = sw.run(em);
+        if (CENSUS) {
+            cs->sweeps += 1;
+            cs->pieces += (unsigned long long)np;
+        }
+    }
     if (em.s.open && em.written < out.n_s) em.store(em.s.fS, em.bt, em.s.P, em.s.A);
     for (int j = em.written; j < out.n_s; ++j) {
         size_t idx = (size_t)p * out.n_s + j;
@@ -486,19 +903,509 @@ __device__ __forceinline__ void composite_pixel(const PeIn* pe, int k, const Out
     if (em.written != count) atomicCAS(status, 0u, (unsigned)VDI_ERR_CUDA);
 }
 
-template <int PREC>
-__device__ __forceinline__ void composite_pixel_sched(int sched, const PeIn* pe, int k, const OutDev& out, int iters,
-                                                      unsigned int* status, uint32_t p) {
-    if (sched == 1) composite_pixel<8, 2, PREC>(pe, k, out, iters, status, p);
-    else if (sched == 3) composite_pixel<VDI_MAX_PE, 3, PREC>(pe, k, out, iters, status, p);
-    else composite_pixel<VDI_MAX_PE, 2, PREC>(pe, k, out, iters, status, p);
+// Direct path: the pieces are swept from the K lists on every march.
+template <int KMAX, int P, int NLEV, int PREC, bool CENSUS = false>
+__device__ __forceinline__ void composite_pixel(const PeIn* pe, int k, const OutDev& out, int iters,
+                                                unsigned int* status, uint32_t p, uint32_t* smem,
+                                                CompCensus* cs = nullptr) {
+    Sweeper<KMAX, P, PREC> sw;
+    sw.init(pe, k, p, smem);
+    if (CENSUS) {
+        cs->pixels += 1;
+        cs->records += sw.records();
+    }
+    composite_search_emit<NLEV, CENSUS>(sw, out, iters, status, p, cs);
 }
 
-template <int KMAX, int NLEV, int PREC>
-__global__ void __launch_bounds__(128) composite_kernel(const __grid_constant__ CompArgs a) {
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void census_flush(const CompCensus& cs, unsigned long long* ctr) {
+    const unsigned long long v[7] = {cs.pixels, cs.searched, cs.sweeps, cs.pieces, cs.cand_steps, cs.records,
+                                     cs.table_hits};
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const unsigned long long w = warp_sum(v[i]);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(ctr + i, w);
+    }
+}
+
+template <int KMAX, int P, int NLEV, int PREC, bool CENSUS>
+__global__ void __launch_bounds__(128, NLEV > 2 ? 2 : 3) composite_kernel(const __grid_constant__ CompArgs a) {
+    extern __shared__ uint32_t smem[];
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= (uint32_t)a.npix) return;
-    composite_pixel<KMAX, NLEV, PREC>(a.pe, a.k, a.out, a.iters, a.status, p);
+    CompCensus cs;
+    if (p < (uint32_t)a.npix)
+        composite_pixel<KMAX, P, NLEV, PREC, CENSUS>(a.pe, a.k, a.out, a.iters, a.status, p, smem, &cs);
+    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
+}
+
+
+// ---------------------------------------------------------------------------
+// Staged path
+// ---------------------------------------------------------------------------
+// A warp takes 32 consecutive pixels at a time.  Phase G builds the pieces of
+// each of them in turn, the whole warp on one pixel: it loads the pixel's
+// records from all K lists, drops those with b <= f, sorts their bounds (each
+// list's bounds are already in order, so a stable merge of the K runs: log2 K
+// rounds in which every bound finds its place in its partner run by binary
+// search; ties go to the lower PE) and obtains the active set's sums after
+// every bound by an exact prefix scan of the records' terms.  The pieces go to
+// the warp's piece buffer, pixel i of the batch in column i.  Phase S: lane i
+// runs the search and the emission of pixel i over column i.  The pieces are
+// bit for bit those of the direct sweep.  Pixels with more records than the
+// stage holds are listed for the direct path (a second launch).
+
+constexpr int kStageRMax = 1024;           // records per pixel held by the stage
+constexpr int kStageCap = 2 * kStageRMax;  // piece rows per column (pieces <= 2 R - 1)
+constexpr int kStageWarps = 8;             // warps per CTA
+
+struct StageSmem {
+    uint16_t pay[2][2 * kStageRMax];  // bounds: (valid record << 1) | is_back
+    float2 rfb[kStageRMax];           // bounds of the valid records
+    uint32_t rloc[kStageRMax];        // (PE << 16) | index in the PE's list, of the valid records
+    uint32_t pref[VDI_MAX_PE + 1];    // records before PE e
+    uint32_t vpref[VDI_MAX_PE + 1];   // valid records before PE e
+    uint64_t off[VDI_MAX_PE];         // start of PE e's list for the pixel
+};
+
+__device__ __forceinline__ float bound_key(const StageSmem& S, uint32_t w) {
+    const float2 fb = S.rfb[w >> 1];
+    return (w & 1u) ? fb.y : fb.x;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+
+__device__ __forceinline__ U128 shfl_up_u128(const U128& v, int d) {
+    U128 r;
+    r.hi = __shfl_up_sync(0xffffffffu, v.hi, d);
+    r.lo = __shfl_up_sync(0xffffffffu, v.lo, d);
+    return r;
+}
+
+// running state of the stage's scan
+struct ScanState {
+    MixSums s;
+    uint32_t xr;   // xor of the active records' indices
+    uint32_t nb;   // bounds followed by a larger one (pieces)
+};
+
+__device__ __forceinline__ void scan_reset(ScanState& a) {
+    sums_reset(a.s);
+    a.xr = 0u;
+    a.nb = 0u;
+}
+
+// a + b (element-wise, modulo 2^128 for the sums)
+template <bool OPQ>
+__device__ __forceinline__ void scan_add(ScanState& a, const ScanState& b) {
+    u128_add(a.s.M, b.s.M);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        u128_add(a.s.MC[q], b.s.MC[q]);
+        if (OPQ) u128_add(a.s.OC[q], b.s.OC[q]);
+    }
+    a.s.nop += b.s.nop;
+    a.s.nact += b.s.nact;
+    a.xr ^= b.xr;
+    a.nb += b.nb;
+}
+
+template <bool OPQ>
+__device__ __forceinline__ ScanState shfl_up_state(const ScanState& v, int d) {
+    ScanState r;
+    r.s.M = shfl_up_u128(v.s.M, d);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        r.s.MC[q] = shfl_up_u128(v.s.MC[q], d);
+        if (OPQ) r.s.OC[q] = shfl_up_u128(v.s.OC[q], d);
+        else u128_zero(r.s.OC[q]);
+    }
+    r.s.nop = __shfl_up_sync(0xffffffffu, v.s.nop, d);
+    r.s.nact = __shfl_up_sync(0xffffffffu, v.s.nact, d);
+    r.xr = __shfl_up_sync(0xffffffffu, v.xr, d);
+    r.nb = __shfl_up_sync(0xffffffffu, v.nb, d);
+    return r;
+}
+
+// applies bound w (sorted position i) to the state
+template <int PREC, bool OPQ>
+__device__ __forceinline__ void stage_apply(const PeIn* pe, const StageSmem& S, uint32_t w, ScanState& a) {
+    const uint32_t c = w >> 1;
+    const uint32_t loc = S.rloc[c];
+    const int e = (int)(loc >> 16);
+    const float2 fb = S.rfb[c];
+    const float4 col = load_rgba<PREC>(pe[e], S.off[e] + (loc & 0xFFFFu));
+    const Contrib x = contrib(col, fb.x, fb.y);
+    if (w & 1u) sums_update<false, OPQ>(a.s, x);
+    else sums_update<true, OPQ>(a.s, x);
+    a.xr ^= c;
+}
+
+// Phase G after the merge: exact prefix scan of the records' terms over the
+// sorted bounds (srt, E of them; nv valid records), in contiguous chunks per
+// lane, and the pieces written to the column.
+template <int PREC, bool OPQ>
+__device__ __forceinline__ void stage_scan(const PeIn* pe, const StageSmem& S, const uint16_t* srt, uint32_t E,
+                                           uint32_t nv, float4* colA, float2* colB, int& npieces, int& nt,
+                                           float& f0) {
+    const int lane = threadIdx.x & 31;
+    // exact prefix scan of the records' terms over the sorted bounds, in
+    // contiguous chunks per lane
+    const uint32_t chunk = (E + 31) / 32;
+    const uint32_t i0 = min(E, lane * chunk), i1 = min(E, i0 + chunk);
+    ScanState loc;
+    scan_reset(loc);
+#pragma unroll 4
+    for (uint32_t i = i0; i < i1; ++i) {
+        stage_apply<PREC, OPQ>(pe, S, srt[i], loc);
+        if (i + 1 < E && bound_key(S, srt[i]) < bound_key(S, srt[i + 1])) ++loc.nb;
+    }
+    // exclusive prefix of the lanes' totals
+    ScanState inc = loc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const ScanState o = shfl_up_state<OPQ>(inc, d);
+        if (lane >= d) {
+            ScanState t = o;
+            scan_add<OPQ>(t, inc);
+            inc = t;
+        }
+    }
+    ScanState st = shfl_up_state<OPQ>(inc, 1);
+    if (lane == 0) scan_reset(st);
+    const uint32_t total_pieces = __shfl_sync(0xffffffffu, inc.nb, 31);
+    // the pieces: after bound i the active set is that of [key_i, key_{i+1}]
+    int my_nt = 0;
+    uint32_t row = st.nb;
+    for (uint32_t i = i0; i < i1; ++i) {
+        stage_apply<PREC, OPQ>(pe, S, srt[i], st);
+        if (i + 1 >= E) break;
+        const float t = bound_key(S, srt[i]), t1 = bound_key(S, srt[i + 1]);
+        if (!(t < t1)) continue;
+        bool whole = false;
+        float4 wc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (st.s.nact == 1) {
+            const uint32_t c = min(st.xr, nv - 1);
+            const float2 fb = S.rfb[c];
+            if (fb.x == t && fb.y == t1) {
+                const uint32_t l = S.rloc[c];
+                const int e = (int)(l >> 16);
+                wc = load_rgba<PREC>(pe[e], S.off[e] + (l & 0xFFFFu));
+                whole = true;
+            }
+        }
+        Piece x;
+        piece_from(st.s, whole, wc, t, t1, x);
+        colA[(size_t)row * 32] = make_float4(x.P[0], x.P[1], x.P[2], x.a);
+        colB[(size_t)row * 32] = make_float2(x.b, x.lgT);
+        my_nt += x.a > 0.f;
+        ++row;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) my_nt += __shfl_xor_sync(0xffffffffu, my_nt, d);
+    npieces = (int)total_pieces;
+    nt = my_nt;
+    f0 = bound_key(S, srt[0]);
+}
+
+// Phase G for pixel p into one column of the piece buffer (colA/colB point at
+// row 0 of the column; rows are 32 elements apart).  Returns false when the
+// pixel has more than kStageRMax records.
+template <int PREC>
+__device__ bool stage_pixel(const PeIn* pe, int k, uint32_t p, StageSmem& S, float4* colA, float2* colB, int rows,
+                            int& npieces, int& nt, float& f0) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    // counts and list starts, prefix over PEs
+    uint32_t c0 = 0, c1 = 0;
+    if (lane < k) {
+        c0 = __ldg(pe[lane].counts + p);
+        S.off[lane] = __ldg(pe[lane].offsets + p);
+    }
+    if (lane + 32 < k) {
+        c1 = __ldg(pe[lane + 32].counts + p);
+        S.off[lane + 32] = __ldg(pe[lane + 32].offsets + p);
+    }
+    const uint32_t x0 = warp_incl_scan_u32(c0);
+    const uint32_t t0 = __shfl_sync(0xffffffffu, x0, 31);
+    const uint32_t x1 = warp_incl_scan_u32(c1);
+    const uint32_t R = t0 + __shfl_sync(0xffffffffu, x1, 31);
+    S.pref[lane] = x0 - c0;
+    S.pref[lane + 32] = t0 + x1 - c1;
+    if (lane == 0) S.pref[VDI_MAX_PE] = R;
+    __syncwarp();
+    if (R > (uint32_t)kStageRMax) return false;
+    // bounds of every record; the valid ones (b > f) compacted in list order
+    uint32_t nv = 0;
+    bool opaque = false;
+    for (uint32_t r0 = 0; r0 < R; r0 += 32) {
+        const uint32_t r = r0 + lane;
+        bool valid = false;
+        float f = 0.f, b = 0.f;
+        int e = 0;
+        uint32_t j = 0;
+        if (r < R) {
+            int lo = 0, hi = k - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (S.pref[mid] <= r) lo = mid;
+                else hi = mid - 1;
+            }
+            e = lo;
+            j = r - S.pref[e];
+            load_fb<PREC>(pe[e], S.off[e] + j, f, b);
+            valid = b > f;
+            if (valid) opaque |= load_rgba<PREC>(pe[e], S.off[e] + j).w >= 1.f;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            const uint32_t c = nv + __popc(m & lt_mask);
+            S.rfb[c] = make_float2(f, b);
+            S.rloc[c] = ((uint32_t)e << 16) | j;
+        }
+        nv += __popc(m);
+    }
+    __syncwarp();
+    if (nv > 0 && 2 * nv - 1 > (uint32_t)rows) return false;  // more pieces than the column holds
+    // each list must be in depth order (b of a record <= f of the next): else
+    // the merge below would not be a permutation; such pixels go to the
+    // direct path
+    bool unsorted = false;
+    for (uint32_t c = lane + 1; c < nv; c += 32)
+        unsorted |= (S.rloc[c] >> 16) == (S.rloc[c - 1] >> 16) && !(S.rfb[c].x >= S.rfb[c - 1].y);
+    if (__any_sync(0xffffffffu, unsorted)) return false;
+    opaque = __any_sync(0xffffffffu, opaque);
+    // valid records before PE e: the first compacted record of a PE >= e
+    for (int e = lane; e <= k; e += 32) {
+        uint32_t lo = 0, hi = nv;
+        const uint32_t key = (uint32_t)e << 16;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (S.rloc[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        S.vpref[e] = lo;
+    }
+    const uint32_t E = 2 * nv;
+    for (uint32_t i = lane; i < E; i += 32) S.pay[0][i] = (uint16_t)i;
+    __syncwarp();
+    if (E == 0) {
+        npieces = 0;
+        nt = 0;
+        f0 = 0.f;
+        return true;
+    }
+    // stable merge of the PEs' runs of bounds: round r merges the groups of
+    // 2^r PEs pairwise (merge path: every lane takes an equal share of the
+    // output, finds where it starts in the two runs by binary search and
+    // merges sequentially from there; ties go to the lower run)
+    int src = 0;
+    for (int r = 0; (1 << r) < k; ++r) {
+        const uint16_t* in = S.pay[src];
+        uint16_t* outp = S.pay[src ^ 1];
+        const int span = 2 << r;
+        const int ngroups = (k + span - 1) / span;
+        const uint32_t per = (E + 31) / 32;
+        uint32_t o = min(E, (uint32_t)lane * per);
+        const uint32_t o_end = min(E, o + per);
+        while (o < o_end) {
+            // the merged group holding output o: the last one starting at or before o
+            int qlo = 0, qhi = ngroups - 1;
+            while (qlo < qhi) {
+                const int mid = (qlo + qhi + 1) >> 1;
+                if (2u * S.vpref[mid * span] <= o) qlo = mid;
+                else qhi = mid - 1;
+            }
+            const int e0 = qlo * span, em = min(e0 + (span >> 1), k), e1 = min(e0 + span, k);
+            const uint32_t a0 = 2u * S.vpref[e0], b0 = 2u * S.vpref[em], b1 = 2u * S.vpref[e1];
+            const uint32_t la = b0 - a0, lb = b1 - b0, d = o - a0;
+            uint32_t lo = d > lb ? d - lb : 0u, hi = min(d, la);
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (bound_key(S, in[a0 + mid]) <= bound_key(S, in[b0 + d - mid - 1])) lo = mid + 1;
+                else hi = mid;
+            }
+            uint32_t i = lo, j = d - lo;
+            float ka = i < la ? bound_key(S, in[a0 + i]) : 0.f;
+            float kb = j < lb ? bound_key(S, in[b0 + j]) : 0.f;
+            const uint32_t stop = min(o_end, b1);
+            for (; o < stop; ++o) {
+                if (i < la && (j >= lb || ka <= kb)) {
+                    outp[o] = in[a0 + i];
+                    ++i;
+                    if (i < la) ka = bound_key(S, in[a0 + i]);
+                } else {
+                    outp[o] = in[b0 + j];
+                    ++j;
+                    if (j < lb) kb = bound_key(S, in[b0 + j]);
+                }
+            }
+        }
+        src ^= 1;
+        __syncwarp();
+    }
+    const uint16_t* srt = S.pay[src];
+    if (opaque) stage_scan<PREC, true>(pe, S, srt, E, nv, colA, colB, npieces, nt, f0);
+    else stage_scan<PREC, false>(pe, S, srt, E, nv, colA, colB, npieces, nt, f0);
+    __syncwarp();
+    return true;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// rows ahead of the current one whose lines are requested into L2
+constexpr int kPrefetchRows = 16;
+
+// Phase S: the pieces of one column, streamed with loads two pieces ahead
+// (and L2 prefetches further ahead).
+struct BufSweeper {
+    const float4* A;
+    const float2* B;
+    int n;
+    float f0;
+    template <typename V>
+    __device__ __forceinline__ int run(V& visit) const {
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+        float2 b0 = make_float2(0.f, 0.f), b1 = b0;
+        if (n > 0) {
+            a0 = __ldcg(A);
+            b0 = __ldcg(B);
+        }
+        if (n > 1) {
+            a1 = __ldcg(A + 32);
+            b1 = __ldcg(B + 32);
+        }
+        float f = f0;
+        for (int j = 0; j < n; ++j) {
+            if ((j & 3) == 0 && j + kPrefetchRows < n) {
+                prefetch_l2(A + (size_t)(j + kPrefetchRows) * 32);
+                prefetch_l2(B + (size_t)(j + kPrefetchRows) * 32);
+            }
+            const float4 a = a0;
+            const float2 b = b0;
+            a0 = a1;
+            b0 = b1;
+            if (j + 2 < n) {
+                a1 = __ldcg(A + (size_t)(j + 2) * 32);
+                b1 = __ldcg(B + (size_t)(j + 2) * 32);
+            }
+            Piece x;
+            x.f = f;
+            x.b = b.x;
+            x.P[0] = a.x;
+            x.P[1] = a.y;
+            x.P[2] = a.z;
+            x.a = a.w;
+            x.lgT = b.y;
+            visit(x);
+            f = b.x;
+        }
+        return n;
+    }
+};
+
+struct StageArgs {
+    float4* bufA;  // per warp: rows x 32 columns
+    float2* bufB;
+    uint32_t* overflow;  // [0]: count, [2..]: entries
+    unsigned int* counter;
+    int rows;  // piece rows per column (at most kStageCap)
+};
+
+// Phase G for the batch's pixels, then Phase S for this lane's pixel.
+// `pixel_ok` etc. are per-lane results for pixel base + lane.
+template <int PREC>
+__device__ __forceinline__ void stage_batch(const PeIn* pe, int k, uint32_t base, uint32_t npix, StageSmem& S,
+                                            float4* wA, float2* wB, int rows, bool& ok, int& n, int& nt, float& f0) {
+    const int lane = threadIdx.x & 31;
+    ok = false;
+    n = nt = 0;
+    f0 = 0.f;
+    for (int col = 0; col < 32; ++col) {
+        const uint32_t p = base + (uint32_t)col;
+        if (p >= npix) break;
+        int pn, pnt;
+        float pf0;
+        const bool pok = stage_pixel<PREC>(pe, k, p, S, wA + col, wB + col, rows, pn, pnt, pf0);
+        if (lane == col) {
+            ok = pok;
+            n = pn;
+            nt = pnt;
+            f0 = pf0;
+        }
+    }
+}
+
+template <int PREC, bool CENSUS>
+__global__ void __launch_bounds__(kStageWarps * 32) composite_staged_kernel(const __grid_constant__ CompArgs a,
+                                                                          const __grid_constant__ StageArgs sa) {
+    extern __shared__ __align__(16) unsigned char stage_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    StageSmem& S = reinterpret_cast<StageSmem*>(stage_smem)[warp];
+    const size_t gw = (size_t)blockIdx.x * kStageWarps + warp;
+    float4* wA = sa.bufA + gw * (size_t)sa.rows * 32;
+    float2* wB = sa.bufB + gw * (size_t)sa.rows * 32;
+    const uint32_t nbatch = ((uint32_t)a.npix + 31u) / 32u;
+    CompCensus cs;
+    while (true) {
+        uint32_t batch = 0;
+        if (lane == 0) batch = atomicAdd(sa.counter, 1u);
+        batch = __shfl_sync(0xffffffffu, batch, 0);
+        if (batch >= nbatch) break;
+        const uint32_t base = batch * 32u;
+        bool ok;
+        int n, nt;
+        float f0;
+        stage_batch<PREC>(a.pe, a.k, base, (uint32_t)a.npix, S, wA, wB, sa.rows, ok, n, nt, f0);
+        const uint32_t p = base + (uint32_t)lane;
+        if (p < (uint32_t)a.npix) {
+            if (ok) {
+                BufSweeper sw;
+                sw.A = wA + lane;
+                sw.B = wB + lane;
+                sw.n = n;
+                sw.f0 = f0;
+                if (CENSUS) {
+                    cs.pixels += 1;
+                    for (int e = 0; e < a.k; ++e) cs.records += __ldg(a.pe[e].counts + p);
+                }
+                composite_search_emit<2, CENSUS>(sw, a.out, a.iters, a.status, p, &cs);
+            } else {
+                const uint32_t slot = atomicAdd(sa.overflow, 1u);
+                sa.overflow[1 + slot] = p;
+            }
+        }
+        __syncwarp();
+    }
+    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
+}
+
+// the pixels the stage could not hold, by the direct path (heads in shared memory)
+template <int P, int PREC, bool CENSUS>
+__global__ void __launch_bounds__(128) composite_overflow_kernel(const __grid_constant__ CompArgs a,
+                                                                 const uint32_t* overflow) {
+    extern __shared__ uint32_t smem[];
+    const uint32_t n = *overflow;
+    CompCensus cs;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < n; i += gridDim.x * blockDim.x) {
+        if (i < n) composite_pixel<0, P, 2, PREC, CENSUS>(a.pe, a.k, a.out, a.iters, a.status, overflow[1 + i], smem,
+                                                          &cs);
+    }
+    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
 }
 
 // ---------------------------------------------------------------------------
@@ -507,7 +1414,7 @@ __global__ void __launch_bounds__(128) composite_kernel(const __grid_constant__ 
 struct ReqDev {
     OutDev out;
     uint32_t npix;
-    uint32_t item_begin;  // first work item of the request
+    uint32_t item_begin;  // first 32-pixel batch of the request
     uint32_t pe_begin;    // index of its first PE descriptor
     int k, schedule;
 };
@@ -517,40 +1424,83 @@ struct BatchArgs {
     const PeIn* pes;
     int n;
     uint32_t total_items;
-    unsigned int* counter;
     unsigned int* status;
     int iters;
 };
 
-constexpr int kBatchTile = 128;
+__device__ __forceinline__ int request_of(const BatchArgs& a, uint32_t item) {
+    int lo = 0, hi = a.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&a.reqs[mid].item_begin) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
+// Items are (request, 32-pixel batch).  Requests with the staged schedule run
+// phases G and S; the others, and the pixels the stage cannot hold, are
+// listed (request << 32 | pixel) for the direct kernel that follows.
 template <int PREC>
-__global__ void __launch_bounds__(kBatchTile) composite_batched_kernel(const __grid_constant__ BatchArgs a) {
-    __shared__ uint32_t s_item;
+__global__ void __launch_bounds__(kStageWarps * 32) composite_batched_kernel(const __grid_constant__ BatchArgs a,
+                                                                            const __grid_constant__ StageArgs sa) {
+    extern __shared__ __align__(16) unsigned char stage_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    StageSmem& S = reinterpret_cast<StageSmem*>(stage_smem)[warp];
+    const size_t gw = (size_t)blockIdx.x * kStageWarps + warp;
+    float4* wA = sa.bufA + gw * (size_t)sa.rows * 32;
+    float2* wB = sa.bufB + gw * (size_t)sa.rows * 32;
+    unsigned long long* list = reinterpret_cast<unsigned long long*>(sa.overflow + 2);
     while (true) {
-        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
-        __syncthreads();
-        const uint32_t item = s_item;
-        __syncthreads();
-        if (item >= a.total_items) return;
-        // request holding the item: last r with item_begin <= item
-        int lo = 0, hi = a.n - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (__ldg(&a.reqs[mid].item_begin) <= item) lo = mid;
-            else hi = mid - 1;
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(sa.counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= a.total_items) break;
+        const int rq = request_of(a, item);
+        const ReqDev& r = a.reqs[rq];
+        const uint32_t base = (item - r.item_begin) * 32u;
+        const uint32_t p = base + (uint32_t)lane;
+        bool ok = false;
+        int n = 0, nt = 0;
+        float f0 = 0.f;
+        if (r.schedule == VDI_SCHED_STAGED)
+            stage_batch<PREC>(a.pes + r.pe_begin, r.k, base, r.npix, S, wA, wB, sa.rows, ok, n, nt, f0);
+        if (p < r.npix) {
+            if (ok) {
+                BufSweeper sw;
+                sw.A = wA + lane;
+                sw.B = wB + lane;
+                sw.n = n;
+                sw.f0 = f0;
+                composite_search_emit<2, false>(sw, r.out, a.iters, a.status, p, nullptr);
+            } else {
+                const uint32_t slot = atomicAdd(sa.overflow, 1u);
+                list[slot] = ((unsigned long long)rq << 32) | p;
+            }
         }
-        const ReqDev& r = a.reqs[lo];
-        const uint32_t p = (item - r.item_begin) * kBatchTile + threadIdx.x;
-        if (p < r.npix)
-            composite_pixel_sched<PREC>(r.schedule, a.pes + r.pe_begin, r.k, r.out, a.iters, a.status, p);
+        __syncwarp();
+    }
+}
+
+template <int P, int PREC>
+__global__ void __launch_bounds__(128) composite_batched_direct_kernel(const __grid_constant__ BatchArgs a,
+                                                                       const uint32_t* overflow) {
+    extern __shared__ uint32_t smem[];
+    const uint32_t n = *overflow;
+    const unsigned long long* list = reinterpret_cast<const unsigned long long*>(overflow + 2);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < n; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            const unsigned long long v = list[i];
+            const ReqDev& r = a.reqs[(int)(v >> 32)];
+            composite_pixel<0, P, 2, PREC>(a.pes + r.pe_begin, r.k, r.out, a.iters, a.status, (uint32_t)v, smem);
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-int default_schedule(int k) { return k <= 8 ? 1 : 2; }
+int default_schedule(int k) { return k <= 8 ? 1 : VDI_SCHED_STAGED; }
 
 static OutDev out_dev(const vdi_regular* out) {
     OutDev o;
@@ -563,8 +1513,124 @@ static OutDev out_dev(const vdi_regular* out) {
     return o;
 }
 
+// leaves of the winner tree for K PEs
+static int tree_leaves(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : 64); }
+
+template <int P>
+static size_t heads_smem_bytes(int threads) {
+    return (size_t)threads * smem_words_per_thread<P>() * sizeof(uint32_t);
+}
+
+static int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+    return sms;
+}
+
+// Workspace of the staged path: [header][batch counter][overflow count, pad,
+// entries][piece buffers], for `batches` 32-pixel batches and `entries`
+// overflow entries of `entry_bytes`.
+static size_t stage_ctas(uint64_t batches) {
+    const uint64_t need = (batches + kStageWarps - 1) / kStageWarps;
+    const uint64_t sms = (uint64_t)device_sms();
+    return (size_t)(need < sms ? (need > 0 ? need : 1) : sms);
+}
+
+static size_t stage_list_bytes(uint64_t entries, size_t entry_bytes) {
+    return align_up(8 + entries * entry_bytes, 256);
+}
+
+static size_t stage_buffer_bytes(size_t ctas, int rows) {
+    return ctas * kStageWarps * (size_t)rows * 32 * (sizeof(float4) + sizeof(float2));
+}
+
+size_t composite_workspace_bytes(int w, int h) {
+    const uint64_t npix = (uint64_t)w * (uint64_t)h;
+    const uint64_t batches = (npix + 31) / 32;
+    return kWsHeader + 256 + stage_list_bytes(npix, 4) + stage_buffer_bytes(stage_ctas(batches), kStageCap);
+}
+
+// Staged-path layout in the workspace; rows = 0 when the workspace holds no
+// piece buffer of at least 2 rows.
+static StageArgs stage_args(void* workspace, size_t ws_bytes, uint64_t npix, size_t entry_bytes, size_t ctas) {
+    char* base = static_cast<char*>(workspace);
+    StageArgs sa;
+    sa.counter = reinterpret_cast<unsigned int*>(base + kWsHeader);
+    sa.overflow = reinterpret_cast<uint32_t*>(base + kWsHeader + 256);
+    const size_t fixed = kWsHeader + 256 + stage_list_bytes(npix, entry_bytes);
+    const size_t per_row = stage_buffer_bytes(ctas, 1);
+    size_t rows = ws_bytes > fixed ? (ws_bytes - fixed) / per_row : 0;
+    if (rows > (size_t)kStageCap) rows = kStageCap;
+    sa.rows = rows >= 2 ? (int)rows : 0;
+    char* buf = base + fixed;
+    sa.bufA = reinterpret_cast<float4*>(buf);
+    sa.bufB = reinterpret_cast<float2*>(buf + ctas * kStageWarps * (size_t)sa.rows * 32 * sizeof(float4));
+    return sa;
+}
+
+template <int KMAX, int P, int NLEV, int PREC>
+static cudaError_t launch_cs(bool census, unsigned blocks, int threads, cudaStream_t st, const CompArgs& a) {
+    const size_t sm = KMAX > 0 ? 0 : heads_smem_bytes<P>(threads);
+    auto kern = census ? composite_kernel<KMAX, P, NLEV, PREC, true> : composite_kernel<KMAX, P, NLEV, PREC, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, threads, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t launch_sched(int schedule, int k, bool census, unsigned blocks, int threads, cudaStream_t st,
+                                const CompArgs& a) {
+    if (schedule == 1) return launch_cs<8, 16, 2, PREC>(census, blocks, threads, st, a);
+    const int P = tree_leaves(k);
+    if (schedule == 3) {
+        if (P == 16) return launch_cs<0, 16, 3, PREC>(census, blocks, threads, st, a);
+        if (P == 32) return launch_cs<0, 32, 3, PREC>(census, blocks, threads, st, a);
+        return launch_cs<0, 64, 3, PREC>(census, blocks, threads, st, a);
+    }
+    if (P == 16) return launch_cs<0, 16, 2, PREC>(census, blocks, threads, st, a);
+    if (P == 32) return launch_cs<0, 32, 2, PREC>(census, blocks, threads, st, a);
+    return launch_cs<0, 64, 2, PREC>(census, blocks, threads, st, a);
+}
+
+template <int P, int PREC>
+static cudaError_t launch_overflow(bool census, const CompArgs& a, const uint32_t* overflow, cudaStream_t st) {
+    const size_t sm = heads_smem_bytes<P>(128);
+    auto kern = census ? composite_overflow_kernel<P, PREC, true> : composite_overflow_kernel<P, PREC, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    unsigned blocks = (unsigned)(((uint64_t)a.npix + 127) / 128);
+    const unsigned cap = (unsigned)device_sms() * 8u;
+    if (blocks > cap) blocks = cap;
+    kern<<<blocks, 128, sm, st>>>(a, overflow);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t launch_staged(bool census, const CompArgs& a, void* workspace, size_t ws_bytes, cudaStream_t st) {
+    const uint64_t npix = (uint64_t)a.npix;
+    const size_t ctas = stage_ctas((npix + 31) / 32);
+    const StageArgs sa = stage_args(workspace, ws_bytes, npix, 4, ctas);
+    if (sa.rows == 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(sa.counter, 0, 256 + 8, st);
+    if (e != cudaSuccess) return e;
+    const size_t sm = kStageWarps * sizeof(StageSmem);
+    auto kern = census ? composite_staged_kernel<PREC, true> : composite_staged_kernel<PREC, false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)ctas, kStageWarps * 32, sm, st>>>(a, sa);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int P = tree_leaves(a.k);
+    if (P == 16) return launch_overflow<16, PREC>(census, a, sa.overflow, st);
+    if (P == 32) return launch_overflow<32, PREC>(census, a, sa.overflow, st);
+    return launch_overflow<64, PREC>(census, a, sa.overflow, st);
+}
+
 vdi_status launch_composite(const vdi_compact* pe, int k, int w, int h, const vdi_regular* out, int iters,
-                            int schedule, unsigned int* status, cudaStream_t st) {
+                            int schedule, unsigned int* status, void* workspace, size_t ws_bytes, cudaStream_t st,
+                            bool census) {
     CompArgs a;
     for (int e = 0; e < k; ++e) {
         a.pe[e].counts = pe[e].counts;
@@ -579,30 +1645,26 @@ vdi_status launch_composite(const vdi_compact* pe, int k, int w, int h, const vd
     a.status = status;
     const int prec_in = pe[0].prec;
     if (schedule == 0 || (schedule == 1 && k > 8)) schedule = default_schedule(k);
-    const int threads = 128;
-    const unsigned blocks = (unsigned)((a.npix + threads - 1) / threads);
     if (a.npix == 0) return VDI_OK;
     const bool f32 = prec_in == VDI_PREC_F32;
-    switch (schedule) {
-        case 1:
-            if (f32) composite_kernel<8, 2, VDI_PREC_F32><<<blocks, threads, 0, st>>>(a);
-            else composite_kernel<8, 2, VDI_PREC_F16><<<blocks, threads, 0, st>>>(a);
-            break;
-        case 3:
-            if (f32) composite_kernel<VDI_MAX_PE, 3, VDI_PREC_F32><<<blocks, threads, 0, st>>>(a);
-            else composite_kernel<VDI_MAX_PE, 3, VDI_PREC_F16><<<blocks, threads, 0, st>>>(a);
-            break;
-        default:
-            if (f32) composite_kernel<VDI_MAX_PE, 2, VDI_PREC_F32><<<blocks, threads, 0, st>>>(a);
-            else composite_kernel<VDI_MAX_PE, 2, VDI_PREC_F16><<<blocks, threads, 0, st>>>(a);
-            break;
+    cudaError_t e;
+    if (schedule == VDI_SCHED_STAGED) {
+        e = f32 ? launch_staged<VDI_PREC_F32>(census, a, workspace, ws_bytes, st)
+                : launch_staged<VDI_PREC_F16>(census, a, workspace, ws_bytes, st);
+    } else {
+        const int threads = 128;
+        const unsigned blocks = (unsigned)((a.npix + threads - 1) / threads);
+        e = f32 ? launch_sched<VDI_PREC_F32>(schedule, k, census, blocks, threads, st, a)
+                : launch_sched<VDI_PREC_F16>(schedule, k, census, blocks, threads, st, a);
     }
-    return cuda_check(cudaGetLastError(), "composite_kernel launch");
+    return cuda_check(e, "composite launch");
 }
 
 // Device table: [BatchHeader][ReqDev x n][PeIn x sum k]
 struct BatchHeader {
     uint32_t n, total_items, total_pes, prec_in;
+    uint32_t max_k, pad;
+    uint64_t total_pixels;
     uint64_t reqs_off, pes_off;
 };
 
@@ -620,7 +1682,8 @@ vdi_status batch_table_pack(const vdi_request* reqs, int n, void* host_table, si
     hd->pes_off = hd->reqs_off + align_up(sizeof(ReqDev) * (size_t)n, 64);
     ReqDev* rd = reinterpret_cast<ReqDev*>(base + hd->reqs_off);
     PeIn* pd = reinterpret_cast<PeIn*>(base + hd->pes_off);
-    uint64_t items = 0, pes = 0;
+    uint64_t items = 0, pes = 0, pixels = 0;
+    uint32_t max_k = 0;
     for (int r = 0; r < n; ++r) {
         const vdi_request& q = reqs[r];
         rd[r].out = out_dev(&q.out);
@@ -628,7 +1691,7 @@ vdi_status batch_table_pack(const vdi_request* reqs, int n, void* host_table, si
         rd[r].item_begin = (uint32_t)items;
         rd[r].pe_begin = (uint32_t)pes;
         rd[r].k = q.k;
-        rd[r].schedule = (q.schedule == 0 || (q.schedule == 1 && q.k > 8)) ? default_schedule(q.k) : q.schedule;
+        rd[r].schedule = q.schedule == VDI_SCHED_STAGED || q.schedule == 0 ? VDI_SCHED_STAGED : 2;
         for (int e = 0; e < q.k; ++e) {
             pd[pes + e].counts = q.pe[e].counts;
             pd[pes + e].offsets = q.pe[e].offsets;
@@ -636,18 +1699,63 @@ vdi_status batch_table_pack(const vdi_request* reqs, int n, void* host_table, si
             pd[pes + e].fb = reinterpret_cast<const float2*>(q.pe[e].fb);
         }
         pes += (uint64_t)q.k;
-        items += ((uint64_t)rd[r].npix + kBatchTile - 1) / kBatchTile;
+        pixels += rd[r].npix;
+        items += ((uint64_t)rd[r].npix + 31) / 32;
+        if ((uint32_t)q.k > max_k) max_k = (uint32_t)q.k;
     }
     if (items > 0xFFFFFFFFull) return set_error(VDI_ERR_INVALID_ARG, "batch table: too many work items");
     hd->n = (uint32_t)n;
     hd->total_items = (uint32_t)items;
     hd->total_pes = (uint32_t)pes;
     hd->prec_in = n > 0 ? (uint32_t)reqs[0].pe[0].prec : 0u;
+    hd->max_k = max_k;
+    hd->pad = 0;
+    hd->total_pixels = pixels;
     return VDI_OK;
 }
 
-vdi_status launch_composite_batched(const void* dev_table, const void* host_table, int iters, unsigned int* counter,
-                                    unsigned int* status, int device_sms, cudaStream_t st) {
+size_t batched_workspace_bytes(const void* host_table) {
+    const BatchHeader* hd = static_cast<const BatchHeader*>(host_table);
+    return kWsHeader + 256 + stage_list_bytes(hd->total_pixels, 8) +
+           stage_buffer_bytes(stage_ctas(hd->total_items), kStageCap);
+}
+
+template <int P, int PREC>
+static cudaError_t launch_batched_direct(const BatchArgs& a, const uint32_t* overflow, uint64_t pixels,
+                                         cudaStream_t st) {
+    const size_t sm = heads_smem_bytes<P>(128);
+    cudaError_t e = cudaFuncSetAttribute(composite_batched_direct_kernel<P, PREC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    uint64_t blocks = (pixels + 127) / 128;
+    const uint64_t cap = (uint64_t)device_sms() * 8u;
+    if (blocks > cap) blocks = cap;
+    composite_batched_direct_kernel<P, PREC><<<(unsigned)blocks, 128, sm, st>>>(a, overflow);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t launch_batched(const BatchArgs& a, const BatchHeader* hd, void* workspace, size_t ws_bytes,
+                                  cudaStream_t st) {
+    const size_t ctas = stage_ctas(hd->total_items);
+    const StageArgs sa = stage_args(workspace, ws_bytes, hd->total_pixels, 8, ctas);
+    if (sa.rows == 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(sa.counter, 0, 256 + 8, st);
+    if (e != cudaSuccess) return e;
+    const size_t sm = kStageWarps * sizeof(StageSmem);
+    e = cudaFuncSetAttribute(composite_batched_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    composite_batched_kernel<PREC><<<(unsigned)ctas, kStageWarps * 32, sm, st>>>(a, sa);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int P = tree_leaves((int)hd->max_k);
+    if (P == 16) return launch_batched_direct<16, PREC>(a, sa.overflow, hd->total_pixels, st);
+    if (P == 32) return launch_batched_direct<32, PREC>(a, sa.overflow, hd->total_pixels, st);
+    return launch_batched_direct<64, PREC>(a, sa.overflow, hd->total_pixels, st);
+}
+
+vdi_status launch_composite_batched(const void* dev_table, const void* host_table, int iters, unsigned int* status,
+                                    void* workspace, size_t ws_bytes, cudaStream_t st) {
     const BatchHeader* hd = static_cast<const BatchHeader*>(host_table);
     if (hd->n == 0 || hd->total_items == 0) return VDI_OK;
     BatchArgs a;
@@ -655,21 +1763,11 @@ vdi_status launch_composite_batched(const void* dev_table, const void* host_tabl
     a.pes = reinterpret_cast<const PeIn*>(static_cast<const char*>(dev_table) + hd->pes_off);
     a.n = (int)hd->n;
     a.total_items = hd->total_items;
-    a.counter = counter;
     a.status = status;
     a.iters = iters;
-    int per_sm = 1;
-    cudaError_t e;
-    if (hd->prec_in == VDI_PREC_F32)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, composite_batched_kernel<VDI_PREC_F32>, kBatchTile, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, composite_batched_kernel<VDI_PREC_F16>, kBatchTile, 0);
-    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-    unsigned blocks = (unsigned)(device_sms * per_sm);
-    if (blocks > hd->total_items) blocks = hd->total_items;
-    if (hd->prec_in == VDI_PREC_F32) composite_batched_kernel<VDI_PREC_F32><<<blocks, kBatchTile, 0, st>>>(a);
-    else composite_batched_kernel<VDI_PREC_F16><<<blocks, kBatchTile, 0, st>>>(a);
-    return cuda_check(cudaGetLastError(), "composite_batched_kernel launch");
+    const cudaError_t e = hd->prec_in == VDI_PREC_F32 ? launch_batched<VDI_PREC_F32>(a, hd, workspace, ws_bytes, st)
+                                                       : launch_batched<VDI_PREC_F16>(a, hd, workspace, ws_bytes, st);
+    return cuda_check(e, "composite_batched launch");
 }
 
 }  // namespace vdi

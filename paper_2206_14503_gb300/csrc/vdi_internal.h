@@ -75,12 +75,15 @@ size_t scan_workspace(int k, int n);
 vdi_status launch_scan(int k, int n, uint32_t* const* counts, uint64_t* const* offsets, void* ws, cudaStream_t st);
 
 vdi_status launch_composite(const vdi_compact* pe, int k, int w, int h, const vdi_regular* out, int iters,
-                            int schedule, unsigned int* status, cudaStream_t st);
+                            int schedule, unsigned int* status, void* workspace, size_t ws_bytes, cudaStream_t st,
+                            bool census = false);
 int default_schedule(int k);
+size_t composite_workspace_bytes(int w, int h);
 size_t batch_table_bytes(const vdi_request* reqs, int n);
 vdi_status batch_table_pack(const vdi_request* reqs, int n, void* host_table, size_t bytes);
-vdi_status launch_composite_batched(const void* dev_table, const void* host_table, int iters, unsigned int* counter,
-                                    unsigned int* status, int device_sms, cudaStream_t st);
+size_t batched_workspace_bytes(const void* host_table);
+vdi_status launch_composite_batched(const void* dev_table, const void* host_table, int iters, unsigned int* status,
+                                    void* workspace, size_t ws_bytes, cudaStream_t st);
 vdi_status launch_flatten(const vdi_regular* v, int w, int h, float* rgba, cudaStream_t st);
 
 // learned gamma (learned.cu)

@@ -24,6 +24,9 @@ SEED_VOLUME = 0xC0FFEE
 SEED_TF = 7
 SEED_ORBIT = 11
 SEED_REQUESTS = 13
+# request index of the record pool's runs (pooled lists)
+POOL_REQ = 0xFFFF
+POOL_RUN = 64
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +60,9 @@ def _load():
         lib.synth_lists_compact.restype = C.c_uint64
         lib.synth_hash4.argtypes = [C.c_uint64] * 4
         lib.synth_hash4.restype = C.c_uint64
+        lib.synth_pool_pick.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_int, C.c_uint64,
+                                        C.c_void_p, C.c_void_p]
+        lib.synth_pool_pick.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -137,3 +143,33 @@ def lists_compact(seed, req, set_, n_pix, n_s, dense=False, with_records=True):
 
 def hash4(seed, a, b, c) -> int:
     return _load().synth_hash4(seed, a, b, c)
+
+
+def pool_pick(seed, req, set_, pixel, n_s, runs):
+    """(n, run, start) of the pooled list of (req, set, pixel): records
+    [start, start + n) of pool run `run` (run r = one_list(seed, POOL_REQ, 0, r, POOL_RUN, dense=True))."""
+    run = C.c_uint64(0)
+    start = C.c_int(0)
+    n = _load().synth_pool_pick(seed, req, set_, pixel, n_s, runs, C.byref(run), C.byref(start))
+    return n, run.value, start.value
+
+
+def pooled_lists(seed, req, set_, pixels, n_s, runs):
+    """Per pixel (fb[n,2], rgba[n,4]) float32 of pooled lists, built on the host from the pool's runs."""
+    out = []
+    for p in pixels:
+        n, r, s0 = pool_pick(seed, req, set_, int(p), n_s, runs)
+        fb, rgba = one_list(seed, POOL_REQ, 0, r, POOL_RUN, dense=True)
+        out.append((fb[s0:s0 + n], rgba[s0:s0 + n]))
+    return out
+
+
+def requests(n, seed=SEED_REQUESTS, w_range=(256, 1920), h_range=(256, 1080), k_range=(2, 32), n_s_range=(8, 64)):
+    """Seeded request table of the batched workload: list of (w, h, k, n_s), each uniform on its range."""
+    out = []
+    for r in range(n):
+        vals = []
+        for i, (lo, hi) in enumerate((w_range, h_range, k_range, n_s_range)):
+            vals.append(lo + hash4(seed, 0x72657173, r, i) % (hi - lo + 1))
+        out.append(tuple(int(v) for v in vals))
+    return out

@@ -67,12 +67,16 @@ def lengths(seed, req, set_, pixels, n_s, dense=False):
     return _mod_u64(mix(key ^ 0x4c454e47), n_s + 1)
 
 
-def _mod_u64(z, m):
-    """unsigned 64-bit z mod m (m small) for an int64 tensor holding the bits of z"""
+def _mod_u64(z, m, m_tensor=None):
+    """unsigned 64-bit z mod m (m small, or the int64 tensor m_tensor) for an int64 tensor holding the bits of z"""
     import torch
 
     hi = _srl(z, 32)
     lo = z & 0xFFFFFFFF
+    if m_tensor is not None:
+        m = m_tensor
+        r32 = torch.remainder(torch.full_like(m, 1 << 32), m)
+        return ((torch.remainder(hi, m) * r32 + torch.remainder(lo, m)) % m).to(torch.int32)
     return ((torch.remainder(hi, m) * ((1 << 32) % m) + torch.remainder(lo, m)) % m).to(torch.int32)
 
 
@@ -99,3 +103,72 @@ def lists(seed, req, set_, pixels, n_s, dense=False):
     fb = torch.where(keep[..., None], fb, torch.zeros_like(fb))
     rgba = torch.where(keep[..., None], rgba, torch.zeros_like(rgba))
     return cnt, fb, rgba
+
+
+def pool_picks(seed, req, set_, pixels, n_s, runs):
+    """(n int32, first record index int64 = run * 64 + start) of pooled lists; twin of synth.pool_pick."""
+    import torch
+
+    n = lengths(seed, req, set_, pixels, n_s, dense=False)
+    key = list_keys(seed, req, set_, pixels)
+    run = _mod_u64_big(mix(key ^ 0x706f6f6c), runs)
+    start = _mod_u64(mix(key ^ 0x73747274), None, m_tensor=(64 - n + 1).to(torch.int64))
+    return n, run * 64 + start.to(torch.int64)
+
+
+def _mod_u64_big(z, m):
+    """unsigned 64-bit z mod m for m < 2^31 (int64 result)"""
+    import torch
+
+    hi = _srl(z, 32)
+    lo = z & 0xFFFFFFFF
+    return (torch.remainder(hi, m) * ((1 << 32) % m) + torch.remainder(lo, m)) % m
+
+
+def pool(seed, runs, chunk=1 << 19, device="cuda"):
+    """Record pool of the pooled lists: (fb float32 [runs * 64, 2], rgba float32 [runs * 64, 4]); run r is
+    one_list(seed, POOL_REQ, 0, r, 64, dense=True)."""
+    import torch
+
+    from synth import POOL_REQ, POOL_RUN
+
+    fb = torch.empty((runs * POOL_RUN, 2), dtype=torch.float32, device=device)
+    rgba = torch.empty((runs * POOL_RUN, 4), dtype=torch.float32, device=device)
+    for r0 in range(0, runs, chunk):
+        r1 = min(runs, r0 + chunk)
+        pix = torch.arange(r0, r1, dtype=torch.int64, device=device)
+        _, f, c = lists(seed, POOL_REQ, 0, pix, POOL_RUN, dense=True)
+        fb[r0 * POOL_RUN:r1 * POOL_RUN] = f.reshape(-1, 2)
+        rgba[r0 * POOL_RUN:r1 * POOL_RUN] = c.reshape(-1, 4)
+    return fb, rgba
+
+
+def dense_set(seed, req, set_, npix, n_s, chunk=1 << 20, device="cuda"):
+    """Dense compact lists of one (request, set) over pixels [0, npix): (counts int32 [npix],
+    offsets int64 [npix + 1] = p * n_s, fb float32 [npix * n_s, 2], rgba float32 [npix * n_s, 4])."""
+    import torch
+
+    counts = torch.full((npix,), n_s, dtype=torch.int32, device=device)
+    offsets = torch.arange(npix + 1, dtype=torch.int64, device=device) * n_s
+    fb = torch.empty((npix * n_s, 2), dtype=torch.float32, device=device)
+    rgba = torch.empty((npix * n_s, 4), dtype=torch.float32, device=device)
+    for p0 in range(0, npix, chunk):
+        p1 = min(npix, p0 + chunk)
+        pix = torch.arange(p0, p1, dtype=torch.int64, device=device)
+        _, f, c = lists(seed, req, set_, pix, n_s, dense=True)
+        fb[p0 * n_s:p1 * n_s] = f.reshape(-1, 2)
+        rgba[p0 * n_s:p1 * n_s] = c.reshape(-1, 4)
+    return counts, offsets, fb, rgba
+
+
+def pack_f16(fb, rgba, chunk=1 << 24):
+    """16-byte records {float32 f, float32 b, float16 r, g, b, a (round to nearest even)} as int32 [n, 4]."""
+    import torch
+
+    n = fb.shape[0]
+    out = torch.empty((n, 4), dtype=torch.int32, device=fb.device)
+    for i0 in range(0, n, chunk):
+        i1 = min(n, i0 + chunk)
+        out[i0:i1, 0:2] = fb[i0:i1].view(torch.int32)
+        out[i0:i1, 2:4] = rgba[i0:i1].to(torch.float16).contiguous().view(torch.int32)
+    return out

@@ -324,3 +324,19 @@ uint64_t synth_lists_compact(uint64_t seed, uint32_t req, uint32_t set, uint64_t
     }
     return acc;
 }
+
+/*
+ * Pooled lists (the batched workload, whose lists would not fit in memory if
+ * every one were stored): a pool of `runs` sorted 64-record runs, run r being
+ * synth_list(seed, SYNTH_POOL_REQ, 0, r, 64, dense).  The list of (req, set,
+ * pixel) is the window of n = synth_list_len(...) consecutive records of run
+ * `run`, starting at `start`; returns n and writes run and start.
+ */
+int synth_pool_pick(uint64_t seed, uint32_t req, uint32_t set, uint64_t pixel, int n_s, uint64_t runs,
+                    uint64_t* run, int* start) {
+    int n = synth_list_len(seed, req, set, pixel, n_s, 0);
+    uint64_t key = list_key(seed, req, set, pixel);
+    *run = sm64_mix(key ^ 0x706f6f6cULL) % runs;
+    *start = (int)(sm64_mix(key ^ 0x73747274ULL) % (uint64_t)(64 - n + 1));
+    return n;
+}

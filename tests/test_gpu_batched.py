@@ -51,7 +51,7 @@ def batched(vdi, torch, reqs, outs, schedules=None, graph=False, replays=1):
     R = vdi.Requests(items)
     host = vdi.vdi_batch_table_pack(R)
     dev = torch.frombuffer(bytearray(host), dtype=torch.uint8).cuda()
-    ws = vdi.Workspace(vdi.vdi_composite_batched_workspace(len(R)))
+    ws = vdi.Workspace(vdi.vdi_composite_batched_workspace(host))
     params = vdi.make_params()
     if not graph:
         vdi.check(vdi.vdi_composite_batched(dev.data_ptr(), host, params, ws.ptr, ws.nbytes), "batched")
@@ -109,7 +109,7 @@ def test_schedules_and_autotuner_agree():
     reqs = make_requests(6, 3)
     for q in reqs:
         base = outputs(run_single(vdi, q, schedule=0))
-        for sched in (1, 2, 3):
+        for sched in (1, 2, 3, vdi.VDI_SCHED_STAGED):
             if sched == 1 and q["k"] > 8:
                 continue
             got = outputs(run_single(vdi, q, schedule=sched))
@@ -119,10 +119,10 @@ def test_schedules_and_autotuner_agree():
     outs = [vdi.Regular(q["w"] * q["h"], q["n_s"]) for q in reqs]
     items = [([p.struct() for p in q["pes"]], q["w"], q["h"], o.struct(), 0) for q, o in zip(reqs, outs)]
     R = vdi.Requests(items)
-    ws = vdi.Workspace(256)
+    ws = vdi.Workspace(vdi.vdi_composite_workspace(64, 65536, 1, 64))
     vdi.check(vdi.vdi_composite_autotune(R, vdi.make_params(), ws.ptr, ws.nbytes), "autotune")
     scheds = [R.arr[i].schedule for i in range(len(R))]
-    assert all(s in (1, 2, 3) for s in scheds)
+    assert all(s in (1, 2, 3, vdi.VDI_SCHED_STAGED) for s in scheds)
     assert all(not (s == 1 and q["k"] > 8) for s, q in zip(scheds, reqs))
     ref = [outputs(run_single(vdi, q)) for q in reqs]
     outs2 = [vdi.Regular(q["w"] * q["h"], q["n_s"]) for q in reqs]
