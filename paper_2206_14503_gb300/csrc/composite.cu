@@ -1351,7 +1351,7 @@ __device__ __forceinline__ void stage_batch(const PeIn* pe, int k, uint32_t base
 }
 
 template <int PREC, bool CENSUS>
-__global__ void __launch_bounds__(kStageWarps * 32) composite_staged_kernel(const __grid_constant__ CompArgs a,
+__global__ void __launch_bounds__(kStageWarps * 32, 1) composite_staged_kernel(const __grid_constant__ CompArgs a,
                                                                           const __grid_constant__ StageArgs sa) {
     extern __shared__ __align__(16) unsigned char stage_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1442,7 +1442,7 @@ __device__ __forceinline__ int request_of(const BatchArgs& a, uint32_t item) {
 // phases G and S; the others, and the pixels the stage cannot hold, are
 // listed (request << 32 | pixel) for the direct kernel that follows.
 template <int PREC>
-__global__ void __launch_bounds__(kStageWarps * 32) composite_batched_kernel(const __grid_constant__ BatchArgs a,
+__global__ void __launch_bounds__(kStageWarps * 32, 1) composite_batched_kernel(const __grid_constant__ BatchArgs a,
                                                                             const __grid_constant__ StageArgs sa) {
     extern __shared__ __align__(16) unsigned char stage_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
