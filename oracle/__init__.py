@@ -81,6 +81,10 @@ def _load():
         lib.oc_dvr.restype = i
         lib.oc_ray.argtypes = [vp, i, i, vp, vp]
         lib.oc_ray.restype = None
+        lib.oc_render_view.argtypes = [vp, vp, i, vp, vp, vp, i, vp]
+        lib.oc_render_view.restype = None
+        lib.oc_render_ray.argtypes = [vp, vp, i, d, vp, vp, vp, vp]
+        lib.oc_render_ray.restype = None
         lib.oc_hit_box.argtypes = [vp, vp, vp, vp, vp]
         lib.oc_hit_box.restype = i
         lib.oc_value.argtypes = [vp, vp]
@@ -286,6 +290,36 @@ def flatten(counts, recs):
     np_, stride = recs.shape[0], recs.shape[1]
     out = np.zeros((np_, 4), dtype=np.float64)
     _load().oc_flatten(_p(counts), _p(recs), np_, stride, _p(out))
+    return out
+
+
+def render_view(counts, recs, gen_cam, view_cam, pixels=None):
+    """A regular VDI of camera gen_cam (counts[W H], recs[W H, n_s, 6]) rendered from view_cam:
+    premultiplied rgba[np, 4] for the given pixels of view_cam (all by default)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32).ravel()
+    recs = np.ascontiguousarray(recs, dtype=np.float64)
+    n_s = recs.shape[1]
+    if pixels is None:
+        pixels = np.arange(view_cam.width * view_cam.height, dtype=np.int32)
+    pixels = np.ascontiguousarray(pixels, dtype=np.int32)
+    out = np.zeros((len(pixels), 4), dtype=np.float64)
+    g, v = camera(gen_cam), camera(view_cam)
+    _load().oc_render_view(_p(counts), _p(recs), n_s, _ref(g), _ref(v), _p(pixels), len(pixels), _p(out))
+    return out
+
+
+def render_ray(counts, recs, gen_cam, o, d):
+    """One ray o + s d (unit d) through the VDI of gen_cam: premultiplied rgba[4]."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32).ravel()
+    recs = np.ascontiguousarray(recs, dtype=np.float64)
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    out = np.zeros(4, dtype=np.float64)
+    g = camera(gen_cam)
+    n_s = recs.shape[1]
+    used = np.arange(n_s)[None, :] < counts[:, None]
+    rho_max = float(recs[..., 1][used].max()) if used.any() else 0.0
+    _load().oc_render_ray(_p(counts), _p(recs), n_s, rho_max, _ref(g), _p(o), _p(d), _p(out))
     return out
 
 

@@ -878,3 +878,172 @@ double oc_mlp_loss_grad(const double* th, const double* x, const double* label, 
     }
     return loss;
 }
+
+/* ====================================================================== */
+/* Rendering a regular VDI from another viewpoint.  The paper renders its   */
+/* VDIs from deviated viewpoints to judge them (sec. 5.2, the comparison    */
+/* with DVR at viewpoint deviations) with a renderer from earlier work that */
+/* it does not restate; this is the plain reading of a VDI as a             */
+/* view-dependent volume:                                                   */
+/*  - the generating camera G splits space into frustum columns, one per   */
+/*    pixel: the points whose projection through G's eye falls in the      */
+/*    pixel's square on G's image plane (the plane at unit distance along  */
+/*    G's forward axis);                                                    */
+/*  - within pixel p's column, supersegment (f, b, P, A) occupies the      */
+/*    points at distance f..b from G's eye (reading R1: the depth of a     */
+/*    point off the column's centre ray is its distance from G's eye, which*/
+/*    is the generation depth on the centre ray) and is a homogeneous      */
+/*    emission-absorption medium: a path of length l through it has        */
+/*    opacity 1 - (1 - A)^(l / (b - f)) (the length correction of Eq. 2)   */
+/*    and straight colour P / A;                                           */
+/*  - a ray of the viewing camera V is cut where it crosses column faces   */
+/*    and supersegment shells, and the pieces are composited front to back */
+/*    with "over" (sec. 2.3).  Everything outside the columns, and between */
+/*    supersegments, is empty.                                              */
+/* With V = G every ray stays on its column's centre line and the result   */
+/* is the flattened VDI (oc_flatten).                                       */
+/* ====================================================================== */
+typedef struct {
+    double eye[3], fwd[3], right[3], up[3];
+    double th, asp;
+    int W, H;
+} oc_frame;
+
+static void oc_frame_of(const oc_camera* c, oc_frame* F) {
+    for (int a = 0; a < 3; ++a) F->eye[a] = c->eye[a];
+    v_sub(c->center, c->eye, F->fwd);
+    v_norm(F->fwd);
+    v_cross(F->fwd, c->up, F->right);
+    v_norm(F->right);
+    v_cross(F->right, F->fwd, F->up);
+    F->th = tan(0.5 * c->fovy_deg * 3.14159265358979323846 / 180.0);
+    F->asp = (double)c->width / (double)c->height;
+    F->W = c->width;
+    F->H = c->height;
+}
+
+static double v_dot(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static int cmp_dbl_up(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* One ray o + s d (unit d, s >= 0) through the VDI of G: counts[W_G H_G],  */
+/* recs[W_G H_G][n_s][REC], rho_max at least the largest back depth.        */
+/* Writes premultiplied RGBA to rgba[4].                                    */
+void oc_render_ray(const int* counts, const double* recs, int n_s, double rho_max, const oc_camera* gen,
+                   const double* o, const double* d, double* rgba) {
+    oc_frame G;
+    oc_frame_of(gen, &G);
+    double q0[3];
+    v_sub(o, G.eye, q0);
+    const double qx = v_dot(q0, G.right), qy = v_dot(q0, G.up), qz = v_dot(q0, G.fwd);
+    const double dx = v_dot(d, G.right), dy = v_dot(d, G.up), dz = v_dot(d, G.fwd);
+    const double X0 = -G.th * G.asp, X1 = G.th * G.asp, Y0 = G.th, Y1 = -G.th;
+    /* inside the frustum: x - X0 z >= 0, X1 z - x >= 0, Y0 z - y >= 0, y - Y1 z >= 0, all linear in s */
+    double s_in = 0.0, s_out = INFINITY;
+    const double A[4] = {qx - X0 * qz, X1 * qz - qx, Y0 * qz - qy, qy - Y1 * qz};
+    const double B[4] = {dx - X0 * dz, X1 * dz - dx, Y0 * dz - dy, dy - Y1 * dz};
+    rgba[0] = rgba[1] = rgba[2] = rgba[3] = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        if (B[c] == 0.0) {
+            if (A[c] < 0.0) return;
+            continue;
+        }
+        double s = -A[c] / B[c];
+        if (B[c] > 0.0) { if (s > s_in) s_in = s; }
+        else if (s < s_out) s_out = s;
+    }
+    /* beyond |q0| + rho_max the distance from G's eye exceeds every back depth */
+    const double s_far = sqrt(v_dot(q0, q0)) + rho_max + 1.0;
+    if (s_out > s_far) s_out = s_far;
+    if (!(s_out > s_in)) return;
+    /* cut points: column faces, row faces, closest approach to G's eye */
+    const int ncut_max = G.W + G.H + 4;
+    double* cut = (double*)malloc(sizeof(double) * (size_t)ncut_max);
+    int nc = 0;
+    cut[nc++] = s_in;
+    cut[nc++] = s_out;
+    for (int i = 1; i < G.W; ++i) {
+        const double Xi = (2.0 * i / G.W - 1.0) * G.th * G.asp;
+        const double den = dx - Xi * dz;
+        if (den == 0.0) continue;
+        const double s = -(qx - Xi * qz) / den;
+        if (s > s_in && s < s_out) cut[nc++] = s;
+    }
+    for (int j = 1; j < G.H; ++j) {
+        const double Yj = (1.0 - 2.0 * j / G.H) * G.th;
+        const double den = dy - Yj * dz;
+        if (den == 0.0) continue;
+        const double s = -(qy - Yj * qz) / den;
+        if (s > s_in && s < s_out) cut[nc++] = s;
+    }
+    const double s_star = -v_dot(q0, d); /* closest approach of the line to G's eye */
+    if (s_star > s_in && s_star < s_out) cut[nc++] = s_star;
+    qsort(cut, nc, sizeof(double), cmp_dbl_up);
+    double perp[3];
+    for (int a = 0; a < 3; ++a) perp[a] = q0[a] + s_star * d[a];
+    const double rho_star = sqrt(v_dot(perp, perp));
+    double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+    for (int m = 0; m + 1 < nc; ++m) {
+        const double sa = cut[m], sb = cut[m + 1];
+        if (!(sb > sa)) continue;
+        const double sm = 0.5 * (sa + sb);
+        const double zm = qz + sm * dz;
+        const double Xm = (qx + sm * dx) / zm, Ym = (qy + sm * dy) / zm;
+        int iu = (int)floor((Xm / (G.th * G.asp) + 1.0) * 0.5 * G.W);
+        int iv = (int)floor((1.0 - Ym / G.th) * 0.5 * G.H);
+        if (iu < 0) iu = 0;
+        if (iu >= G.W) iu = G.W - 1;
+        if (iv < 0) iv = 0;
+        if (iv >= G.H) iv = G.H - 1;
+        const size_t p = (size_t)iv * G.W + iu;
+        const int n = counts[p];
+        const int rising = sm >= s_star; /* distance from G's eye grows with s on this piece */
+        for (int t = 0; t < n; ++t) {
+            const int k = rising ? t : n - 1 - t;
+            const double* r = recs + ((size_t)p * n_s + k) * REC;
+            const double f = r[0], b = r[1], Ar = r[5];
+            if (!(b > f) || Ar <= 0.0) continue;
+            /* s-interval of the piece where the distance lies in [f, b] */
+            double lo, hi;
+            const double cf = f > rho_star ? sqrt((f - rho_star) * (f + rho_star)) : 0.0;
+            const double cb = b > rho_star ? sqrt((b - rho_star) * (b + rho_star)) : 0.0;
+            if (b <= rho_star) continue;
+            if (rising) { lo = s_star + cf; hi = s_star + cb; }
+            else { lo = s_star - cb; hi = s_star - cf; }
+            if (lo < sa) lo = sa;
+            if (hi > sb) hi = sb;
+            const double l = hi - lo;
+            if (!(l > 0.0)) continue;
+            double alpha;
+            if (Ar >= 1.0) alpha = 1.0;
+            else alpha = -expm1(log1p(-Ar) * l / (b - f));
+            for (int c = 0; c < 3; ++c) C[c] += T * (r[2 + c] / Ar) * alpha;
+            T *= 1.0 - alpha;
+        }
+    }
+    free(cut);
+    rgba[0] = C[0];
+    rgba[1] = C[1];
+    rgba[2] = C[2];
+    rgba[3] = 1.0 - T;
+}
+
+/* Pixels (i, j) of V (pixel index j W_V + i) through the VDI of G. */
+void oc_render_view(const int* counts, const double* recs, int n_s, const oc_camera* gen, const oc_camera* view,
+                    const int* pixels, int np, double* rgba) {
+    double rho_max = 0.0;
+    for (size_t p = 0; p < (size_t)gen->width * gen->height; ++p)
+        for (int k = 0; k < counts[p]; ++k) {
+            const double b = recs[(p * n_s + k) * REC + 1];
+            if (b > rho_max) rho_max = b;
+        }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int q = 0; q < np; ++q) {
+        double o[3], d[3];
+        oc_ray(view, pixels[q] % view->width, pixels[q] / view->width, o, d);
+        oc_render_ray(counts, recs, n_s, rho_max, gen, o, d, rgba + (size_t)4 * q);
+    }
+}

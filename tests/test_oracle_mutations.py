@@ -43,6 +43,13 @@ MUTANTS = [
     ("inclusive scan", "offsets[i] = acc;\n        acc += (uint64_t)counts[i];", "acc += (uint64_t)counts[i];\n        offsets[i] = acc;"),
     ("un-premultiply skipped", "cs[c] = A > 0.0 ? P[c] / A : 0.0;", "cs[c] = P[c];"),
     ("half exponent bias", "else v = ldexp((double)(1024 + m), e - 25);", "else v = ldexp((double)(1024 + m), e - 24);"),
+    ("render falling branch in list order", "const int k = rising ? t : n - 1 - t;", "const int k = t;"),
+    ("render opacity ignores thickness", "log1p(-Ar) * l / (b - f)", "log1p(-Ar) * l"),
+    ("render rows offset", "const double Yj = (1.0 - 2.0 * j / G.H) * G.th;",
+     "const double Yj = (1.0 - 2.0 * (j + 0.5) / G.H) * G.th;"),
+    ("render colour premultiplied twice", "(r[2 + c] / Ar) * alpha", "r[2 + c] * alpha"),
+    ("render no split at closest approach", "if (s_star > s_in && s_star < s_out) cut[nc++] = s_star;",
+     "if (0) cut[nc++] = s_star;"),
     ("split not near-equal", "boxes[e].hi[a] = (int)(((long)cells * (idx[a] + 1)) / g[a]);", "boxes[e].hi[a] = idx[a] + 1 == g[a] ? cells : boxes[e].lo[a] + cells / g[a] - (idx[a] == 0);"),
 ]
 
@@ -58,7 +65,8 @@ def _run(name, old, new, tmp):
     env = dict(os.environ, VDI_ORACLE_LIB=path_so, OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_invariants.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_invariants.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_render.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode
 
