@@ -363,6 +363,37 @@ def batched_eval(vdi, torch, stream, hbm_peak, warmup=1, steps=3, runs=1 << 22):
     return res
 
 
+def novel_view_eval(vdi, torch, stream, wl, frame0, reg, W, H, reps=5):
+    """Times vdi_render_view of the composited VDI of orbit view 0 from views rotated about the volume's
+    centre by 0 (the flatten from the generating view), 5, 20 and 50 degrees, 1920 x 1080 each."""
+    import dataclasses
+    import math
+
+    frame0()
+    gen = wl.cams[0]
+    img = torch.zeros((W * H, 4), dtype=torch.float32, device="cuda")
+    c = np.array(gen.center, float)
+    up = np.array(gen.up, float) / np.linalg.norm(gen.up)
+    gc = vdi.make_camera(gen)
+    times = {}
+    for theta in (0.0, 5.0, 20.0, 50.0):
+        e = np.array(gen.eye, float) - c
+        t = math.radians(theta)
+        e_rot = e * math.cos(t) + np.cross(up, e) * math.sin(t) + up * np.dot(up, e) * (1 - math.cos(t))
+        vc = vdi.make_camera(dataclasses.replace(gen, eye=tuple(c + e_rot))) if theta else None
+        vdi.check(vdi.vdi_render_view(reg.struct(), W, H, gc, vc, img.data_ptr(), stream), "view")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            vdi.check(vdi.vdi_render_view(reg.struct(), W, H, gc, vc, img.data_ptr(), stream), "view")
+        e1.record(stream)
+        stream.synchronize()
+        times[f"{theta:g}"] = round(e0.elapsed_time(e1) / reps, 3)
+    return {"vdi": f"{W}x{H}, N_S={wl.n_s}, orbit view 0", "ms_by_degrees": times,
+            "mpix_s_at_20": W * H / (times["20"] * 1e-3) / 1e6}
+
+
 def gen_traffic(wl):
     """DRAM bytes per gen_count_kernel launch from the committed ncu capture of this workload, or None when
     the workload differs or the kernel's sources changed since the capture."""
@@ -636,6 +667,11 @@ def main():
         e2e = {"value": npix * nsteps * world / (ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # rendering the last frame's composited VDI from other viewpoints (outside the timed region)
+    novel = None
+    if rank == 0:
+        novel = novel_view_eval(vdi, torch, stream, wl, lambda: frame(0), reg, W, H)
+
     learned = None
     if not args.no_learned and rank == 0:
         learned = learned_eval(vdi, torch, stream)
@@ -667,7 +703,7 @@ def main():
                               "bytes_per_frame": int(statistics.mean(comp_bytes)),
                               "census": _comp_census(vdi, comp_ctr), "schedule": comp_schedule,
                               "schedule_ms": sched_ms},
-                "composite_scale": scale, "composite_batched": batched,
+                "composite_scale": scale, "composite_batched": batched, "render_view": novel,
                 "gen": {"mrays_s": npix / (mean["choose_gamma"] + mean["scan+emit"] + mean["brick"]) / 1e3,
                         "sample_evals_per_frame": evals // args.steps,
                         "sm_steps_per_frame": steps_sm // args.steps, "tops": gen_tops,

@@ -398,12 +398,21 @@ vdi_status vdi_choose_gamma_learned(const vdi_brick* bricks, int32_t k, const fl
                                     const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream);
 
 /* ------------------------------------------------------------------------ */
-/* Rendering from the generating view (sec. 2.3: a VDI is exact from its    */
-/* viewpoint of generation by associativity of "over")                      */
+/* Rendering a regular VDI (sec. 2.3: exact from its viewpoint of           */
+/* generation by associativity of "over"; from other viewpoints the paper  */
+/* judges VDIs against DVR but does not restate the renderer)               */
 /* ------------------------------------------------------------------------ */
-/* Flattens the regular VDI front to back into rgba_out (device float4[w*h],
- * premultiplied).  `view` must be NULL or equal to `gen`; other views return
- * VDI_ERR_UNSUPPORTED. */
+/* `vdi` is w x h pixels of camera `gen`.  With `view` NULL or equal to
+ * `gen`: flattens each pixel's supersegments front to back into rgba_out
+ * (device float4[w*h], premultiplied).  With another `view`: renders the
+ * VDI as a view-dependent volume into rgba_out (device float4[view->width *
+ * view->height], premultiplied; gen->width == w and gen->height == h):
+ * pixel (i, j)'s frustum column (the points whose projection through gen's
+ * eye falls in the pixel's square) holds its supersegments, each filling the
+ * points at distance f..b from gen's eye with opacity 1 - (1 - A)^(l /
+ * (b - f)) over a path of length l (the length correction of Eq. 2) and
+ * straight colour P / A; each view ray is cut at column faces and shells
+ * and composited front to back.  Stream-ordered, no allocation. */
 vdi_status vdi_render_view(const vdi_regular* vdi, int32_t w, int32_t h, const vdi_camera* gen,
                            const vdi_camera* view, float* rgba_out, vdi_stream stream);
 

@@ -635,9 +635,16 @@ vdi_status vdi_render_view(const vdi_regular* vdi, int32_t w, int32_t h, const v
     if (!vdi || !rgba_out || !vdi->counts || !vdi->rgba || vdi->n_s < 1)
         return set_error(VDI_ERR_INVALID_ARG, "vdi_render_view: NULL argument");
     if (w < 0 || h < 0) return set_error(VDI_ERR_INVALID_ARG, "vdi_render_view: image size");
-    if (view && (!gen || memcmp(view, gen, sizeof(vdi_camera)) != 0))
-        return set_error(VDI_ERR_UNSUPPORTED, "vdi_render_view: only the generating view is implemented");
-    return launch_flatten(vdi, w, h, rgba_out, (cudaStream_t)stream);
+    if (!view || (gen && memcmp(view, gen, sizeof(vdi_camera)) == 0))
+        return launch_flatten(vdi, w, h, rgba_out, (cudaStream_t)stream);
+    if (!gen) return set_error(VDI_ERR_INVALID_ARG, "vdi_render_view: another view needs the generating camera");
+    if (gen->width != w || gen->height != h)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_render_view: the VDI is %d x %d, its camera %d x %d", w, h,
+                         gen->width, gen->height);
+    if (!camera_ok(gen) || !camera_ok(view))
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_render_view: camera");
+    if (vdi->prec == VDI_PREC_F32 && !vdi->fb) return set_error(VDI_ERR_INVALID_ARG, "vdi_render_view: fb NULL");
+    return launch_novel_view(vdi, *gen, *view, rgba_out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -85,6 +85,8 @@ size_t batched_workspace_bytes(const void* host_table);
 vdi_status launch_composite_batched(const void* dev_table, const void* host_table, int iters, unsigned int* status,
                                     void* workspace, size_t ws_bytes, cudaStream_t st);
 vdi_status launch_flatten(const vdi_regular* v, int w, int h, float* rgba, cudaStream_t st);
+vdi_status launch_novel_view(const vdi_regular* v, const vdi_camera& gen, const vdi_camera& view, float* rgba,
+                             cudaStream_t st);
 
 // learned gamma (learned.cu)
 size_t model_bytes();

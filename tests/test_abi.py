@@ -114,9 +114,10 @@ def test_argument_errors_before_launch(vdi):
     bad = vdi.vdi_compact(None, fake, fake, fake, None, 0, 0)
     assert vdi.vdi_composite([bad], 4, 4, reg, params, fake, 256) == vdi.VDI_ERR_INVALID_ARG
     assert vdi.vdi_composite([out], 4, 4, reg, params, None, 0) == vdi.VDI_ERR_WORKSPACE
-    # rendering from a different view is not implemented
+    # rendering from a different view: the VDI's size must be its camera's, and the camera is required
     view = vdi.vdi_camera((1, 0, -10), (0, 0, 0), (0, 1, 0), 45.0, 8, 8)
-    assert vdi.vdi_render_view(reg, 8, 8, cam, view, fake) == vdi.VDI_ERR_UNSUPPORTED
+    assert vdi.vdi_render_view(reg, cam.width + 1, cam.height, cam, view, fake) == vdi.VDI_ERR_INVALID_ARG
+    assert vdi.vdi_render_view(reg, 8, 8, None, view, fake) == vdi.VDI_ERR_INVALID_ARG
 
 
 def test_product_path_does_not_touch_oracle():
