@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-layout", action="store_true", help="skip the regular-vs-compact layout comparison")
     ap.add_argument("--no-scale", action="store_true", help="skip the 2048^2 K=32 dense compositing runs")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-request batched compositing run")
     ap.add_argument("--scale-size", type=int, default=2048, help="image side of the K=32 dense compositing run")
@@ -67,7 +68,6 @@ def parse():
 
 class Workload:
     def __init__(self, dims=512, W=1920, H=1080):
-        import oracle  # noqa: F401  (only for the decomposition check below in tests; not used here)
         import synth
 
         self.dims = (dims, dims, dims)
@@ -394,6 +394,103 @@ def novel_view_eval(vdi, torch, stream, wl, frame0, reg, W, H, reps=5):
             "mpix_s_at_20": W * H / (times["20"] * 1e-3) / 1e6}
 
 
+def layout_eval(vdi, torch, stream, wl, bricks, lut_d, cams, outs, params, params_c, wsg, wsc, reg, reps=3):
+    """Sub-VDIs generated in the regular layout (every list padded to N_S slots) against the compact
+    layout (count, prefix sum, emit), as in sec. 3.1's generation-time and memory comparison, and both
+    composited: the regular sub-VDIs are read through offsets p * N_S."""
+    W, H, n_s = wl.W, wl.H, wl.n_s
+    npix = W * H
+    k = len(outs)
+    regs = [vdi.Regular(npix, n_s, vdi.VDI_PREC_F32, outs[0].counts.device) for _ in range(k)]
+    rstructs = [r.struct() for r in regs]
+    ostructs = [o.struct() for o in outs]
+    # the regular sub-VDIs seen as compact lists with a fixed stride (the layout descriptor, built once)
+    stride_off = torch.arange(npix + 1, dtype=torch.int64, device=outs[0].counts.device) * n_s
+    rviews = [vdi.vdi_compact(r.counts.data_ptr(), stride_off.data_ptr(), r.rgba.data_ptr(), r.fb.data_ptr(),
+                              r.gamma.data_ptr(), npix * n_s, vdi.VDI_PREC_F32) for r in regs]
+    out_c = vdi.Regular(npix, n_s, vdi.VDI_PREC_F32, outs[0].counts.device)
+    out_r = vdi.Regular(npix, n_s, vdi.VDI_PREC_F32, outs[0].counts.device)
+    sc, sr = out_c.struct(), out_r.struct()
+
+    def timed(fn):
+        fn(0)
+        ms = []
+        for v in range(1, reps + 1):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(v)
+            b.record(stream)
+            stream.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.mean(ms)
+
+    def gen_c(v):
+        vdi.check(vdi.vdi_generate(bricks.bricks, lut_d.data_ptr(), cams[v], n_s, vdi.VDI_GAMMA_SEARCH, ostructs,
+                                   params, wsg.ptr, wsg.nbytes, stream), "generate compact")
+
+    def gen_r(v):
+        vdi.check(vdi.vdi_generate_regular(bricks.bricks, lut_d.data_ptr(), cams[v], n_s, vdi.VDI_GAMMA_SEARCH,
+                                           rstructs, params, wsg.ptr, wsg.nbytes, stream), "generate regular")
+
+    g_c = timed(gen_c)
+    g_r = timed(gen_r)
+    vdi.check(wsg.status(stream), "generate status")
+    records = sum(int(o.offsets[-1].item()) for o in outs)  # last view generated by both
+    # both layouts hold the same lists: composite each and compare the outputs
+    c_c = timed(lambda v: vdi.check(vdi.vdi_composite(ostructs, W, H, sc, params_c, wsc.ptr, wsc.nbytes, stream),
+                                    "composite compact"))
+    c_r = timed(lambda v: vdi.check(vdi.vdi_composite(rviews, W, H, sr, params_c, wsc.ptr, wsc.nbytes, stream),
+                                    "composite regular"))
+    vdi.check(wsc.status(stream), "composite status")
+    same = bool(torch.equal(out_c.counts, out_r.counts) and torch.equal(out_c.rgba, out_r.rgba)
+                and torch.equal(out_c.fb, out_r.fb))
+    bytes_r = k * npix * n_s * 24 + k * npix * 8
+    bytes_c = records * 24 + k * (npix + 1) * 8 + k * npix * 8
+    del regs, rviews, stride_off, out_c, out_r
+    torch.cuda.empty_cache()
+    return {"gen_ms": {"compact": round(g_c, 3), "regular": round(g_r, 3)},
+            "composite_ms": {"compact": round(c_c, 3), "regular": round(c_r, 3)},
+            "bytes": {"compact": bytes_c, "regular": bytes_r}, "memory_ratio": round(bytes_r / bytes_c, 3),
+            "records": records, "composites_identical": same, "views": reps}
+
+
+def ns_sweep_eval(vdi, torch, stream, wl, bricks, lut_d, cams, outs, params, wsg, wsc, values=(20, 25, 30),
+                  reps=3):
+    """Generation and compositing time of the plain frame at several N_S (supplementary Fig. S1 reports
+    generation rates at N_S = 20, 25, 30): compact sub-VDIs with the γ search, composited with the
+    default schedule choice into a regular VDI of the same N_S."""
+    W, H = wl.W, wl.H
+    npix = W * H
+    ostructs = [o.struct() for o in outs]
+    res = {}
+    for n_s in values:
+        out = vdi.Regular(npix, n_s, vdi.VDI_PREC_F32, outs[0].counts.device)
+        so = out.struct()
+        gen, comp = [], []
+        for v in range(reps + 1):
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            vdi.check(vdi.vdi_generate(bricks.bricks, lut_d.data_ptr(), cams[v], n_s, vdi.VDI_GAMMA_SEARCH, ostructs,
+                                       params, wsg.ptr, wsg.nbytes, stream), "generate")
+            b.record(stream)
+            vdi.check(vdi.vdi_composite(ostructs, W, H, so, params, wsc.ptr, wsc.nbytes, stream), "composite")
+            c.record(stream)
+            stream.synchronize()
+            if v:
+                gen.append(a.elapsed_time(b))
+                comp.append(b.elapsed_time(c))
+        vdi.check(wsg.status(stream), "generate status")
+        vdi.check(wsc.status(stream), "composite status")
+        records = sum(int(o.offsets[-1].item()) for o in outs)
+        g, cm = statistics.mean(gen), statistics.mean(comp)
+        res[str(n_s)] = {"gen_ms": round(g, 3), "composite_ms": round(cm, 3),
+                         "gen_mrays_s": round(npix / g / 1e3, 2), "records": records}
+        del out
+    torch.cuda.empty_cache()
+    return res
+
+
 def gen_traffic(wl):
     """DRAM bytes per gen_count_kernel launch from the committed ncu capture of this workload, or None when
     the workload differs or the kernel's sources changed since the capture."""
@@ -672,6 +769,11 @@ def main():
     if rank == 0:
         novel = novel_view_eval(vdi, torch, stream, wl, lambda: frame(0), reg, W, H)
 
+    layout = None
+    if rank == 0 and not args.no_layout:
+        layout = layout_eval(vdi, torch, stream, wl, bricks, lut_d, cams, outs, params, params_c, wsg, wsc, reg)
+        layout["n_s_sweep"] = ns_sweep_eval(vdi, torch, stream, wl, bricks, lut_d, cams, outs, params, wsg, wsc)
+
     learned = None
     if not args.no_learned and rank == 0:
         learned = learned_eval(vdi, torch, stream)
@@ -704,6 +806,7 @@ def main():
                               "census": _comp_census(vdi, comp_ctr), "schedule": comp_schedule,
                               "schedule_ms": sched_ms},
                 "composite_scale": scale, "composite_batched": batched, "render_view": novel,
+                "layout": layout,
                 "gen": {"mrays_s": npix / (mean["choose_gamma"] + mean["scan+emit"] + mean["brick"]) / 1e3,
                         "sample_evals_per_frame": evals // args.steps,
                         "sm_steps_per_frame": steps_sm // args.steps, "tops": gen_tops,

@@ -223,6 +223,16 @@ vdi_status vdi_choose_gamma(const vdi_brick* bricks, int32_t k, const float* tf_
 vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
                         int32_t n_s, float gamma, vdi_compact* out, const vdi_params* params, void* workspace,
                         size_t ws_bytes, vdi_stream stream);
+/* Sub-VDIs in the regular layout instead (sec. 4: the layout earlier VDI
+ * generation used; Table 1 compares its generation time and memory with the
+ * compact layout's):
+ * out[e] (k descriptors, n_s slots per pixel, one precision) receives PE e's
+ * counts, gamma and records at p * n_s with a zero tail.  No prefix sum and
+ * no capacity question: every pixel owns n_s slots.  gamma as for
+ * vdi_generate, except VDI_GAMMA_CHOSEN.  Workspace as vdi_generate. */
+vdi_status vdi_generate_regular(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
+                                int32_t n_s, float gamma, vdi_regular* out, const vdi_params* params,
+                                void* workspace, size_t ws_bytes, vdi_stream stream);
 
 /* Generation for callers that cannot allocate device memory (an in-situ
  * simulation that reserves its whole device budget at start-up, a plugin with

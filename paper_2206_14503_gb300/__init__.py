@@ -93,6 +93,7 @@ def _load():
         "vdi_choose_gamma": ([vp, i32, vp, vp, i32, f32, vp, vp, vp, sz, vp], i32),
         "vdi_generate": ([vp, i32, vp, vp, i32, f32, vp, vp, vp, sz, vp], i32),
         "vdi_generate_static_scratch": ([vp, i32, vp, vp, i32, f32, vp, vp, vp], i32),
+        "vdi_generate_regular": ([vp, i32, vp, vp, i32, f32, vp, vp, vp, sz, vp], i32),
         "vdi_composite_workspace": ([i32, i32, i32, i32], sz),
         "vdi_composite": ([vp, i32, i32, i32, vp, vp, vp, sz, vp], i32),
         "vdi_render_view": ([vp, i32, i32, vp, vp, vp, vp], i32),
@@ -128,7 +129,7 @@ _lib = _load()
 SYMBOLS = ("vdi_version", "vdi_status_string", "vdi_last_error", "vdi_workspace_status", "vdi_workspace_counters",
            "vdi_split_boxes",
            "vdi_brick_bytes", "vdi_brick_build", "vdi_generate_workspace", "vdi_choose_gamma", "vdi_generate",
-           "vdi_generate_static_scratch",
+           "vdi_generate_static_scratch", "vdi_generate_regular",
            "vdi_composite_workspace", "vdi_composite", "vdi_render_view", "vdi_batch_table_bytes",
            "vdi_batch_table_pack", "vdi_composite_batched_workspace", "vdi_composite_batched", "vdi_composite_autotune",
            "vdi_model_bytes", "vdi_model_nparams", "vdi_model_init", "vdi_model_save", "vdi_model_load",
@@ -224,6 +225,14 @@ def vdi_choose_gamma(bricks, lut_ptr, cam: vdi_camera, n_s, gamma, outs, params:
     oarr = (vdi_compact * k)(*outs)
     return _lib.vdi_choose_gamma(_arr(bricks), k, C.c_void_p(lut_ptr), _ref(cam), n_s, gamma, _arr(oarr),
                                  _ref(params), C.c_void_p(ws_ptr), ws_bytes, _stream(stream))
+
+
+def vdi_generate_regular(bricks, lut_ptr, cam: vdi_camera, n_s, gamma, outs, params: vdi_params, ws_ptr, ws_bytes,
+                         stream=None) -> int:
+    k = len(outs)
+    oarr = (vdi_regular * k)(*outs)
+    return _lib.vdi_generate_regular(_arr(bricks), k, C.c_void_p(lut_ptr), _ref(cam), n_s, gamma, _arr(oarr),
+                                     _ref(params), C.c_void_p(ws_ptr), ws_bytes, _stream(stream))
 
 
 def vdi_generate(bricks, lut_ptr, cam: vdi_camera, n_s, gamma, outs, params: vdi_params, ws_ptr, ws_bytes,

@@ -329,6 +329,52 @@ vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut,
                            out[0].prec, od, status, st);
 }
 
+vdi_status vdi_generate_regular(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
+                                int32_t n_s, float gamma, vdi_regular* out, const vdi_params* params,
+                                void* workspace, size_t ws_bytes, vdi_stream stream) {
+    if (!out) return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_regular: NULL argument");
+    vdi_compact tmp[VDI_MAX_PE];
+    const int kk = (k >= 1 && k <= VDI_MAX_PE) ? k : 0;
+    for (int e = 0; e < kk; ++e)
+        tmp[e] = vdi_compact{out[e].counts, nullptr, out[e].rgba, out[e].fb, out[e].gamma, 0, out[e].prec};
+    vdi_status s = gen_common("vdi_generate_regular", bricks, k, tf_lut, cam, n_s, gamma, kk ? tmp : nullptr, params,
+                              workspace, ws_bytes, false);
+    if (s != VDI_OK) return s;
+    if (gamma == VDI_GAMMA_CHOSEN) return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_regular: gamma mode");
+    for (int e = 0; e < k; ++e) {
+        const vdi_regular& o = out[e];
+        if (o.n_s != n_s) return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_regular: out[%d].n_s != n_s", e);
+        if ((o.prec != VDI_PREC_F32 && o.prec != VDI_PREC_F16) || o.prec != out[0].prec)
+            return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_regular: out[%d].prec", e);
+        if (!o.rgba || (o.prec == VDI_PREC_F32 && !o.fb))
+            return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_regular: out[%d] record arrays NULL", e);
+        if ((reinterpret_cast<uintptr_t>(o.rgba) & 15) || (reinterpret_cast<uintptr_t>(o.fb) & 7))
+            return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_regular: out[%d] record arrays misaligned", e);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int* status = reinterpret_cast<unsigned int*>(workspace);
+    s = cuda_check(cudaMemsetAsync(status, 0, kGenFixed, st), "status clear");
+    if (s != VDI_OK) return s;
+    const uint64_t slots = (uint64_t)cam->width * (uint64_t)cam->height * (uint64_t)n_s;
+    BrickDev bd[VDI_MAX_PE];
+    CompactDev od[VDI_MAX_PE];
+    for (int e = 0; e < k; ++e) {
+        bd[e] = brick_dev(bricks[e]);
+        od[e] = CompactDev{out[e].counts, nullptr, out[e].rgba, reinterpret_cast<float*>(out[e].fb), out[e].gamma,
+                           slots};
+    }
+    CamDev cd = make_cam(*cam);
+    float scale255 = (float)(255.0 * (double)bricks[0].value_scale);
+    const size_t fixed = gen_min_workspace(k, cam->width, cam->height);
+    char* ws = static_cast<char*>(workspace);
+    s = launch_gen_count(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s, gamma,
+                         params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0,
+                         reinterpret_cast<unsigned int*>(ws + kWsHeader), ws + fixed, ws_bytes - fixed, st);
+    if (s != VDI_OK) return s;
+    return launch_gen_emit(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s,
+                           out[0].prec, od, status, st, true);
+}
+
 size_t vdi_composite_workspace(int32_t k, int32_t w, int32_t h, int32_t n_s) {
     (void)k; (void)n_s;
     if (w < 0 || h < 0) return 0;

@@ -50,6 +50,7 @@ struct GenArgs {
     float4* cache_a;        // sample cache: [cap][slots] (P.rgb, a)
     float2* cache_b;        // [cap][slots] (log2(1 - a), transparent samples before it)
     int cache_cap, slots;
+    int regular;  // emit: records of pixel p at p * n_s with a zero tail (regular layout), no offsets
 };
 
 constexpr int kTileW = 16, kTileH = 8, kGenThreads = 128;
@@ -522,19 +523,33 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_c
     const CompactDev& o = a.out[e];
     const size_t p = (size_t)j * a.cam.W + i;
     const uint32_t want = o.counts[p];
-    if (want == 0) return;
+    // regular layout: a pixel owns n_s slots (counts never exceed n_s for box-shaped domains)
+    const uint32_t room = a.regular ? min(want, (uint32_t)a.n_s) : want;
+    const uint64_t base = a.regular ? (uint64_t)p * (uint64_t)a.n_s : o.offsets[p];
+    uint32_t written = 0;
+    // regular layout: the slots after the pixel's records are zero
+    auto zero_tail = [&]() {
+        if (!a.regular) return;
+        const RecOut z{0.f, 0.f, {0.f, 0.f, 0.f}, 0.f};
+        for (uint32_t q = min(written, (uint32_t)a.n_s); q < (uint32_t)a.n_s; ++q) store_record(a, o, base + q, z);
+    };
+    if (want == 0) {
+        zero_tail();
+        return;
+    }
     Ray r;
     int k0 = 0, k1 = 0;
-    if (!(ray_setup(a.cam, i, j, a.dims, a.step, r) && owned_range(r, a.step, b, a.dims, k0, k1))) return;
+    if (!(ray_setup(a.cam, i, j, a.dims, a.step, r) && owned_range(r, a.step, b, a.dims, k0, k1))) {
+        zero_tail();
+        return;
+    }
     const float gamma = o.gamma ? o.gamma[p] : a.gamma;
     const float g2 = __fmul_rn(gamma, gamma);
-    const uint64_t base = o.offsets[p];
     const int cap = a.n_s;
     // the GenCount state machine (same decisions), tracking the records
     GenCount st;
     gc_reset(st);
     int kopen = 0, klast = 0;
-    uint32_t written = 0;
     march(r, k0, k1, b, lut2, a.scale255, [&](int k, const Sample& s) {
         const bool was_open = st.m != 0.f;
         const int before = st.cnt;
@@ -544,7 +559,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_c
         // S closed by this sample: either it was shut (m = 0) or a new one opened
         const bool closed = was_open && (st.m == 0.f || st.cnt != before);
         if (closed) {
-            if (written < want) store_record(a, o, base + written, cur);
+            if (written < room) store_record(a, o, base + written, cur);
             ++written;
         }
         if (st.cnt != before) {
@@ -555,7 +570,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_c
         }
     });
     if (st.m != 0.f) {
-        if (written < want) {
+        if (written < room) {
             RecOut ro{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1), {st.P[0], st.P[1], st.P[2]},
                       st.A};
             store_record(a, o, base + written, ro);
@@ -563,6 +578,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_c
         ++written;
     }
     if (written != want) atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CUDA);
+    zero_tail();
 }
 
 static void fill_args(GenArgs& a, const BrickDev* bricks, int k, const float* lut, const CamDev& cam,
@@ -588,6 +604,7 @@ static void fill_args(GenArgs& a, const BrickDev* bricks, int k, const float* lu
     a.cache_b = nullptr;
     a.cache_cap = 0;
     a.slots = 0;
+    a.regular = 0;
 }
 
 // persistent grid of gen_count_kernel on the current device
@@ -647,9 +664,10 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
 
 vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                            float scale255, float step, float ref_len, int n_s, int prec, const CompactDev* out,
-                           unsigned int* status, cudaStream_t st) {
+                           unsigned int* status, cudaStream_t st, bool regular) {
     GenArgs a;
     fill_args(a, bricks, k, lut, cam, dims, scale255, step, ref_len, n_s, out, status);
+    a.regular = regular ? 1 : 0;
     a.iters = 0;
     a.gamma = 0.f;
     a.mode = 0;

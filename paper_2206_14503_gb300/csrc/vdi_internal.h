@@ -70,7 +70,7 @@ constexpr size_t kGenFixed = 512;
 constexpr float kGammaLearnedBracket = -5.0f;
 vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                            float scale255, float step, float ref_len, int n_s, int prec, const CompactDev* out,
-                           unsigned int* status, cudaStream_t st);
+                           unsigned int* status, cudaStream_t st, bool regular = false);
 size_t scan_workspace(int k, int n);
 vdi_status launch_scan(int k, int n, uint32_t* const* counts, uint64_t* const* offsets, void* ws, cudaStream_t st);
 

@@ -107,6 +107,20 @@ def test_argument_errors_before_launch(vdi):
     bricks[0].dims[:] = [4, 4, 4]
     bricks[0].value_scale = 1.0
     assert vdi.vdi_generate(bricks, fake, cam, 4, -1.0, [out], params, fake, 16) == vdi.VDI_ERR_WORKSPACE
+    # regular generation: the output's N_S must be the call's, records present and aligned, no chosen-γ mode
+    rout = vdi.vdi_regular(fake, fake, fake, fake, 4, 0)
+    assert vdi.vdi_generate_regular(bricks, fake, cam, 5, -1.0, [rout], params, fake,
+                                    1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    assert "n_s" in vdi.last_error()
+    assert vdi.vdi_generate_regular(bricks, fake, cam, 4, vdi.VDI_GAMMA_CHOSEN, [rout], params, fake,
+                                    1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    rout.rgba = fake + 4
+    assert vdi.vdi_generate_regular(bricks, fake, cam, 4, -1.0, [rout], params, fake,
+                                    1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    assert "misaligned" in vdi.last_error()
+    rout.rgba, rout.fb = fake, None
+    assert vdi.vdi_generate_regular(bricks, fake, cam, 4, -1.0, [rout], params, fake,
+                                    1 << 20) == vdi.VDI_ERR_INVALID_ARG
     # composite: n_s < 1, missing arrays
     reg = vdi.vdi_regular(fake, fake, fake, None, 0, 0)
     assert vdi.vdi_composite([out], 4, 4, reg, params, fake, 256) == vdi.VDI_ERR_INVALID_ARG

@@ -154,3 +154,53 @@ def test_plain_config_sampled_rays():
     ref = oracle.dvr(vol, lut, cam, 0.5, 1.0, pixels=pix)
     err = np.abs(g["image"][pix] - ref).max()
     assert err <= GEN_TOL_512, err
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("gamma_mode", ["search", "fixed"])
+def test_generate_regular_equals_compact(tiny_workload, prec, gamma_mode):
+    # generation straight into the regular layout (sec. 3.1) writes the records compact generation
+    # writes, at pixel * n_s, with zeroed slots past each count
+    import torch
+
+    import paper_2206_14503_gb300 as vdi
+    from gpu_run import to_dev
+
+    w = tiny_workload
+    cam = w["cams"][4]
+    gamma = -1.0 if gamma_mode == "search" else w["gamma"]
+    n_s = w["n_s"]
+    lists, gam = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, n_s, gamma, step=w["step"], prec=prec)
+    npix = cam.width * cam.height
+    vb = [vdi.vdi_box(tuple(lo), tuple(hi)) for lo, hi in w["boxes"]]
+    br = vdi.Bricks(to_dev(w["vol"]), w["dims"], vb)
+    outs = [vdi.Regular(npix, n_s, prec) for _ in vb]
+    for o in outs:  # poison: every slot must be written
+        o.rgba.fill_(-7)
+        if o.fb is not None:
+            o.fb.fill_(-7.0)
+    ws = vdi.Workspace(vdi.vdi_generate_workspace(len(vb), cam.width, cam.height))
+    lut_d = to_dev(w["lut"].astype(np.float32))
+    vdi.check(vdi.vdi_generate_regular(br.bricks, lut_d.data_ptr(), vdi.make_camera(cam), n_s, gamma,
+                                       [o.struct() for o in outs], vdi.make_params(step=w["step"]), ws.ptr,
+                                       ws.nbytes), "vdi_generate_regular")
+    vdi.check(ws.status(), "generate status")
+    torch.cuda.synchronize()
+    for e, o in enumerate(outs):
+        c, off, fb_c, rgba_c, _ = lists[e]
+        cnt = o.counts.cpu().numpy().astype(np.uint32)
+        assert np.array_equal(cnt, c)
+        assert np.array_equal(o.gamma.cpu().numpy(), gam[e])
+        if prec == 0:
+            fb_r = o.fb.view(npix, n_s, 2).cpu().numpy()
+            raw_r = o.rgba.view(npix, n_s, 4).cpu().numpy()
+        else:
+            raw = o.rgba.view(npix, n_s, 4).cpu().numpy()
+            fb_r = raw[..., 0:2].copy().view(np.float32)
+            raw_r = raw[..., 2:4].copy().view(np.float16).astype(np.float32)
+        slot = np.arange(n_s)[None, :] < cnt[:, None].astype(np.int64)
+        idx = off[:-1].astype(np.int64)[:, None] + np.arange(n_s)[None, :]
+        idx = np.where(slot, idx, 0)
+        assert np.array_equal(np.where(slot[..., None], fb_r, 0), np.where(slot[..., None], fb_c[idx], 0))
+        assert np.array_equal(np.where(slot[..., None], raw_r, 0), np.where(slot[..., None], rgba_c[idx], 0))
+        assert not np.any(fb_r[~slot]) and not np.any(raw_r[~slot])
