@@ -219,7 +219,9 @@ vdi_status vdi_choose_gamma(const vdi_brick* bricks, int32_t k, const float* tf_
  * Records of a list are in depth order, at most n_s per list for box-shaped
  * domains.  If a PE's total exceeds out[e].capacity, no record past the
  * capacity is written and VDI_ERR_CAPACITY is reported through the workspace
- * status (or returned, with offsets valid, under VDI_FLAG_SYNC_CAPACITY). */
+ * status (or returned, with offsets valid, under VDI_FLAG_SYNC_CAPACITY); in
+ * the first case the counts of the lists the capacity cuts are reduced to the
+ * records written, so the sub-VDI remains valid input for vdi_composite. */
 vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
                         int32_t n_s, float gamma, vdi_compact* out, const vdi_params* params, void* workspace,
                         size_t ws_bytes, vdi_stream stream);
@@ -425,6 +427,76 @@ vdi_status vdi_choose_gamma_learned(const vdi_brick* bricks, int32_t k, const fl
  * and composited front to back.  Stream-ordered, no allocation. */
 vdi_status vdi_render_view(const vdi_regular* vdi, int32_t w, int32_t h, const vdi_camera* gen,
                            const vdi_camera* view, float* rgba_out, vdi_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Frame pipeline (sec. 7: sub-VDI generation of the next VDI overlaps the   */
+/* final gather of the previous one).  On one GPU the final gather is the    */
+/* device-to-host copy of the composited regular VDI; the pipeline also     */
+/* overlaps the host-to-device copy of the next time step's volume.          */
+/* ------------------------------------------------------------------------ */
+/* Per frame: volume upload (copy-in stream), brick build, generation and
+ * compositing (compute stream), regular-VDI download (copy-out stream).  The
+ * volume and the regular VDI are double-buffered in device memory, so frame
+ * f + 1's upload and generation run while frame f's download is in flight.
+ * Results equal those of vdi_brick_build, vdi_generate and vdi_composite
+ * called in order on one stream, bit for bit. */
+typedef struct vdi_pipeline vdi_pipeline; /* opaque, host-side */
+
+typedef struct {
+    int32_t dims[3];      /* nodes of the volume per axis */
+    int32_t type;         /* vdi_voltype of the uploaded volumes */
+    int32_t k;            /* PEs, 1..VDI_MAX_PE */
+    vdi_box boxes[VDI_MAX_PE]; /* the PEs' cells (first k used) */
+    int32_t width, height;
+    int32_t n_s;          /* supersegments per list, sub-VDIs and output */
+    int32_t prec;         /* vdi_precision of the sub-VDIs and the output */
+    float gamma;          /* VDI_GAMMA_SEARCH or a fixed gamma >= 0 */
+    uint64_t capacity;    /* records per PE sub-VDI; 0: width * height * n_s
+                             (always enough for box-shaped domains) */
+    vdi_params params;    /* schedule 0: autotuned on the first frame */
+} vdi_pipeline_desc;
+
+/* Device bytes of the arena a pipeline with this description needs (two
+ * volumes, the k bricks, the k compact sub-VDIs, two regular VDIs, the
+ * generation and compositing workspaces).  0 for an invalid description. */
+size_t vdi_pipeline_arena_bytes(const vdi_pipeline_desc* desc);
+/* Creates a pipeline on the current device.  arena: caller-allocated device
+ * memory of vdi_pipeline_arena_bytes(desc) bytes, 256-byte aligned, owned by
+ * the caller and used until vdi_pipeline_destroy.  tf_lut (device
+ * float[256*4]) is copied into the arena.  The pipeline creates three
+ * non-blocking streams, its events and a small page-locked status mirror;
+ * *out receives the handle.  One host thread at a time may use a pipeline. */
+vdi_status vdi_pipeline_create(const vdi_pipeline_desc* desc, void* arena, size_t arena_bytes, const float* tf_lut,
+                               vdi_pipeline** out);
+/* Submits one frame and returns without waiting for it, once the frame two
+ * submissions back has completed (at most two frames in flight; that
+ * frame's status is then held for vdi_pipeline_wait).
+ *   volume: HOST pointer to the frame's volume (dims, type), or NULL to keep
+ *     the previous frame's volume and bricks (a camera-only frame; invalid on
+ *     the first frame).  Read until the frame's upload has run: keep it
+ *     unchanged until vdi_pipeline_wait(ticket) returns.
+ *   cam: the frame's camera (width x height of the description), copied.
+ *   dst: HOST buffers receiving the regular VDI (counts[W*H], rgba and, for
+ *     FP32, fb of W*H*n_s records; gamma[W*H] if non-NULL); n_s and prec must
+ *     be the description's.  Written asynchronously; valid after
+ *     vdi_pipeline_wait(ticket).
+ *   ticket: receives the frame's number (0, 1, 2, ...).
+ * Host buffers should be page-locked: pageable copies do not overlap. */
+vdi_status vdi_pipeline_submit(vdi_pipeline* pl, const void* volume, const vdi_camera* cam, const vdi_regular* dst,
+                               uint64_t* ticket);
+/* Waits for frame `ticket` (and all frames before it) and returns its status:
+ * the status words the generation and compositing kernels left for that
+ * frame (VDI_ERR_CAPACITY when a sub-VDI overflowed its capacity), or the
+ * error of a CUDA call.  A ticket not yet submitted is VDI_ERR_INVALID_ARG.
+ * For a ticket older than the last two, the first error of any earlier
+ * frame is returned (VDI_OK if none). */
+vdi_status vdi_pipeline_wait(vdi_pipeline* pl, uint64_t ticket);
+/* The pipeline's copy-in, compute and copy-out streams (streams[3], host),
+ * for ordering other work or timing events against the pipeline. */
+vdi_status vdi_pipeline_streams(const vdi_pipeline* pl, vdi_stream streams[3]);
+/* Waits for every submitted frame and releases the streams, events and
+ * status mirror.  The arena is the caller's to free afterwards. */
+vdi_status vdi_pipeline_destroy(vdi_pipeline* pl);
 
 #ifdef __cplusplus
 }

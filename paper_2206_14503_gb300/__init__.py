@@ -60,6 +60,12 @@ class vdi_brick(C.Structure):
     _fields_ = [("cells", C.c_void_p), ("owned", vdi_box), ("dims", C.c_int32 * 3), ("value_scale", C.c_float)]
 
 
+class vdi_pipeline_desc(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("type", C.c_int32), ("k", C.c_int32), ("boxes", vdi_box * 64),
+                ("width", C.c_int32), ("height", C.c_int32), ("n_s", C.c_int32), ("prec", C.c_int32),
+                ("gamma", C.c_float), ("capacity", C.c_uint64), ("params", vdi_params)]
+
+
 class vdi_compact(C.Structure):
     _fields_ = [("counts", C.c_void_p), ("offsets", C.c_void_p), ("rgba", C.c_void_p), ("fb", C.c_void_p),
                 ("gamma", C.c_void_p), ("capacity", C.c_uint64), ("prec", C.c_int32)]
@@ -115,6 +121,12 @@ def _load():
         "vdi_mlp_train_step": ([vp, vp, vp, vp, i32, f32, vp, vp, sz, vp], i32),
         "vdi_learned_workspace": ([i32, i32, i32], sz),
         "vdi_choose_gamma_learned": ([vp, i32, vp, vp, i32, vp, f32, vp, vp, vp, sz, vp], i32),
+        "vdi_pipeline_arena_bytes": ([vp], sz),
+        "vdi_pipeline_create": ([vp, vp, sz, vp, vp], i32),
+        "vdi_pipeline_submit": ([vp, vp, vp, vp, vp], i32),
+        "vdi_pipeline_wait": ([vp, C.c_uint64], i32),
+        "vdi_pipeline_streams": ([vp, vp], i32),
+        "vdi_pipeline_destroy": ([vp], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -134,7 +146,9 @@ SYMBOLS = ("vdi_version", "vdi_status_string", "vdi_last_error", "vdi_workspace_
            "vdi_batch_table_pack", "vdi_composite_batched_workspace", "vdi_composite_batched", "vdi_composite_autotune",
            "vdi_model_bytes", "vdi_model_nparams", "vdi_model_init", "vdi_model_save", "vdi_model_load",
            "vdi_tile_features", "vdi_tile_labels", "vdi_mlp_infer", "vdi_mlp_train_workspace", "vdi_mlp_grad",
-           "vdi_mlp_train_step", "vdi_learned_workspace", "vdi_choose_gamma_learned")
+           "vdi_mlp_train_step", "vdi_learned_workspace", "vdi_choose_gamma_learned",
+           "vdi_pipeline_arena_bytes", "vdi_pipeline_create", "vdi_pipeline_submit", "vdi_pipeline_wait",
+           "vdi_pipeline_streams", "vdi_pipeline_destroy")
 
 
 def lib():
@@ -386,6 +400,39 @@ def vdi_render_view(vdi: vdi_regular, w, h, gen: vdi_camera, view, rgba_ptr, str
                                 C.c_void_p(rgba_ptr), _stream(stream))
 
 
+def vdi_pipeline_arena_bytes(desc: vdi_pipeline_desc) -> int:
+    return _lib.vdi_pipeline_arena_bytes(_ref(desc))
+
+
+def vdi_pipeline_create(desc: vdi_pipeline_desc, arena_ptr: int, arena_bytes: int, lut_ptr: int):
+    """Returns (status, handle)."""
+    h = C.c_void_p()
+    st = _lib.vdi_pipeline_create(_ref(desc), C.c_void_p(arena_ptr), arena_bytes, C.c_void_p(lut_ptr), C.byref(h))
+    return st, h
+
+
+def vdi_pipeline_submit(handle, volume_host_ptr, cam: vdi_camera, dst: vdi_regular):
+    """volume_host_ptr: host address or None.  Returns (status, ticket)."""
+    t = C.c_uint64()
+    st = _lib.vdi_pipeline_submit(handle, None if volume_host_ptr is None else C.c_void_p(volume_host_ptr), _ref(cam),
+                                  _ref(dst), C.byref(t))
+    return st, t.value
+
+
+def vdi_pipeline_wait(handle, ticket: int) -> int:
+    return _lib.vdi_pipeline_wait(handle, ticket)
+
+
+def vdi_pipeline_streams(handle):
+    out = (C.c_void_p * 3)()
+    check(_lib.vdi_pipeline_streams(handle, _arr(out)), "vdi_pipeline_streams")
+    return [int(x or 0) for x in out]
+
+
+def vdi_pipeline_destroy(handle) -> int:
+    return _lib.vdi_pipeline_destroy(handle)
+
+
 # --------------------------------------------------------------------------
 # torch conveniences (buffer allocation and struct filling)
 # --------------------------------------------------------------------------
@@ -515,3 +562,85 @@ class Workspace:
 
     def status(self, stream=None) -> int:
         return vdi_workspace_status(self.ptr, stream)
+
+
+class HostRegular:
+    """Page-locked host buffers of one regular VDI (a pipeline's destination) and their C struct."""
+
+    def __init__(self, npix: int, n_s: int, prec: int = VDI_PREC_F32, gamma: bool = True):
+        import torch
+
+        self.npix, self.n_s, self.prec = npix, n_s, prec
+        self.counts = torch.zeros(npix, dtype=torch.int32).pin_memory()
+        self.gamma = torch.zeros(npix, dtype=torch.float32).pin_memory() if gamma else None
+        if prec == VDI_PREC_F32:
+            self.rgba = torch.zeros((npix * n_s, 4), dtype=torch.float32).pin_memory()
+            self.fb = torch.zeros((npix * n_s, 2), dtype=torch.float32).pin_memory()
+        else:
+            self.rgba = torch.zeros((npix * n_s, 4), dtype=torch.int32).pin_memory()
+            self.fb = None
+
+    def struct(self) -> vdi_regular:
+        return vdi_regular(self.counts.data_ptr(), self.rgba.data_ptr(),
+                           None if self.fb is None else self.fb.data_ptr(),
+                           None if self.gamma is None else self.gamma.data_ptr(), self.n_s, self.prec)
+
+    def nbytes(self) -> int:
+        n = self.counts.numel() * 4 + self.rgba.numel() * 4
+        if self.fb is not None:
+            n += self.fb.numel() * 4
+        if self.gamma is not None:
+            n += self.gamma.numel() * 4
+        return n
+
+
+class Pipeline:
+    """A frame pipeline (vdi_pipeline_*) with its device arena allocated by torch."""
+
+    def __init__(self, dims, voltype, boxes, width, height, n_s, lut, prec=VDI_PREC_F32, gamma=VDI_GAMMA_SEARCH,
+                 capacity=0, params=None, device="cuda"):
+        import torch
+
+        d = vdi_pipeline_desc()
+        d.dims[:] = [int(x) for x in dims]
+        d.type = voltype
+        d.k = len(boxes)
+        for e, b in enumerate(boxes):
+            d.boxes[e] = b
+        d.width, d.height, d.n_s, d.prec = width, height, n_s, prec
+        d.gamma = gamma
+        d.capacity = capacity
+        d.params = params if params is not None else make_params()
+        self.desc = d
+        nbytes = vdi_pipeline_arena_bytes(d)
+        if nbytes == 0:
+            raise VdiError(VDI_ERR_INVALID_ARG, f"vdi_pipeline_arena_bytes: {last_error()}")
+        self.arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.arena.data_ptr()
+        self.arena_ptr = (base + 255) // 256 * 256
+        self.lut = lut if lut.is_cuda else lut.to(device)
+        st, self.handle = vdi_pipeline_create(d, self.arena_ptr, nbytes, self.lut.data_ptr())
+        check(st, "vdi_pipeline_create")
+
+    def submit(self, volume_host, cam: vdi_camera, dst: HostRegular) -> int:
+        st, t = vdi_pipeline_submit(self.handle, None if volume_host is None else volume_host.data_ptr(), cam,
+                                    dst.struct())
+        check(st, "vdi_pipeline_submit")
+        return t
+
+    def wait(self, ticket: int):
+        check(vdi_pipeline_wait(self.handle, ticket), "vdi_pipeline_wait")
+
+    def streams(self):
+        return vdi_pipeline_streams(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            check(vdi_pipeline_destroy(self.handle), "vdi_pipeline_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

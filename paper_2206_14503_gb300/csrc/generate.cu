@@ -523,9 +523,16 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_c
     const CompactDev& o = a.out[e];
     const size_t p = (size_t)j * a.cam.W + i;
     const uint32_t want = o.counts[p];
-    // regular layout: a pixel owns n_s slots (counts never exceed n_s for box-shaped domains)
-    const uint32_t room = a.regular ? min(want, (uint32_t)a.n_s) : want;
     const uint64_t base = a.regular ? (uint64_t)p * (uint64_t)a.n_s : o.offsets[p];
+    // regular layout: a pixel owns n_s slots (counts never exceed n_s for box-shaped domains)
+    uint32_t room = a.regular ? min(want, (uint32_t)a.n_s) : want;
+    if (!a.regular && base + want > o.capacity) {
+        // a list cut by the capacity keeps the records that fit as its count, so the
+        // sub-VDI stays valid input for compositing; the status reports the overflow
+        room = base >= o.capacity ? 0u : (uint32_t)(o.capacity - base);
+        o.counts[p] = room;
+        atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CAPACITY);
+    }
     uint32_t written = 0;
     // regular layout: the slots after the pixel's records are zero
     auto zero_tail = [&]() {

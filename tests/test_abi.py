@@ -142,3 +142,64 @@ def test_product_path_does_not_touch_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.replace("oracle is", ""), f
+
+
+def _pipeline_desc(vdi):
+    d = vdi.vdi_pipeline_desc()
+    d.dims[:] = [33, 17, 9]
+    d.type = vdi.VDI_VOL_U16
+    boxes = vdi.vdi_split_boxes((33, 17, 9), (2, 1, 1))
+    d.k = 2
+    d.boxes[0], d.boxes[1] = boxes
+    d.width, d.height, d.n_s, d.prec = 40, 30, 6, vdi.VDI_PREC_F32
+    d.gamma = vdi.VDI_GAMMA_SEARCH
+    d.params = vdi.make_params()
+    return d
+
+
+def test_pipeline_arena_layout(vdi):
+    # the arena holds two volumes, the bricks, the sub-VDIs at full capacity, two regular VDIs and
+    # both workspaces; an invalid description gives 0
+    d = _pipeline_desc(vdi)
+    n = vdi.vdi_pipeline_arena_bytes(d)
+    npix, slots = 40 * 30, 40 * 30 * 6
+    need = 2 * 33 * 17 * 9 * 2 + sum(vdi.vdi_brick_bytes(d.boxes[e]) for e in range(2)) + 4096
+    need += 2 * (npix * 4 + (npix + 1) * 8 + npix * 4 + slots * 24) + 2 * (npix * 8 + slots * 24)
+    need += vdi.vdi_generate_workspace(2, 40, 30) + vdi.vdi_composite_workspace(2, 40, 30, 6)
+    assert need <= n <= need + 256 * 40
+    d.capacity = 100
+    assert vdi.vdi_pipeline_arena_bytes(d) < n
+    d16 = _pipeline_desc(vdi)
+    d16.prec = vdi.VDI_PREC_F16
+    assert vdi.vdi_pipeline_arena_bytes(d16) < n
+    for field, bad in [("k", 0), ("n_s", 0), ("prec", 2), ("gamma", -3.0), ("type", 5), ("width", 0)]:
+        b = _pipeline_desc(vdi)
+        setattr(b, field, bad)
+        assert vdi.vdi_pipeline_arena_bytes(b) == 0, field
+    b = _pipeline_desc(vdi)
+    b.boxes[1] = vdi.vdi_box((0, 0, 0), (33, 16, 8))  # past the last cell
+    assert vdi.vdi_pipeline_arena_bytes(b) == 0
+    b = _pipeline_desc(vdi)
+    b.params = vdi.make_params(schedule=5)
+    assert vdi.vdi_pipeline_arena_bytes(b) == 0
+
+
+def test_pipeline_argument_errors(vdi):
+    # every one of these fails on the host, before any CUDA call
+    d = _pipeline_desc(vdi)
+    n = vdi.vdi_pipeline_arena_bytes(d)
+    fake = 1 << 20
+    st, h = vdi.vdi_pipeline_create(d, fake + 16, n, fake)
+    assert st == vdi.VDI_ERR_INVALID_ARG and "aligned" in vdi.last_error() and not h.value
+    st, h = vdi.vdi_pipeline_create(d, fake, n - 1, fake)
+    assert st == vdi.VDI_ERR_WORKSPACE and not h.value
+    st, h = vdi.vdi_pipeline_create(d, fake, n, 0)
+    assert st == vdi.VDI_ERR_INVALID_ARG
+    d.n_s = 0
+    st, h = vdi.vdi_pipeline_create(d, fake, n, fake)
+    assert st == vdi.VDI_ERR_INVALID_ARG
+    cam = vdi.vdi_camera((0, 0, -10), (0, 0, 0), (0, 1, 0), 45.0, 40, 30)
+    dst = vdi.vdi_regular(fake, fake, fake, None, 6, 0)
+    assert vdi.vdi_pipeline_submit(None, fake, cam, dst)[0] == vdi.VDI_ERR_INVALID_ARG
+    assert vdi.vdi_pipeline_wait(None, 0) == vdi.VDI_ERR_INVALID_ARG
+    assert vdi.vdi_pipeline_destroy(None) == vdi.VDI_ERR_INVALID_ARG

@@ -111,6 +111,21 @@ def test_capacity_error_reported():
                          vdi.make_params(), ws.ptr, ws.nbytes)
     assert s == vdi.VDI_OK and ws.status() == vdi.VDI_OK
     torch.cuda.synchronize()
+    # the overflowed sub-VDI's lists were cut to the records that fit: every span lies inside the
+    # capacity and holds the records the large buffer got
+    c_cut = out.counts.cpu().numpy().astype(np.int64)
+    c_full = out2.counts.cpu().numpy().astype(np.int64)
+    off = out.offsets.cpu().numpy().astype(np.int64)
+    assert np.array_equal(off, out2.offsets.cpu().numpy().astype(np.int64))
+    assert np.all((c_cut == 0) | (off[:-1] + c_cut <= 3)) and np.all(c_cut <= c_full) and c_cut.sum() == 3
+    assert np.array_equal(c_cut, np.clip(3 - off[:-1], 0, c_full))
+    assert torch.equal(out.rgba[:3], out2.rgba[:3]) and torch.equal(out.fb[:3], out2.fb[:3])
+    # and composites without reading past it
+    reg = vdi.Regular(256, 4)
+    wsc = vdi.Workspace(vdi.vdi_composite_workspace(1, 16, 16, 4))
+    vdi.check(vdi.vdi_composite([out.struct()], 16, 16, reg.struct(), vdi.make_params(), wsc.ptr, wsc.nbytes),
+              "composite")
+    vdi.check(wsc.status(), "composite status")
 
 
 def test_given_gamma_with_fallback(tiny_workload):
