@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-layout", action="store_true", help="skip the regular-vs-compact layout comparison")
+    ap.add_argument("--no-nonconvex", action="store_true", help="skip the checkerboard-ownership frame")
     ap.add_argument("--no-scale", action="store_true", help="skip the 2048^2 K=32 dense compositing runs")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-request batched compositing run")
     ap.add_argument("--scale-size", type=int, default=2048, help="image side of the K=32 dense compositing run")
@@ -424,6 +425,62 @@ def pipeline_e2e(vdi, torch, wl, boxes, lut_d, vol_host, cams, capacity, schedul
     del pl
     torch.cuda.empty_cache()
     return ms, d2h
+
+
+def nonconvex_eval(vdi, torch, stream, wl, vol_d, lut_d, cams, outs, params, wsg, wsc, block=64, reps=3):
+    """The plain frame under a non-convex decomposition (sec. 5.3): a checkerboard of block^3-cell
+    blocks over the K PEs ((bx + by + bz) mod K), every PE sampling one shared whole-volume brick.
+    Generation (search) and compositing time, against the box decomposition's, and the largest
+    difference between the two flattened images (both render the same volume)."""
+    W, H, n_s = wl.W, wl.H, wl.n_s
+    npix = W * H
+    k = len(outs)
+    cells = [d - 1 for d in wl.dims]
+    nb = [-(-c // block) for c in cells]
+    bz, by, bx = np.meshgrid(np.arange(nb[2]), np.arange(nb[1]), np.arange(nb[0]), indexing="ij")
+    bmap = torch.from_numpy(((bx + by + bz) % k).astype(np.uint8)).to(vol_d.device)
+    own = vdi.vdi_ownership(bmap.data_ptr(), block, tuple(nb))
+    whole = vdi.Bricks(vol_d, wl.dims, [vdi.vdi_box((0, 0, 0), tuple(cells))], stream)
+    shared = (vdi.vdi_brick * k)(*([whole.bricks[0]] * k))
+    boxes = vdi.vdi_split_boxes(wl.dims, wl.grid)
+    split = vdi.Bricks(vol_d, wl.dims, boxes, stream)
+    ostructs = [o.struct() for o in outs]
+    out = vdi.Regular(npix, n_s, vdi.VDI_PREC_F32, vol_d.device)
+    img = [torch.zeros((npix, 4), dtype=torch.float32, device=vol_d.device) for _ in range(2)]
+    res = {}
+    for label, gen in (("boxes", lambda cam: vdi.vdi_generate(split.bricks, lut_d.data_ptr(), cam, n_s,
+                                                              vdi.VDI_GAMMA_SEARCH, ostructs, params, wsg.ptr,
+                                                              wsg.nbytes, stream)),
+                       ("checkerboard", lambda cam: vdi.vdi_generate_owned(shared, lut_d.data_ptr(), cam, n_s,
+                                                                           vdi.VDI_GAMMA_SEARCH, own, ostructs,
+                                                                           params, wsg.ptr, wsg.nbytes, stream))):
+        g_ms, c_ms, recs = [], [], []
+        for v in range(reps + 1):
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            vdi.check(gen(cams[v]), label)
+            b.record(stream)
+            vdi.check(vdi.vdi_composite(ostructs, W, H, out.struct(), params, wsc.ptr, wsc.nbytes, stream),
+                      "composite")
+            c.record(stream)
+            stream.synchronize()
+            if v:
+                g_ms.append(a.elapsed_time(b))
+                c_ms.append(b.elapsed_time(c))
+                recs.append(sum(int(o.offsets[-1].item()) for o in outs))
+        vdi.check(wsg.status(stream), "generate status")
+        vdi.check(wsc.status(stream), "composite status")
+        vdi.check(vdi.vdi_render_view(out.struct(), W, H, cams[reps], None, img[len(res)].data_ptr(), stream),
+                  "flatten")
+        res[label] = {"gen_ms": round(statistics.mean(g_ms), 3), "composite_ms": round(statistics.mean(c_ms), 3),
+                      "records": int(statistics.mean(recs)),
+                      "max_list": int(max(int(o.counts.max().item()) for o in outs))}
+    stream.synchronize()
+    res["image_max_diff"] = float((img[0] - img[1]).abs().max().item())
+    res["map"] = f"checkerboard of {block}^3-cell blocks, K={k}, one shared brick"
+    del whole, split, out, img, bmap
+    torch.cuda.empty_cache()
+    return res
 
 
 def layout_eval(vdi, torch, stream, wl, bricks, lut_d, cams, outs, params, params_c, wsg, wsc, reg, reps=3):
@@ -814,6 +871,10 @@ def main():
     if rank == 0:
         novel = novel_view_eval(vdi, torch, stream, wl, lambda: frame(0), reg, W, H)
 
+    nonconvex = None
+    if rank == 0 and not args.no_nonconvex:
+        nonconvex = nonconvex_eval(vdi, torch, stream, wl, vol_d, lut_d, cams, outs, params, wsg, wsc)
+
     layout = None
     if rank == 0 and not args.no_layout:
         layout = layout_eval(vdi, torch, stream, wl, bricks, lut_d, cams, outs, params, params_c, wsg, wsc, reg)
@@ -851,7 +912,7 @@ def main():
                               "census": _comp_census(vdi, comp_ctr), "schedule": comp_schedule,
                               "schedule_ms": sched_ms},
                 "composite_scale": scale, "composite_batched": batched, "render_view": novel,
-                "layout": layout,
+                "layout": layout, "nonconvex": nonconvex,
                 "gen": {"mrays_s": npix / (mean["choose_gamma"] + mean["scan+emit"] + mean["brick"]) / 1e3,
                         "sample_evals_per_frame": evals // args.steps,
                         "sm_steps_per_frame": steps_sm // args.steps, "tops": gen_tops,

@@ -236,6 +236,29 @@ vdi_status vdi_generate_regular(const vdi_brick* bricks, int32_t k, const float*
                                 int32_t n_s, float gamma, vdi_regular* out, const vdi_params* params,
                                 void* workspace, size_t ws_bytes, vdi_stream stream);
 
+/* Non-convex decompositions (sec. 5.3): ownership given per block of cells
+ * instead of by boxes.  owner[(bz * nb[1] + by) * nb[0] + bx] (device, one
+ * byte per block, x fastest) is the PE owning the block's cells; a value >= k
+ * means no PE.  block: edge of a block in cells, a power of two 1..1024;
+ * nb[a] = ceil((dims[a] - 1) / block). */
+typedef struct {
+    const uint8_t* owner;
+    int32_t block;
+    int32_t nb[3];
+} vdi_ownership;
+/* vdi_generate under an ownership map: bricks[e].owned must contain every
+ * cell PE e owns (its blocks' bounding box, say); PE e keeps the samples whose
+ * cell it owns.  Where a ray leaves PE e's domain and comes back, the open
+ * supersegment ends there, and the next non-transparent sample opens a new
+ * one even when n_s have been opened: a list may then hold more than n_s
+ * records (one per domain run at gamma = 2, the flat-DVR limit of sec. 5.3),
+ * and the search returns gamma = 2 with that count when no gamma meets n_s.
+ * gamma >= 0, VDI_GAMMA_SEARCH or VDI_GAMMA_GIVEN; other arguments, outputs
+ * and errors as vdi_generate. */
+vdi_status vdi_generate_owned(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
+                              int32_t n_s, float gamma, const vdi_ownership* own, vdi_compact* out,
+                              const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream);
+
 /* Generation for callers that cannot allocate device memory (an in-situ
  * simulation that reserves its whole device budget at start-up, a plugin with
  * no access to its host application's allocator).  The paper has no

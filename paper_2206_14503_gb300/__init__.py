@@ -60,6 +60,10 @@ class vdi_brick(C.Structure):
     _fields_ = [("cells", C.c_void_p), ("owned", vdi_box), ("dims", C.c_int32 * 3), ("value_scale", C.c_float)]
 
 
+class vdi_ownership(C.Structure):
+    _fields_ = [("owner", C.c_void_p), ("block", C.c_int32), ("nb", C.c_int32 * 3)]
+
+
 class vdi_pipeline_desc(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("type", C.c_int32), ("k", C.c_int32), ("boxes", vdi_box * 64),
                 ("width", C.c_int32), ("height", C.c_int32), ("n_s", C.c_int32), ("prec", C.c_int32),
@@ -100,6 +104,7 @@ def _load():
         "vdi_generate": ([vp, i32, vp, vp, i32, f32, vp, vp, vp, sz, vp], i32),
         "vdi_generate_static_scratch": ([vp, i32, vp, vp, i32, f32, vp, vp, vp], i32),
         "vdi_generate_regular": ([vp, i32, vp, vp, i32, f32, vp, vp, vp, sz, vp], i32),
+        "vdi_generate_owned": ([vp, i32, vp, vp, i32, f32, vp, vp, vp, vp, sz, vp], i32),
         "vdi_composite_workspace": ([i32, i32, i32, i32], sz),
         "vdi_composite": ([vp, i32, i32, i32, vp, vp, vp, sz, vp], i32),
         "vdi_render_view": ([vp, i32, i32, vp, vp, vp, vp], i32),
@@ -141,7 +146,7 @@ _lib = _load()
 SYMBOLS = ("vdi_version", "vdi_status_string", "vdi_last_error", "vdi_workspace_status", "vdi_workspace_counters",
            "vdi_split_boxes",
            "vdi_brick_bytes", "vdi_brick_build", "vdi_generate_workspace", "vdi_choose_gamma", "vdi_generate",
-           "vdi_generate_static_scratch", "vdi_generate_regular",
+           "vdi_generate_static_scratch", "vdi_generate_regular", "vdi_generate_owned",
            "vdi_composite_workspace", "vdi_composite", "vdi_render_view", "vdi_batch_table_bytes",
            "vdi_batch_table_pack", "vdi_composite_batched_workspace", "vdi_composite_batched", "vdi_composite_autotune",
            "vdi_model_bytes", "vdi_model_nparams", "vdi_model_init", "vdi_model_save", "vdi_model_load",
@@ -239,6 +244,14 @@ def vdi_choose_gamma(bricks, lut_ptr, cam: vdi_camera, n_s, gamma, outs, params:
     oarr = (vdi_compact * k)(*outs)
     return _lib.vdi_choose_gamma(_arr(bricks), k, C.c_void_p(lut_ptr), _ref(cam), n_s, gamma, _arr(oarr),
                                  _ref(params), C.c_void_p(ws_ptr), ws_bytes, _stream(stream))
+
+
+def vdi_generate_owned(bricks, lut_ptr, cam: vdi_camera, n_s, gamma, own: vdi_ownership, outs, params: vdi_params,
+                       ws_ptr, ws_bytes, stream=None) -> int:
+    k = len(outs)
+    oarr = (vdi_compact * k)(*outs)
+    return _lib.vdi_generate_owned(_arr(bricks), k, C.c_void_p(lut_ptr), _ref(cam), n_s, gamma, _ref(own), _arr(oarr),
+                                   _ref(params), C.c_void_p(ws_ptr), ws_bytes, _stream(stream))
 
 
 def vdi_generate_regular(bricks, lut_ptr, cam: vdi_camera, n_s, gamma, outs, params: vdi_params, ws_ptr, ws_bytes,

@@ -278,11 +278,11 @@ vdi_status vdi_choose_gamma(const vdi_brick* bricks, int32_t k, const float* tf_
                             reinterpret_cast<unsigned int*>(ws + kWsHeader), ws + fixed, ws_bytes - fixed, st);
 }
 
-vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam, int32_t n_s,
-                        float gamma, vdi_compact* out, const vdi_params* params, void* workspace, size_t ws_bytes,
-                        vdi_stream stream) {
-    vdi_status s = gen_common("vdi_generate", bricks, k, tf_lut, cam, n_s, gamma, out, params, workspace, ws_bytes,
-                              true);
+static vdi_status generate_compact(const char* fn, const vdi_brick* bricks, int32_t k, const float* tf_lut,
+                                   const vdi_camera* cam, int32_t n_s, float gamma, vdi_compact* out,
+                                   const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream,
+                                   const OwnerDev* own) {
+    vdi_status s = gen_common(fn, bricks, k, tf_lut, cam, n_s, gamma, out, params, workspace, ws_bytes, true);
     if (s != VDI_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned int* status = reinterpret_cast<unsigned int*>(workspace);
@@ -306,7 +306,8 @@ vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut,
     if (gamma != VDI_GAMMA_CHOSEN) {
         s = launch_gen_count(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s, gamma,
                              params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0,
-                             reinterpret_cast<unsigned int*>(ws + kWsHeader), ws + fixed, ws_bytes - fixed, st);
+                             reinterpret_cast<unsigned int*>(ws + kWsHeader), ws + fixed, ws_bytes - fixed, st,
+                             own);
         if (s != VDI_OK) return s;
     }
     s = launch_scan(k, npix, cnts, offs, ws + kGenFixed, st);
@@ -322,11 +323,39 @@ vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut,
         if (s != VDI_OK) return s;
         for (int e = 0; e < k; ++e)
             if (tot[e] > out[e].capacity)
-                return set_error(VDI_ERR_CAPACITY, "vdi_generate: PE %d needs %llu records, capacity %llu", e,
+                return set_error(VDI_ERR_CAPACITY, "%s: PE %d needs %llu records, capacity %llu", fn, e,
                                  (unsigned long long)tot[e], (unsigned long long)out[e].capacity);
     }
     return launch_gen_emit(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s,
-                           out[0].prec, od, status, st);
+                           out[0].prec, od, status, st, false, own);
+}
+
+vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam, int32_t n_s,
+                        float gamma, vdi_compact* out, const vdi_params* params, void* workspace, size_t ws_bytes,
+                        vdi_stream stream) {
+    return generate_compact("vdi_generate", bricks, k, tf_lut, cam, n_s, gamma, out, params, workspace, ws_bytes,
+                            stream, nullptr);
+}
+
+vdi_status vdi_generate_owned(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
+                              int32_t n_s, float gamma, const vdi_ownership* own, vdi_compact* out,
+                              const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream) {
+    if (!own || !own->owner || !bricks) return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_owned: NULL argument");
+    if (gamma == VDI_GAMMA_CHOSEN)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_owned: gamma mode VDI_GAMMA_CHOSEN");
+    int shift = 0;
+    while (shift < 11 && (1 << shift) != own->block) ++shift;
+    if (shift >= 11) return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_owned: block %d", own->block);
+    if (k >= 1 && k <= VDI_MAX_PE)
+        for (int a = 0; a < 3; ++a) {
+            const int cells = bricks[0].dims[a] - 1;
+            if (cells < 1 || own->nb[a] != (cells + own->block - 1) / own->block)
+                return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_owned: nb[%d] = %d for %d cells", a, own->nb[a],
+                                 cells);
+        }
+    const OwnerDev od{own->owner, shift, {own->nb[0], own->nb[1], own->nb[2]}};
+    return generate_compact("vdi_generate_owned", bricks, k, tf_lut, cam, n_s, gamma, out, params, workspace,
+                            ws_bytes, stream, &od);
 }
 
 vdi_status vdi_generate_regular(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,

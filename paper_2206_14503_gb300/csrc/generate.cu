@@ -26,6 +26,16 @@
 //
 // gen_emit_kernel re-marches with the chosen gamma and writes the records at
 // the prefix-sum offsets (compact layout, sec. 4).
+//
+// Non-convex ownership (sec. 5.3; the OWNED instantiations): a PE marches the
+// samples of its bounding box and keeps those whose cell lies in one of its
+// blocks.  Where the ray leaves the PE's domain and comes back, the open
+// supersegment ends (a "break"): every candidate closes, emission writes the
+// record, and the next non-transparent sample opens a new supersegment even
+// when the budget is spent.  The cache marks a break by a negative gap on
+// the next cached sample; at gamma = 2 each run of the domain that holds a
+// non-transparent sample gives one supersegment, so the search's upper end
+// counts those runs.
 #include <climits>
 #include <float.h>
 
@@ -51,6 +61,7 @@ struct GenArgs {
     float2* cache_b;        // [cap][slots] (log2(1 - a), transparent samples before it)
     int cache_cap, slots;
     int regular;  // emit: records of pixel p at p * n_s with a zero tail (regular layout), no offsets
+    OwnerDev own;  // non-convex ownership (own.map != nullptr): b[e] is the bounding box of PE e's blocks
 };
 
 constexpr int kTileW = 16, kTileH = 8, kGenThreads = 128;
@@ -87,6 +98,82 @@ __device__ __forceinline__ void tile_pixel(int tiles_x, int tile, int& i, int& j
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     i = tx * kTileW + (warp & 1) * 8 + (lane & 7);
     j = ty * kTileH + (warp >> 1) * 4 + (lane >> 3);
+}
+
+// PE owning the cell of fixed-point midpoint P (clamped to the volume's cells).
+__device__ __forceinline__ int owner_at(const GenArgs& a, const long long P[3]) {
+    int bl[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        int c = fixed_cell(P[q]);
+        c = c < 0 ? 0 : (c > a.dims[q] - 2 ? a.dims[q] - 2 : c);
+        bl[q] = c >> a.own.shift;
+    }
+    return __ldg(a.own.map + ((size_t)bl[2] * a.own.nb[1] + bl[1]) * a.own.nb[0] + bl[0]);
+}
+
+// Number of samples, from the one at fixed-point position P on, whose
+// midpoints stay in the same block of 2^shift cells on every axis (at least
+// 1, at most limit).  Blocks are taken on the unclamped cell index: every
+// sample of such a run also has the same clamped cell block, hence one owner.
+__device__ __forceinline__ int block_span(const long long P[3], const long long D[3], int shift, int limit) {
+    const int S = kFrac + shift;
+    long long n = limit;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const long long d = D[q];
+        if (d == 0) continue;
+        const long long blk = P[q] >> S;  // floor
+        long long m;
+        if (d > 0) m = (((blk + 1) << S) - P[q] + d - 1) / d;  // first m with P + m d >= next boundary
+        else m = (P[q] - (blk << S)) / (-d) + 1;                // first m with P + m d < this boundary
+        n = m < n ? m : n;
+    }
+    return (int)(n > 1 ? n : 1);
+}
+
+// march() restricted to the samples PE e owns, block by block: a block PE e
+// does not own is passed over in one step; on_break() is called before the
+// first owned sample after a stretch of samples the PE does not own.
+template <typename F, typename B>
+__device__ __forceinline__ void march_owned(const Ray& r, int k0, int k1, const BrickDev& b,
+                                            const float4* __restrict__ lut2, float scale255, const GenArgs& a, int e,
+                                            F&& f, B&& on_break) {
+    long long P[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) P[q] = r.P0[q] + (long long)k0 * r.D[q];
+    bool seen = false, away = false;
+    int k = k0;
+    while (k < k1) {
+        const int n = block_span(P, r.D, a.own.shift, k1 - k);
+        if (owner_at(a, P) != e) {
+            away = seen;
+            k += n;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) P[q] += (long long)n * r.D[q];
+            continue;
+        }
+        if (away) {
+            on_break();
+            away = false;
+        }
+        seen = true;
+        // the block's samples; the next cell is loaded while the current one is processed
+        float4 clo, chi;
+        cell_load(P, b, clo, chi);
+        for (int j = 0; j < n; ++j, ++k) {
+            const float w0 = fixed_frac(P[0]), w1 = fixed_frac(P[1]), w2 = fixed_frac(P[2]);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) P[q] += r.D[q];
+            float4 nlo, nhi;
+            cell_load(P, b, nlo, nhi);
+            Sample s;
+            sample_from(w0, w1, w2, clo, chi, lut2, scale255, s);
+            f(k, s);
+            clo = nlo;
+            chi = nhi;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -159,24 +246,29 @@ struct CacheRef {
 };
 
 // First march: counts non-transparent samples and, if `c` is given, caches
-// them (up to c->cap).  NC gamma candidates ride along (NC may be 0).
-template <int NC>
+// them (up to c->cap).  NC gamma candidates ride along (NC may be 0).  OWNED:
+// PE e's samples under the ownership map of *ga; *runs receives the number of
+// domain runs holding a non-transparent sample (the count at gamma = 2).
+template <int NC, bool OWNED = false>
 __device__ __forceinline__ int first_march(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
                                            float scale255, const float* g2, int cap, const CacheRef* c, int* cnt,
-                                           Census& cs) {
+                                           Census& cs, const GenArgs* ga = nullptr, int e = 0, int* runs = nullptr) {
     cs.evals += (unsigned long long)(k1 - k0);
     cs.steps += (unsigned long long)(k1 - k0) * NC;
     cs.passes += 1;
     GenCount st[NC > 0 ? NC : 1];
 #pragma unroll
     for (int q = 0; q < NC; ++q) gc_reset(st[q]);
-    int nt = 0, gap = 0;
-    march(r, k0, k1, b, lut2, scale255, [&](int, const Sample& s) {
+    int nt = 0, gap = 0, nruns = 0;
+    bool brk = false;
+    auto visit = [&](int, const Sample& s) {
         if (s.a > 0.f) {
             if (c && nt < c->cap) {
                 c->a[c->at(nt)] = make_float4(s.P[0], s.P[1], s.P[2], s.a);
-                c->b[c->at(nt)] = make_float2(s.lgT, (float)gap);
+                c->b[c->at(nt)] = make_float2(s.lgT, (OWNED && brk) ? -1.f : (float)gap);
             }
+            if (OWNED && (nruns == 0 || brk)) ++nruns;
+            brk = false;
             ++nt;
             gap = 0;
         } else {
@@ -184,7 +276,18 @@ __device__ __forceinline__ int first_march(const Ray& r, int k0, int k1, const B
         }
 #pragma unroll
         for (int q = 0; q < NC; ++q) gc_step(st[q], s.P, s.a, s.lgT, g2[q], cap);
-    });
+    };
+    if constexpr (OWNED) {
+        march_owned(r, k0, k1, b, lut2, scale255, *ga, e, visit, [&]() {
+            brk = true;
+            gap = 0;
+#pragma unroll
+            for (int q = 0; q < NC; ++q) st[q].m = 0.f;
+        });
+        *runs = nruns;
+    } else {
+        march(r, k0, k1, b, lut2, scale255, visit);
+    }
 #pragma unroll
     for (int q = 0; q < NC; ++q) cnt[q] = st[q].cnt;
     return nt;
@@ -192,6 +295,8 @@ __device__ __forceinline__ int first_march(const Ray& r, int k0, int k1, const B
 
 // Bisection march over the cached samples: three candidates.  Entries are
 // read two ahead of their use so the loads overlap the state-machine work.
+// OWNED: a negative gap marks a break before the entry.
+template <bool OWNED = false>
 __device__ __forceinline__ void cached_march(const CacheRef& c, int nt, const float g2[3], int cnt[3], Census& cs) {
     cs.steps += (unsigned long long)nt * 3;
     cs.passes += 1;
@@ -214,6 +319,7 @@ __device__ __forceinline__ void cached_march(const CacheRef& c, int nt, const fl
         const float P[3] = {x.x, x.y, x.z};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
+            if (OWNED && y.y < 0.f) st[q].m = 0.f;
             if (y.y > 0.f) gc_run(st[q], y.y, g2[q], INT_MAX);
             gc_step(st[q], P, x.w, y.x, g2[q], INT_MAX);
         }
@@ -227,19 +333,25 @@ __device__ __noinline__ void cached_march_call(const CacheRef& c, int nt, const 
 }
 
 // Bisection march over the volume: three candidates.
+template <bool OWNED = false>
 __device__ __forceinline__ void volume_march(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
-                                             float scale255, const float g2[3], int cnt[3], Census& cs) {
-    first_march<3>(r, k0, k1, b, lut2, scale255, g2, INT_MAX, nullptr, cnt, cs);
+                                             float scale255, const float g2[3], int cnt[3], Census& cs,
+                                             const GenArgs* ga, int e) {
+    int runs = 0;
+    first_march<3, OWNED>(r, k0, k1, b, lut2, scale255, g2, INT_MAX, nullptr, cnt, cs, ga, e, &runs);
 }
 
 // Per-ray bisection search (sec. 2.4), called when the count at gamma = 0
 // (nt) exceeds n_s: sequential bisection of [0, 2]; each march evaluates the
 // midpoint and its two children, so two levels are decided per march.
+// `runs`: the count at gamma = 2 (OWNED; otherwise 1).
+template <bool OWNED = false>
 __device__ __forceinline__ float search(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
                                         float scale255, int n_s, int iters, int nt, const CacheRef* c, int& count,
-                                        Census& cs) {
+                                        Census& cs, const GenArgs* ga = nullptr, int e = 0, int runs = 1) {
     float lo = 0.f, hi = 2.f;
-    int cnt_hi = nt > 0 ? 1 : 0;  // the distance never reaches 2: one supersegment
+    // the distance never reaches 2: one supersegment per domain run
+    int cnt_hi = nt > 0 ? (OWNED ? runs : 1) : 0;
     int it = 0;
     while (it < iters) {
         const float mid = 0.5f * (lo + hi);
@@ -249,10 +361,10 @@ __device__ __forceinline__ float search(const Ray& r, int k0, int k1, const Bric
         for (int q = 0; q < 3; ++q) g2[q] = __fmul_rn(g[q], g[q]);
         int cnt[3];
         if (c) {
-            cached_march(*c, nt, g2, cnt, cs);
+            cached_march<OWNED>(*c, nt, g2, cnt, cs);
             cs.cached += 1;
         } else {
-            volume_march(r, k0, k1, b, lut2, scale255, g2, cnt, cs);
+            volume_march<OWNED>(r, k0, k1, b, lut2, scale255, g2, cnt, cs, ga, e);
             cs.remarched += 1;
         }
         // level 1: the midpoint
@@ -394,7 +506,7 @@ __device__ __noinline__ float search_call(const Ray& r, int k0, int k1, const Br
 
 // The learned-gamma refinement (mode 3) is compiled only into the LEARNED
 // instantiation so that the search kernel keeps its register budget.
-template <bool CENSUS, bool LEARNED>
+template <bool CENSUS, bool LEARNED, bool OWNED = false>
 __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     __shared__ unsigned int s_item;
@@ -428,12 +540,13 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
         const bool any = ray_setup(a.cam, i, j, a.dims, a.step, r) && owned_range(r, a.step, b, a.dims, k0, k1);
         float gamma = mode == 0 ? a.gamma : (mode >= 2 ? fmaxf(o.gamma[p], 0.f) : 0.f);
         int count = 0;
+        int runs = 1;
         if (any) {
             rays += 1;
             if (mode == 0) {
                 const float g2[1] = {__fmul_rn(a.gamma, a.gamma)};
                 int c[1];
-                first_march<1>(r, k0, k1, b, lut2, a.scale255, g2, a.n_s, nullptr, c, cs);
+                first_march<1, OWNED>(r, k0, k1, b, lut2, a.scale255, g2, a.n_s, nullptr, c, cs, &a, e, &runs);
                 count = c[0];
             } else {
                 const bool use_cache = a.cache_a != nullptr;
@@ -443,8 +556,8 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
                     // one march: count at the given gamma, non-transparent count, cache
                     const float g2[1] = {__fmul_rn(gamma, gamma)};
                     int c[1];
-                    nt = first_march<1>(r, k0, k1, b, lut2, a.scale255, g2, INT_MAX, use_cache ? &cref : nullptr, c,
-                                        cs);
+                    nt = first_march<1, OWNED>(r, k0, k1, b, lut2, a.scale255, g2, INT_MAX,
+                                               use_cache ? &cref : nullptr, c, cs, &a, e, &runs);
                     if (mode == 2) {
                         if (c[0] <= a.n_s) {
                             count = c[0];
@@ -455,8 +568,8 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
                     }
                 } else {
                     int dummy[1];
-                    nt = first_march<0>(r, k0, k1, b, lut2, a.scale255, nullptr, INT_MAX, use_cache ? &cref : nullptr,
-                                        dummy, cs);
+                    nt = first_march<0, OWNED>(r, k0, k1, b, lut2, a.scale255, nullptr, INT_MAX,
+                                               use_cache ? &cref : nullptr, dummy, cs, &a, e, &runs);
                 }
                 if (searched) {
                     if (nt <= a.n_s) {
@@ -467,7 +580,8 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
                         cs.searched += 1;
                         cs.overflow += c ? 0 : 1;
                         gamma = LEARNED ? search_call(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count, cs)
-                                        : search(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count, cs);
+                                        : search<OWNED>(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count,
+                                                        cs, &a, e, runs);
                     }
                 }
             }
@@ -512,6 +626,7 @@ __device__ __forceinline__ void store_record(const GenArgs& a, const CompactDev&
     }
 }
 
+template <bool OWNED>
 __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     load_lut(a, lut2);
@@ -557,7 +672,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_c
     GenCount st;
     gc_reset(st);
     int kopen = 0, klast = 0;
-    march(r, k0, k1, b, lut2, a.scale255, [&](int k, const Sample& s) {
+    auto visit = [&](int k, const Sample& s) {
         const bool was_open = st.m != 0.f;
         const int before = st.cnt;
         const RecOut cur{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1),
@@ -575,7 +690,20 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_c
         } else if (st.m != 0.f && s.a > 0.f) {
             klast = k;
         }
-    });
+    };
+    if constexpr (OWNED) {
+        // leaving the PE's domain ends the open supersegment (sec. 5.3)
+        march_owned(r, k0, k1, b, lut2, a.scale255, a, e, visit, [&]() {
+            if (st.m == 0.f) return;
+            const RecOut cur{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1),
+                             {st.P[0], st.P[1], st.P[2]}, st.A};
+            if (written < room) store_record(a, o, base + written, cur);
+            ++written;
+            st.m = 0.f;
+        });
+    } else {
+        march(r, k0, k1, b, lut2, a.scale255, visit);
+    }
     if (st.m != 0.f) {
         if (written < room) {
             RecOut ro{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1), {st.P[0], st.P[1], st.P[2]},
@@ -612,6 +740,7 @@ static void fill_args(GenArgs& a, const BrickDev* bricks, int k, const float* lu
     a.cache_cap = 0;
     a.slots = 0;
     a.regular = 0;
+    a.own = OwnerDev{nullptr, 0, {0, 0, 0}};
 }
 
 // persistent grid of gen_count_kernel on the current device
@@ -621,9 +750,10 @@ vdi_status gen_count_grid(int& ctas) {
     if (s != VDI_OK) return s;
     s = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     if (s != VDI_OK) return s;
-    void (*const kernels[4])(GenArgs) = {gen_count_kernel<false, false>, gen_count_kernel<true, false>,
-                                         gen_count_kernel<false, true>, gen_count_kernel<true, true>};
-    for (int q = 0; q < 4; ++q) {
+    void (*const kernels[6])(GenArgs) = {gen_count_kernel<false, false>, gen_count_kernel<true, false>,
+                                         gen_count_kernel<false, true>,  gen_count_kernel<true, true>,
+                                         gen_count_kernel<false, false, true>, gen_count_kernel<true, false, true>};
+    for (int q = 0; q < 6; ++q) {
         s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, kernels[q], kGenThreads, 0),
                        "occupancy");
         if (s != VDI_OK) return s;
@@ -640,9 +770,10 @@ size_t gen_cache_bytes(int ctas) {
 vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                             float scale255, float step, float ref_len, int n_s, float gamma, int iters,
                             const CompactDev* out, unsigned int* status, bool census, unsigned int* counter,
-                            void* cache, size_t cache_bytes, cudaStream_t st) {
+                            void* cache, size_t cache_bytes, cudaStream_t st, const OwnerDev* own) {
     GenArgs a;  // copied into the launch's parameter space
     fill_args(a, bricks, k, lut, cam, dims, scale255, step, ref_len, n_s, out, status);
+    if (own) a.own = *own;
     a.iters = iters;
     a.gamma = gamma;
     a.mode = gamma >= 0.f ? 0 : (gamma == VDI_GAMMA_GIVEN ? 2 : (gamma == kGammaLearnedBracket ? 3 : 1));
@@ -662,7 +793,10 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
     }
     if ((unsigned)ctas > items) ctas = (int)items;
     const bool learned = a.mode == 3;
-    if (census && learned) gen_count_kernel<true, true><<<ctas, kGenThreads, 0, st>>>(a);
+    if (a.own.map && learned) return set_error(VDI_ERR_UNSUPPORTED, "learned gamma with an ownership map");
+    if (a.own.map && census) gen_count_kernel<true, false, true><<<ctas, kGenThreads, 0, st>>>(a);
+    else if (a.own.map) gen_count_kernel<false, false, true><<<ctas, kGenThreads, 0, st>>>(a);
+    else if (census && learned) gen_count_kernel<true, true><<<ctas, kGenThreads, 0, st>>>(a);
     else if (census) gen_count_kernel<true, false><<<ctas, kGenThreads, 0, st>>>(a);
     else if (learned) gen_count_kernel<false, true><<<ctas, kGenThreads, 0, st>>>(a);
     else gen_count_kernel<false, false><<<ctas, kGenThreads, 0, st>>>(a);
@@ -671,9 +805,10 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
 
 vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                            float scale255, float step, float ref_len, int n_s, int prec, const CompactDev* out,
-                           unsigned int* status, cudaStream_t st, bool regular) {
+                           unsigned int* status, cudaStream_t st, bool regular, const OwnerDev* own) {
     GenArgs a;
     fill_args(a, bricks, k, lut, cam, dims, scale255, step, ref_len, n_s, out, status);
+    if (own) a.own = *own;
     a.regular = regular ? 1 : 0;
     a.iters = 0;
     a.gamma = 0.f;
@@ -681,7 +816,8 @@ vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, cons
     a.prec = prec;
     dim3 grid((unsigned)(a.tiles_x * a.tiles_y), (unsigned)k);
     if (grid.x == 0) return VDI_OK;
-    gen_emit_kernel<<<grid, kGenThreads, 0, st>>>(a);
+    if (a.own.map) gen_emit_kernel<true><<<grid, kGenThreads, 0, st>>>(a);
+    else gen_emit_kernel<false><<<grid, kGenThreads, 0, st>>>(a);
     return cuda_check(cudaGetLastError(), "gen_emit_kernel launch");
 }
 

@@ -18,6 +18,14 @@ struct CamDev {
     int W, H;
 };
 
+// Non-convex ownership (sec. 5.3): the PE of each block of 2^shift cells per
+// axis, x fastest, nb[] blocks per axis; map == nullptr means box ownership.
+struct OwnerDev {
+    const uint8_t* map;
+    int shift;
+    int nb[3];
+};
+
 // One PE's sampling brick: cells [lo-1, hi+1) per axis (a one-cell border),
 // 8 corner values per cell as two float4 (v000 v100 v010 v110 | v001 v101 v011 v111).
 struct BrickDev {
@@ -59,7 +67,7 @@ vdi_status launch_brick_build(const void* volume, int type, const int dims[3], i
 vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                             float scale255, float step, float ref_len, int n_s, float gamma, int iters,
                             const CompactDev* out, unsigned int* status, bool census, unsigned int* counter,
-                            void* cache, size_t cache_bytes, cudaStream_t st);
+                            void* cache, size_t cache_bytes, cudaStream_t st, const OwnerDev* own = nullptr);
 vdi_status gen_count_grid(int& ctas);
 size_t gen_cache_bytes(int ctas);
 // generation workspace: [0, 256) header, [256, 512) work counter, then the
@@ -70,7 +78,8 @@ constexpr size_t kGenFixed = 512;
 constexpr float kGammaLearnedBracket = -5.0f;
 vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                            float scale255, float step, float ref_len, int n_s, int prec, const CompactDev* out,
-                           unsigned int* status, cudaStream_t st, bool regular = false);
+                           unsigned int* status, cudaStream_t st, bool regular = false,
+                           const OwnerDev* own = nullptr);
 size_t scan_workspace(int k, int n);
 vdi_status launch_scan(int k, int n, uint32_t* const* counts, uint64_t* const* offsets, void* ws, cudaStream_t st);
 

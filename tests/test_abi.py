@@ -121,6 +121,21 @@ def test_argument_errors_before_launch(vdi):
     rout.rgba, rout.fb = fake, None
     assert vdi.vdi_generate_regular(bricks, fake, cam, 4, -1.0, [rout], params, fake,
                                     1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    # ownership map: block a power of two, nb the blocks per axis of the brick's volume (dims 4: 3 cells)
+    own = vdi.vdi_ownership(fake, 3, (1, 1, 1))
+    assert vdi.vdi_generate_owned(bricks, fake, cam, 4, -1.0, own, [out], params, fake,
+                                  1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    assert "block" in vdi.last_error()
+    own = vdi.vdi_ownership(fake, 2, (1, 2, 2))
+    assert vdi.vdi_generate_owned(bricks, fake, cam, 4, -1.0, own, [out], params, fake,
+                                  1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    assert "nb[0]" in vdi.last_error()
+    own = vdi.vdi_ownership(fake, 2, (2, 2, 2))
+    assert vdi.vdi_generate_owned(bricks, fake, cam, 4, vdi.VDI_GAMMA_CHOSEN, own, [out], params, fake,
+                                  1 << 20) == vdi.VDI_ERR_INVALID_ARG
+    own.owner = None
+    assert vdi.vdi_generate_owned(bricks, fake, cam, 4, -1.0, own, [out], params, fake,
+                                  1 << 20) == vdi.VDI_ERR_INVALID_ARG
     # composite: n_s < 1, missing arrays
     reg = vdi.vdi_regular(fake, fake, fake, None, 0, 0)
     assert vdi.vdi_composite([out], 4, 4, reg, params, fake, 256) == vdi.VDI_ERR_INVALID_ARG
