@@ -541,21 +541,10 @@ __device__ __forceinline__ void cached_emit(const float4* __restrict__ ca, const
         }
         ++w;
     };
-    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-    float2 y0 = make_float2(0.f, 0.f), y1 = y0;
-    if (nt > 0) { x0 = __ldcg(ca + slot); y0 = __ldcg(cb + slot); }
-    if (nt > 1) { x1 = __ldcg(ca + (size_t)slots + slot); y1 = __ldcg(cb + (size_t)slots + slot); }
     for (int j = 0; j < nt; ++j) {
-        // entries are read two ahead of their use, as in cached_march
-        const float4 x = x0;
-        const float2 y = y0;
-        x0 = x1;
-        y0 = y1;
-        if (j + 2 < nt) {
-            const size_t at = (size_t)(j + 2) * slots + slot;
-            x1 = __ldcg(ca + at);
-            y1 = __ldcg(cb + at);
-        }
+        const size_t at = (size_t)j * slots + slot;
+        const float4 x = __ldcg(ca + at);
+        const float2 y = __ldcg(cb + at);
         k += (int)y.y + 1;
         if (y.y > 0.f && st.m != 0.f) {
             gc_run(st, y.y, g2, cap);
