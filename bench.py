@@ -682,9 +682,6 @@ def main():
     wsg = vdi.Workspace(vdi.vdi_generate_workspace(k, W, H), dev)
     wsc = vdi.Workspace(vdi.vdi_composite_workspace(k, W, H, n_s), dev)
     params = vdi.make_params(step=wl.step, ref_len=wl.ref_len)
-    # the frame's generation: the γ search stages each ray's records from its cached samples, the
-    # emission copies them (VDI_FLAG_STAGE on both calls, same workspace)
-    params_s = vdi.make_params(step=wl.step, ref_len=wl.ref_len, flags=vdi.VDI_FLAG_STAGE)
     cams = [vdi.make_camera(c) for c in wl.cams]
     ostructs = [o.struct() for o in outs]
     rstruct = reg.struct()
@@ -699,11 +696,11 @@ def main():
         if ev:
             ev[1].record(stream)
         vdi.check(vdi.vdi_choose_gamma(bricks.bricks, lut_d.data_ptr(), cam, n_s, vdi.VDI_GAMMA_SEARCH, ostructs,
-                                       params_s, wsg.ptr, wsg.nbytes, stream), "choose_gamma")
+                                       params, wsg.ptr, wsg.nbytes, stream), "choose_gamma")
         if ev:
             ev[2].record(stream)
         vdi.check(vdi.vdi_generate(bricks.bricks, lut_d.data_ptr(), cam, n_s, vdi.VDI_GAMMA_CHOSEN, ostructs,
-                                   params_s, wsg.ptr, wsg.nbytes, stream), "generate")
+                                   params, wsg.ptr, wsg.nbytes, stream), "generate")
         if ev:
             ev[3].record(stream)
         vdi.check(vdi.vdi_composite(ostructs, W, H, rstruct, params_c, wsc.ptr, wsc.nbytes, stream), "composite")
@@ -771,7 +768,7 @@ def main():
     value = rays / (total_ms * 1e-3) / 1e6
 
     # ---- work census and bytes of the timed frames (outside the timed region) ----
-    cen_params = vdi.make_params(step=wl.step, ref_len=wl.ref_len, flags=vdi.VDI_FLAG_CENSUS | vdi.VDI_FLAG_STAGE)
+    cen_params = vdi.make_params(step=wl.step, ref_len=wl.ref_len, flags=vdi.VDI_FLAG_CENSUS)
     evals = steps_sm = passes = pe_rays = searched = overflow = cached = remarched = 0
     comp_bytes = []
     comp_ctr = None
@@ -789,7 +786,7 @@ def main():
         cached += c[6]
         remarched += c[7]
         vdi.check(vdi.vdi_generate(bricks.bricks, lut_d.data_ptr(), cams[view], n_s, vdi.VDI_GAMMA_CHOSEN, ostructs,
-                                   params_s, wsg.ptr, wsg.nbytes, stream), "generate")
+                                   params, wsg.ptr, wsg.nbytes, stream), "generate")
         cen_c = vdi.make_params(step=wl.step, ref_len=wl.ref_len, schedule=comp_schedule, flags=vdi.VDI_FLAG_CENSUS)
         vdi.check(vdi.vdi_composite(ostructs, W, H, rstruct, cen_c, wsc.ptr, wsc.nbytes, stream), "census")
         cc = vdi.vdi_workspace_counters(wsc.ptr, stream)

@@ -98,7 +98,6 @@ typedef struct {
 
 #define VDI_FLAG_SYNC_CAPACITY 1 /* vdi_generate: read totals back and return VDI_ERR_CAPACITY before emitting */
 #define VDI_FLAG_CENSUS 2        /* vdi_choose_gamma / vdi_generate / vdi_composite: count the work done (vdi_workspace_counters) */
-#define VDI_FLAG_STAGE 4         /* vdi_choose_gamma: stage records in the workspace; vdi_generate(VDI_GAMMA_CHOSEN): copy them (see vdi_generate) */
 
 /* A sampling brick: one PE's cells in the library's cell-packed layout, built
  * by vdi_brick_build().  Opaque to the caller apart from its size. */
@@ -191,15 +190,11 @@ vdi_status vdi_brick_build(const void* volume, vdi_voltype type, const int32_t d
 /* ------------------------------------------------------------------------ */
 /* Workspace bytes for vdi_generate / vdi_choose_gamma with k PEs of w x h on
  * the current device: a status header, a work counter, the prefix sum's
- * partial sums (8 bytes per 4096 pixels per PE), a sample cache (about
- * 1.2 GB on a 152-SM GB300) that lets the gamma search run over each ray's
- * cached non-transparent samples instead of re-sampling the volume, and a
- * record stage (4 bytes plus 4 records of 24 bytes per PE and pixel) into
- * which the search emits each cached ray's records, so that emission copies
- * them instead of re-marching the volume.  Any workspace of at least 512 +
- * 8 k ceil(w h / 4096) bytes is accepted; without room for the cache the
- * search re-marches the volume, without room for the stage (or for a ray's
- * records in it) emission does (same result, slower). */
+ * partial sums (8 bytes per 4096 pixels per PE) and a sample cache (about
+ * 400 MB on a 152-SM GB300) that lets the gamma search run over each ray's
+ * cached non-transparent samples instead of re-sampling the volume.  Any
+ * workspace of at least 512 + 8 k ceil(w h / 4096) bytes is accepted; without
+ * room for the cache the search re-marches the volume (same result, slower). */
 size_t vdi_generate_workspace(int32_t k, int32_t w, int32_t h);
 
 /* Chooses gamma and the resulting supersegment count for every (PE, ray)
@@ -221,13 +216,6 @@ vdi_status vdi_choose_gamma(const vdi_brick* bricks, int32_t k, const float* tf_
  * and out[e].gamma then hold the result of an earlier vdi_choose_gamma call
  * with the same bricks, camera, n_s and params (only the prefix sum and the
  * emission run).
- * With gamma >= 0 the records are emitted by a volume march; with the search
- * or VDI_GAMMA_GIVEN the search stages them in the workspace (see
- * vdi_generate_workspace).  VDI_GAMMA_CHOSEN with VDI_FLAG_STAGE copies the
- * records staged by the vdi_choose_gamma call made with VDI_FLAG_STAGE on the
- * same workspace: the caller guarantees that no other call used the
- * workspace in between (otherwise the records of another call are copied);
- * without the flag, emission re-marches the volume.
  * Records of a list are in depth order, at most n_s per list for box-shaped
  * domains.  If a PE's total exceeds out[e].capacity, no record past the
  * capacity is written and VDI_ERR_CAPACITY is reported through the workspace

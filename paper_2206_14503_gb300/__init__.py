@@ -33,7 +33,6 @@ VDI_GAMMA_GIVEN = -2.0
 VDI_GAMMA_CHOSEN = -3.0
 VDI_FLAG_SYNC_CAPACITY = 1
 VDI_FLAG_CENSUS = 2
-VDI_FLAG_STAGE = 4
 VDI_SCHED_STAGED = 4
 
 

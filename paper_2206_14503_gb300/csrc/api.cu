@@ -208,7 +208,7 @@ size_t vdi_generate_workspace(int32_t k, int32_t w, int32_t h) {
     int ctas = 0;
     size_t cache = 0;
     if (gen_count_grid(ctas) == VDI_OK) cache = gen_cache_bytes(ctas);
-    return gen_min_workspace(k, w, h) + align_up(cache, 256) + (cache ? gen_stage_bytes(k, (long long)w * h) : 0);
+    return gen_min_workspace(k, w, h) + align_up(cache, 256);
 }
 
 static vdi_status gen_common(const char* fn, const vdi_brick* bricks, int32_t k, const float* tf_lut,
@@ -275,8 +275,7 @@ vdi_status vdi_choose_gamma(const vdi_brick* bricks, int32_t k, const float* tf_
     char* ws = static_cast<char*>(workspace);
     return launch_gen_count(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s, gamma,
                             params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0,
-                            reinterpret_cast<unsigned int*>(ws + kWsHeader), ws + fixed, ws_bytes - fixed, st,
-                            nullptr, (params->flags & VDI_FLAG_STAGE) != 0);
+                            reinterpret_cast<unsigned int*>(ws + kWsHeader), ws + fixed, ws_bytes - fixed, st);
 }
 
 static vdi_status generate_compact(const char* fn, const vdi_brick* bricks, int32_t k, const float* tf_lut,
@@ -308,7 +307,7 @@ static vdi_status generate_compact(const char* fn, const vdi_brick* bricks, int3
         s = launch_gen_count(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s, gamma,
                              params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0,
                              reinterpret_cast<unsigned int*>(ws + kWsHeader), ws + fixed, ws_bytes - fixed, st,
-                             own, own == nullptr);
+                             own);
         if (s != VDI_OK) return s;
     }
     s = launch_scan(k, npix, cnts, offs, ws + kGenFixed, st);
@@ -327,12 +326,8 @@ static vdi_status generate_compact(const char* fn, const vdi_brick* bricks, int3
                 return set_error(VDI_ERR_CAPACITY, "%s: PE %d needs %llu records, capacity %llu", fn, e,
                                  (unsigned long long)tot[e], (unsigned long long)out[e].capacity);
     }
-    // staged records: from this call's count launch, or under VDI_FLAG_STAGE from the vdi_choose_gamma call
-    // that wrote counts and gamma with this workspace
-    const bool staged = own == nullptr && (gamma != VDI_GAMMA_CHOSEN || (params->flags & VDI_FLAG_STAGE));
     return launch_gen_emit(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s,
-                           out[0].prec, od, status, st, false, own, staged ? ws + fixed : nullptr,
-                           staged ? ws_bytes - fixed : 0);
+                           out[0].prec, od, status, st, false, own);
 }
 
 vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam, int32_t n_s,

@@ -62,19 +62,9 @@ struct GenArgs {
     int cache_cap, slots;
     int regular;  // emit: records of pixel p at p * n_s with a zero tail (regular layout), no offsets
     OwnerDev own;  // non-convex ownership (own.map != nullptr): b[e] is the bounding box of PE e's blocks
-    // staged emission: the count kernel writes each cached ray's records (FP32) to a chunk of the
-    // stage owned by its CTA and their index to stage_idx[e * npix + p] (kNotStaged otherwise);
-    // the emit kernel copies them when *stage_valid != 0
-    float4* stage_a;
-    float2* stage_b;
-    uint32_t* stage_idx;
-    unsigned int* stage_valid;
-    unsigned int stage_chunk;  // records per CTA chunk
-    int npix;
 };
 
 constexpr int kTileW = 16, kTileH = 8, kGenThreads = 128;
-constexpr uint32_t kNotStaged = 0xFFFFFFFFu;
 constexpr int kCacheCap = 640;  // cached non-transparent samples per (PE, ray)
 
 // Work census (VDI_FLAG_CENSUS): kept in registers; the kernel variant
@@ -514,66 +504,12 @@ __device__ __noinline__ float search_call(const Ray& r, int k0, int k1, const Br
     return search(r, k0, k1, b, lut2, scale255, n_s, iters, nt, c, count, cs);
 }
 
-struct RecOut {
-    float f, b, P[3], A;
-};
-
-// Emission over the cached samples at the chosen gamma (g2 = gamma^2), with
-// the budget `cap`: the records the emit kernel's volume march would write
-// (the same decisions: a transparent run is decided by its first sample, so
-// a cached gap equals that many transparent samples), written as FP32 to
-// stage[idx ..].  Sample j of the cache lies `gap` samples after the previous
-// one; its index k fixes the record depths.  Writes at most `want` records.
-// Inlined: an out-of-line call in the persistent loop tripled its time.
-__device__ __forceinline__ void cached_emit(const float4* __restrict__ ca, const float2* __restrict__ cb, int slot,
-                                           int slots, int nt, float g2, int cap, float tin_hi, float tin_lo, int k0,
-                                           float step, float4* __restrict__ sa, float2* __restrict__ sb, size_t idx,
-                                           uint32_t want) {
-    GenCount st;
-    gc_reset(st);
-    int k = k0 - 1, kopen = 0, klast = 0;
-    uint32_t w = 0;
-    auto put = [&]() {
-        if (w < want) {
-            sa[idx + w] = make_float4(st.P[0], st.P[1], st.P[2], st.A);
-            sb[idx + w] = make_float2(__fadd_rn(__fmaf_rn((float)kopen, step, tin_hi), tin_lo),
-                                      __fadd_rn(__fmaf_rn((float)(klast + 1), step, tin_hi), tin_lo));
-        }
-        ++w;
-    };
-    for (int j = 0; j < nt; ++j) {
-        const size_t at = (size_t)j * slots + slot;
-        const float4 x = __ldcg(ca + at);
-        const float2 y = __ldcg(cb + at);
-        k += (int)y.y + 1;
-        if (y.y > 0.f && st.m != 0.f) {
-            gc_run(st, y.y, g2, cap);
-            if (st.m == 0.f) put();  // the run's first sample closed S
-        }
-        const float P[3] = {x.x, x.y, x.z};
-        // gc_step for a non-transparent sample, with the closed S written before the next opens
-        if (st.m != 0.f && !(st.cnt < cap && criterion(st.P, st.A, st.L2, rcp_approx(st.m), P, g2))) {
-            absorb(st.P, st.A, st.L2, P, x.w, y.x);
-            st.m = __fadd_rn(st.m, 1.f);
-            st.run = false;
-        } else {
-            if (st.m != 0.f) put();
-            gc_open(st, P, x.w, y.x);
-            kopen = k;
-        }
-        klast = k;
-    }
-    if (st.m != 0.f) put();
-}
-
 // The learned-gamma refinement (mode 3) is compiled only into the LEARNED
 // instantiation so that the search kernel keeps its register budget.
 template <bool CENSUS, bool LEARNED, bool OWNED = false>
 __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     __shared__ unsigned int s_item;
-    __shared__ unsigned int s_stage_used;  // records of this CTA's stage chunk handed out
-    if (threadIdx.x == 0) s_stage_used = 0;
     load_lut(a, lut2);
     const unsigned tiles = (unsigned)(a.tiles_x * a.tiles_y);
     const unsigned total = tiles * (unsigned)a.k;
@@ -605,7 +541,6 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
         float gamma = mode == 0 ? a.gamma : (mode >= 2 ? fmaxf(o.gamma[p], 0.f) : 0.f);
         int count = 0;
         int runs = 1;
-        int nt_cached = -1;  // non-transparent samples, when all of them are in the cache
         if (any) {
             rays += 1;
             if (mode == 0) {
@@ -636,7 +571,6 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
                     nt = first_march<0, OWNED>(r, k0, k1, b, lut2, a.scale255, nullptr, INT_MAX,
                                                use_cache ? &cref : nullptr, dummy, cs, &a, e, &runs);
                 }
-                if (use_cache && nt <= a.cache_cap) nt_cached = nt;
                 if (searched) {
                     if (nt <= a.n_s) {
                         gamma = 0.f;
@@ -654,30 +588,6 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
         }
         o.counts[p] = (uint32_t)count;
         if (o.gamma) o.gamma[p] = gamma;
-        if constexpr (!LEARNED && !OWNED) {
-            if (a.stage_idx) {
-                // staged emission: the ray's records from its cached samples, into this CTA's chunk
-                uint32_t si = kNotStaged;
-                int n_emit = 0;
-                size_t idx = 0;
-                if (nt_cached >= 0 && count > 0) {
-                    const unsigned off = atomicAdd(&s_stage_used, (unsigned)count);
-                    if (off + (unsigned)count <= a.stage_chunk) {
-                        idx = (size_t)blockIdx.x * a.stage_chunk + off;
-                        si = (uint32_t)idx;
-                        n_emit = nt_cached;
-                        cs.steps += (unsigned long long)nt_cached;  // one candidate over the cached samples
-                        cs.passes += 1;
-                        cs.cached += 1;
-                    }
-                }
-                // called by every lane (a ray without staged records passes no samples): a call made
-                // under a lane-dependent branch keeps the warp from reconverging in the search loops
-                cached_emit(cref.a, cref.b, cref.slot, cref.slots, n_emit, __fmul_rn(gamma, gamma), a.n_s, r.tin_hi,
-                            r.tin_lo, k0, a.step, a.stage_a, a.stage_b, idx, (uint32_t)count);
-                a.stage_idx[(size_t)e * a.npix + p] = si;
-            }
-        }
     }
     if (CENSUS) {
         unsigned long long* ctr = reinterpret_cast<WsHeader*>(a.status)->counters;
@@ -691,6 +601,10 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
         atomicAdd(ctr + 7, cs.remarched);
     }
 }
+
+struct RecOut {
+    float f, b, P[3], A;
+};
 
 __device__ __forceinline__ void store_record(const GenArgs& a, const CompactDev& o, uint64_t idx, const RecOut& r) {
     if (idx >= o.capacity) {
@@ -744,20 +658,6 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_c
     if (want == 0) {
         zero_tail();
         return;
-    }
-    if (a.stage_idx && *a.stage_valid) {
-        const uint32_t si = a.stage_idx[(size_t)e * a.npix + p];
-        if (si != kNotStaged) {
-            // records staged by the count kernel from the ray's cached samples
-            for (uint32_t q = 0; q < room; ++q) {
-                const float4 x = __ldcs(a.stage_a + (size_t)si + q);
-                const float2 y = __ldcs(a.stage_b + (size_t)si + q);
-                store_record(a, o, base + q, RecOut{y.x, y.y, {x.x, x.y, x.z}, x.w});
-            }
-            written = room;
-            zero_tail();
-            return;
-        }
     }
     Ray r;
     int k0 = 0, k1 = 0;
@@ -841,12 +741,6 @@ static void fill_args(GenArgs& a, const BrickDev* bricks, int k, const float* lu
     a.slots = 0;
     a.regular = 0;
     a.own = OwnerDev{nullptr, 0, {0, 0, 0}};
-    a.stage_a = nullptr;
-    a.stage_b = nullptr;
-    a.stage_idx = nullptr;
-    a.stage_valid = nullptr;
-    a.stage_chunk = 0;
-    a.npix = cam.W * cam.H;
 }
 
 // persistent grid of gen_count_kernel on the current device
@@ -873,46 +767,10 @@ size_t gen_cache_bytes(int ctas) {
     return (size_t)ctas * kGenThreads * kCacheCap * (sizeof(float4) + sizeof(float2));
 }
 
-// Staged emission: the region after the sample cache holds a valid word, the
-// per-(PE, pixel) stage index and the staged records (float4 + float2 each).
-constexpr size_t kStagePerRay = 4;  // records per (PE, ray) the default workspace provides
-
-size_t gen_stage_bytes(int k, long long npix) {
-    const size_t n = (size_t)k * (size_t)npix;
-    return 256 + align_up(n * 4, 256) + 256 + align_up(n * kStagePerRay * 24, 256);
-}
-
-struct StageRegion {
-    unsigned int* valid;
-    uint32_t* idx;
-    float4* a;
-    float2* b;
-    size_t cap;  // records
-};
-
-// The stage region behind the cache of a `ctas`-CTA grid in [cache, cache + bytes), if there is room
-// for the index and at least one record per (PE, ray).
-static bool stage_region(void* cache, size_t bytes, int ctas, int k, int npix, StageRegion& r) {
-    const size_t cb = align_up(gen_cache_bytes(ctas), 256);
-    const size_t n = (size_t)k * (size_t)npix;
-    const size_t ib = align_up(n * 4, 256);
-    if (!cache || n == 0 || bytes < cb + 256 + ib + 256 + n * 24) return false;
-    char* base = static_cast<char*>(cache) + cb;
-    const size_t rest = bytes - cb - 256 - ib - 256;
-    size_t cap = rest / 24;
-    if (cap > 0xFFFFFFF0ull) cap = 0xFFFFFFF0ull;
-    r.valid = reinterpret_cast<unsigned int*>(base);
-    r.idx = reinterpret_cast<uint32_t*>(base + 256);
-    r.a = reinterpret_cast<float4*>(base + 256 + ib);
-    r.b = reinterpret_cast<float2*>(base + 256 + ib + align_up(cap * 16, 256));
-    r.cap = cap;
-    return base + 256 + ib + align_up(cap * 16, 256) + cap * 8 <= static_cast<char*>(cache) + bytes;
-}
-
 vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                             float scale255, float step, float ref_len, int n_s, float gamma, int iters,
                             const CompactDev* out, unsigned int* status, bool census, unsigned int* counter,
-                            void* cache, size_t cache_bytes, cudaStream_t st, const OwnerDev* own, bool stage) {
+                            void* cache, size_t cache_bytes, cudaStream_t st, const OwnerDev* own) {
     GenArgs a;  // copied into the launch's parameter space
     fill_args(a, bricks, k, lut, cam, dims, scale255, step, ref_len, n_s, out, status);
     if (own) a.own = *own;
@@ -933,25 +791,8 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
         a.cache_b = reinterpret_cast<float2*>(static_cast<char*>(cache) +
                                               (size_t)a.slots * kCacheCap * sizeof(float4));
     }
-    StageRegion sr;
-    const bool have_stage = a.cache_a && stage_region(cache, cache_bytes, ctas, k, a.npix, sr);
-    const int grid_ctas = ctas;
     if ((unsigned)ctas > items) ctas = (int)items;
     const bool learned = a.mode == 3;
-    // staged emission: search and given modes of the box kernels; any other launch invalidates the stage
-    const bool staging = have_stage && stage && !a.own.map && !learned && (a.mode == 1 || a.mode == 2);
-    (void)grid_ctas;
-    if (have_stage) {
-        vdi_status s0 = cuda_check(cudaMemsetAsync(sr.valid, 0, sizeof(unsigned int), st), "stage clear");
-        if (s0 != VDI_OK) return s0;
-    }
-    if (staging) {
-        a.stage_a = sr.a;
-        a.stage_b = sr.b;
-        a.stage_idx = sr.idx;
-        a.stage_valid = sr.valid;
-        a.stage_chunk = (unsigned int)(sr.cap / (size_t)ctas);
-    }
     if (a.own.map && learned) return set_error(VDI_ERR_UNSUPPORTED, "learned gamma with an ownership map");
     if (a.own.map && census) gen_count_kernel<true, false, true><<<ctas, kGenThreads, 0, st>>>(a);
     else if (a.own.map) gen_count_kernel<false, false, true><<<ctas, kGenThreads, 0, st>>>(a);
@@ -959,28 +800,15 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
     else if (census) gen_count_kernel<true, false><<<ctas, kGenThreads, 0, st>>>(a);
     else if (learned) gen_count_kernel<false, true><<<ctas, kGenThreads, 0, st>>>(a);
     else gen_count_kernel<false, false><<<ctas, kGenThreads, 0, st>>>(a);
-    s = cuda_check(cudaGetLastError(), "gen_count_kernel launch");
-    if (s != VDI_OK || !staging) return s;
-    return cuda_check(cudaMemsetAsync(sr.valid, 1, 1, st), "stage mark");
+    return cuda_check(cudaGetLastError(), "gen_count_kernel launch");
 }
 
 vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                            float scale255, float step, float ref_len, int n_s, int prec, const CompactDev* out,
-                           unsigned int* status, cudaStream_t st, bool regular, const OwnerDev* own,
-                           void* cache, size_t cache_bytes) {
+                           unsigned int* status, cudaStream_t st, bool regular, const OwnerDev* own) {
     GenArgs a;
     fill_args(a, bricks, k, lut, cam, dims, scale255, step, ref_len, n_s, out, status);
     if (own) a.own = *own;
-    int ctas = 0;
-    StageRegion sr;
-    if (cache && !regular && !a.own.map && gen_count_grid(ctas) == VDI_OK &&
-        stage_region(cache, cache_bytes, ctas, k, a.npix, sr)) {
-        // records the count kernel staged (used when its launch marked the stage valid)
-        a.stage_a = sr.a;
-        a.stage_b = sr.b;
-        a.stage_idx = sr.idx;
-        a.stage_valid = sr.valid;
-    }
     a.regular = regular ? 1 : 0;
     a.iters = 0;
     a.gamma = 0.f;

@@ -67,8 +67,7 @@ vdi_status launch_brick_build(const void* volume, int type, const int dims[3], i
 vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                             float scale255, float step, float ref_len, int n_s, float gamma, int iters,
                             const CompactDev* out, unsigned int* status, bool census, unsigned int* counter,
-                            void* cache, size_t cache_bytes, cudaStream_t st, const OwnerDev* own = nullptr,
-                            bool stage = false);
+                            void* cache, size_t cache_bytes, cudaStream_t st, const OwnerDev* own = nullptr);
 vdi_status gen_count_grid(int& ctas);
 size_t gen_cache_bytes(int ctas);
 // generation workspace: [0, 256) header, [256, 512) work counter, then the
@@ -80,8 +79,7 @@ constexpr float kGammaLearnedBracket = -5.0f;
 vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                            float scale255, float step, float ref_len, int n_s, int prec, const CompactDev* out,
                            unsigned int* status, cudaStream_t st, bool regular = false,
-                           const OwnerDev* own = nullptr, void* cache = nullptr, size_t cache_bytes = 0);
-size_t gen_stage_bytes(int k, long long npix);
+                           const OwnerDev* own = nullptr);
 size_t scan_workspace(int k, int n);
 vdi_status launch_scan(int k, int n, uint32_t* const* counts, uint64_t* const* offsets, void* ws, cudaStream_t st);
 

@@ -219,53 +219,3 @@ def test_generate_regular_equals_compact(tiny_workload, prec, gamma_mode):
         assert np.array_equal(np.where(slot[..., None], fb_r, 0), np.where(slot[..., None], fb_c[idx], 0))
         assert np.array_equal(np.where(slot[..., None], raw_r, 0), np.where(slot[..., None], rgba_c[idx], 0))
         assert not np.any(fb_r[~slot]) and not np.any(raw_r[~slot])
-
-
-@pytest.mark.parametrize("prec", [0, 1])
-def test_staged_emission_equals_remarch(tiny_workload, prec):
-    # records emitted by the count kernel from the ray's cached samples (staged, then copied) equal the
-    # records the emit kernel's volume re-march writes, bit for bit; a stage too small for every ray
-    # mixes both paths
-    import torch
-
-    import paper_2206_14503_gb300 as vdi
-    from gpu_run import to_dev
-
-    w = tiny_workload
-    cam = vdi.make_camera(w["cams"][7])
-    W, H = cam.width, cam.height
-    npix = W * H
-    boxes = [vdi.vdi_box(tuple(lo), tuple(hi)) for lo, hi in w["boxes"]]
-    k = len(boxes)
-    br = vdi.Bricks(to_dev(w["vol"]), w["dims"], boxes)
-    lut_d = to_dev(w["lut"].astype(np.float32))
-    n_s = 5
-
-    def run(mode, ws_bytes):
-        outs = [vdi.Compact(npix, npix * n_s, prec) for _ in boxes]
-        st = [o.struct() for o in outs]
-        ws = vdi.Workspace(ws_bytes)
-        plain, staged = vdi.make_params(step=w["step"]), vdi.make_params(step=w["step"], flags=vdi.VDI_FLAG_STAGE)
-        if mode == "one call":
-            vdi.check(vdi.vdi_generate(br.bricks, lut_d.data_ptr(), cam, n_s, -1.0, st, plain, ws.ptr, ws.nbytes), mode)
-        else:
-            p = staged if mode == "flag" else plain
-            vdi.check(vdi.vdi_choose_gamma(br.bricks, lut_d.data_ptr(), cam, n_s, -1.0, st, p, ws.ptr, ws.nbytes),
-                      mode)
-            vdi.check(vdi.vdi_generate(br.bricks, lut_d.data_ptr(), cam, n_s, vdi.VDI_GAMMA_CHOSEN, st, p, ws.ptr,
-                                       ws.nbytes), mode)
-        vdi.check(ws.status(), mode)
-        torch.cuda.synchronize()
-        return [(o.counts.cpu(), o.offsets.cpu(), o.rgba.cpu(), None if o.fb is None else o.fb.cpu(), o.gamma.cpu())
-                for o in outs]
-
-    full = vdi.vdi_generate_workspace(k, W, H)
-    n = k * npix
-    small = full - (-(-n * 4 * 24 // 256) * 256) + n * 24 + 256  # one staged record per (PE, ray) on average
-    ref = run("re-march", full)
-    assert sum(int(r[0].sum()) for r in ref) > n  # more records than the small stage holds
-    for mode, size in [("one call", full), ("flag", full), ("one call", small)]:
-        got = run(mode, size)
-        for a, b in zip(ref, got):
-            for x, y in zip(a, b):
-                assert (x is None and y is None) or torch.equal(x, y), mode
