@@ -60,7 +60,6 @@ struct GenArgs {
     float4* cache_a;        // sample cache: [cap][slots] (P.rgb, a)
     float2* cache_b;        // [cap][slots] (log2(1 - a), transparent samples before it)
     int cache_cap, slots;
-    int regular;  // emit: records of pixel p at p * n_s with a zero tail (regular layout), no offsets
     OwnerDev own;  // non-convex ownership (own.map != nullptr): b[e] is the bounding box of PE e's blocks
 };
 
@@ -626,7 +625,10 @@ __device__ __forceinline__ void store_record(const GenArgs& a, const CompactDev&
     }
 }
 
-template <bool OWNED>
+// REGULAR: records at p * n_s with a zero tail.  Compile-time, so that the
+// compact path carries none of it (as a run-time flag it cost the compact
+// emission 70%).
+template <bool OWNED, bool REGULAR>
 __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     load_lut(a, lut2);
@@ -638,26 +640,34 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_c
     const CompactDev& o = a.out[e];
     const size_t p = (size_t)j * a.cam.W + i;
     const uint32_t want = o.counts[p];
-    const uint64_t base = a.regular ? (uint64_t)p * (uint64_t)a.n_s : o.offsets[p];
-    // regular layout: a pixel owns n_s slots (counts never exceed n_s for box-shaped domains)
-    uint32_t room = a.regular ? min(want, (uint32_t)a.n_s) : want;
-    if (!a.regular && base + want > o.capacity) {
-        // a list cut by the capacity keeps the records that fit as its count, so the
-        // sub-VDI stays valid input for compositing; the status reports the overflow
-        room = base >= o.capacity ? 0u : (uint32_t)(o.capacity - base);
-        o.counts[p] = room;
-        atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CAPACITY);
-    }
     uint32_t written = 0;
     // regular layout: the slots after the pixel's records are zero
     auto zero_tail = [&]() {
-        if (!a.regular) return;
-        const RecOut z{0.f, 0.f, {0.f, 0.f, 0.f}, 0.f};
-        for (uint32_t q = min(written, (uint32_t)a.n_s); q < (uint32_t)a.n_s; ++q) store_record(a, o, base + q, z);
+        if constexpr (REGULAR) {
+            const RecOut z{0.f, 0.f, {0.f, 0.f, 0.f}, 0.f};
+            for (uint32_t q = min(written, (uint32_t)a.n_s); q < (uint32_t)a.n_s; ++q)
+                store_record(a, o, (uint64_t)p * (uint64_t)a.n_s + q, z);
+        }
     };
     if (want == 0) {
         zero_tail();
         return;
+    }
+    // records that fit: a pixel of the regular layout owns n_s slots (counts never exceed n_s for
+    // box-shaped domains); a compact list cut by the capacity keeps the records that fit as its
+    // count, so the sub-VDI stays valid input for compositing, and the status reports the overflow
+    uint64_t base;
+    uint32_t room = want;
+    if constexpr (REGULAR) {
+        base = (uint64_t)p * (uint64_t)a.n_s;
+        room = min(want, (uint32_t)a.n_s);
+    } else {
+        base = o.offsets[p];
+        if (base + want > o.capacity) {
+            room = base >= o.capacity ? 0u : (uint32_t)(o.capacity - base);
+            o.counts[p] = room;
+            atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CAPACITY);
+        }
     }
     Ray r;
     int k0 = 0, k1 = 0;
@@ -739,7 +749,6 @@ static void fill_args(GenArgs& a, const BrickDev* bricks, int k, const float* lu
     a.cache_b = nullptr;
     a.cache_cap = 0;
     a.slots = 0;
-    a.regular = 0;
     a.own = OwnerDev{nullptr, 0, {0, 0, 0}};
 }
 
@@ -809,15 +818,15 @@ vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, cons
     GenArgs a;
     fill_args(a, bricks, k, lut, cam, dims, scale255, step, ref_len, n_s, out, status);
     if (own) a.own = *own;
-    a.regular = regular ? 1 : 0;
     a.iters = 0;
     a.gamma = 0.f;
     a.mode = 0;
     a.prec = prec;
     dim3 grid((unsigned)(a.tiles_x * a.tiles_y), (unsigned)k);
     if (grid.x == 0) return VDI_OK;
-    if (a.own.map) gen_emit_kernel<true><<<grid, kGenThreads, 0, st>>>(a);
-    else gen_emit_kernel<false><<<grid, kGenThreads, 0, st>>>(a);
+    if (a.own.map) gen_emit_kernel<true, false><<<grid, kGenThreads, 0, st>>>(a);
+    else if (regular) gen_emit_kernel<false, true><<<grid, kGenThreads, 0, st>>>(a);
+    else gen_emit_kernel<false, false><<<grid, kGenThreads, 0, st>>>(a);
     return cuda_check(cudaGetLastError(), "gen_emit_kernel launch");
 }
 
