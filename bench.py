@@ -395,7 +395,8 @@ def novel_view_eval(vdi, torch, stream, wl, frame0, reg, W, H, reps=5):
             "mpix_s_at_20": W * H / (times["20"] * 1e-3) / 1e6}
 
 
-def pipeline_e2e(vdi, torch, wl, boxes, lut_d, vol_host, cams, capacity, schedule, steps, warmup=2):
+def pipeline_e2e(vdi, torch, wl, boxes, lut_d, vol_host, cams, capacity, schedule, steps, rank=0, world=1,
+                 warmup=2):
     """End to end through the frame pipeline (vdi_pipeline_*): every frame uploads its volume from
     page-locked host memory and downloads the composited regular VDI into page-locked host memory;
     frame f + 1's upload and generation overlap frame f's download (sec. 7).  Timed with CUDA events
@@ -408,14 +409,14 @@ def pipeline_e2e(vdi, torch, wl, boxes, lut_d, vol_host, cams, capacity, schedul
     dsts = [vdi.HostRegular(npix, n_s, vdi.VDI_PREC_F32, gamma=False) for _ in range(2)]
     t = None
     for f in range(warmup):
-        t = pl.submit(vol_host, cams[f % 16], dsts[f % 2])
+        t = pl.submit(vol_host, cams[replica_view(f, rank, world)], dsts[f % 2])
     pl.wait(t)
     s_in, _, s_out = (torch.cuda.ExternalStream(x) for x in pl.streams())
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(s_in)
     for f in range(steps):
-        t = pl.submit(vol_host, cams[f % 16], dsts[f % 2])
+        t = pl.submit(vol_host, cams[replica_view(warmup + f, rank, world)], dsts[f % 2])
     e1.record(s_out)
     pl.wait(t)
     e1.synchronize()
@@ -602,6 +603,31 @@ def gen_traffic(wl):
     return rec["dram_bytes_read"] + rec["dram_bytes_write"]
 
 
+# ---- replicas (one process per GPU, no data-path collective) ----
+
+def replica_view(frame, rank, world, n_views=16):
+    """Orbit view that rank `rank` renders as its frame `frame`: the replicas render different views
+    (weak scaling: every rank does a whole frame per step)."""
+    return (frame * world + rank) % n_views
+
+
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest value over the ranks: the job's time is its slowest rank's."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_step, steps, world, ms):
+    """Whole-job throughput in millions of units per second: every rank's units over the slowest
+    rank's time (ms)."""
+    return units_per_step * steps * world / (ms * 1e-3) / 1e6
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -732,7 +758,7 @@ def main():
 
     # warm-up (also checks capacity and device status)
     for i in range(args.warmup):
-        frame((i * world + rank) % 16)
+        frame(replica_view(i, rank, world))
     stream.synchronize()
     vdi.check(wsg.status(stream), "generate status")
     vdi.check(wsc.status(stream), "composite status")
@@ -750,7 +776,7 @@ def main():
     t_start.record(stream)
     n_in = []
     for s in range(args.steps):
-        frame((args.warmup + s * world + rank) % 16, evs[s])
+        frame(replica_view(args.warmup + s, rank, world), evs[s])
     t_end.record(stream)
     stream.synchronize()
     if dist:
@@ -760,12 +786,8 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     stage_ms = {name: [evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps)]
                 for i, name in enumerate(stages)}
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    rays = npix * args.steps * world
-    value = rays / (total_ms * 1e-3) / 1e6
+    total_ms = max_over_ranks(total_ms, dist, dev)
+    value = job_rate(npix, args.steps, world, total_ms)
 
     # ---- work census and bytes of the timed frames (outside the timed region) ----
     cen_params = vdi.make_params(step=wl.step, ref_len=wl.ref_len, flags=vdi.VDI_FLAG_CENSUS)
@@ -773,7 +795,7 @@ def main():
     comp_bytes = []
     comp_ctr = None
     for s in range(args.steps):
-        view = (args.warmup + s * world + rank) % 16
+        view = replica_view(args.warmup + s, rank, world)
         vdi.check(vdi.vdi_choose_gamma(bricks.bricks, lut_d.data_ptr(), cams[view], n_s, vdi.VDI_GAMMA_SEARCH,
                                        ostructs, cen_params, wsg.ptr, wsg.nbytes, stream), "census")
         c = vdi.vdi_workspace_counters(wsg.ptr, stream)
@@ -839,29 +861,23 @@ def main():
             e0.record(stream)
             for s in range(nsteps):
                 vol_d.copy_(vol_host, non_blocking=True)
-                frame((s * world + rank) % 16)
+                frame(replica_view(s, rank, world))
                 host_counts.copy_(reg.counts, non_blocking=True)
                 host_rgba.copy_(reg.rgba, non_blocking=True)
                 host_fb.copy_(reg.fb, non_blocking=True)
             e1.record(stream)
         stream.synchronize()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        serial = {"value": npix * nsteps * world / (ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        serial = {"value": job_rate(npix, nsteps, world, ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                   "d2h_bytes_per_step": d2h, "path": "brick build, choose_gamma, generate, composite and the copies "
                   "in order on one stream"}
         # the frame pipeline: the public API for a stream of frames
         # at least 8 frames, so that filling and draining the two-frame pipeline is amortised
         p_steps = max(8, nsteps)
-        p_ms, p_d2h = pipeline_e2e(vdi, torch, wl, boxes, lut_d, vol_host, cams, cap, comp_schedule, p_steps)
-        if dist:
-            t = torch.tensor([p_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            p_ms = float(t.item())
-        e2e = {"value": npix * p_steps * world / (p_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        p_ms, p_d2h = pipeline_e2e(vdi, torch, wl, boxes, lut_d, vol_host, cams, cap, comp_schedule, p_steps,
+                                   rank, world)
+        p_ms = max_over_ranks(p_ms, dist, dev)
+        e2e = {"value": job_rate(npix, p_steps, world, p_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": p_d2h, "vdis_per_s": p_steps * world / (p_ms * 1e-3), "frames": p_steps,
                "path": "vdi_pipeline: volume upload, brick build, generation, compositing, VDI download; "
                        "two frames in flight on three streams", "serial": serial}

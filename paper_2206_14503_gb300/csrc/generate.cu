@@ -631,15 +631,21 @@ __device__ __forceinline__ void store_record(const GenArgs& a, const CompactDev&
 template <bool OWNED, bool REGULAR>
 __global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
-    load_lut(a, lut2);
     int i, j;
     tile_pixel(a.tiles_x, blockIdx.x, i, j);
-    if (i >= a.cam.W || j >= a.cam.H) return;
+    const bool inside = i < a.cam.W && j < a.cam.H;
     const int e = blockIdx.y;
     const BrickDev& b = a.b[e];
     const CompactDev& o = a.out[e];
-    const size_t p = (size_t)j * a.cam.W + i;
-    const uint32_t want = o.counts[p];
+    const size_t p = inside ? (size_t)j * a.cam.W + i : 0;
+    const uint32_t want = inside ? o.counts[p] : 0u;
+    // most (PE, tile) pairs hold no record (rays that miss the PE's box): such a CTA of the compact
+    // layout leaves before building the table
+    if constexpr (!REGULAR) {
+        if (!__syncthreads_or(want > 0)) return;
+    }
+    load_lut(a, lut2);
+    if (!inside) return;
     uint32_t written = 0;
     // regular layout: the slots after the pixel's records are zero
     auto zero_tail = [&]() {
