@@ -2,7 +2,7 @@
 //
 // gen_count_kernel chooses gamma per (PE, ray): a fixed value, the per-ray
 // bisection search of sec. 2.4, or a given per-ray value with the search as
-// fallback.  It is a persistent kernel: CTAs of 128 threads take (PE, 16 x 8
+// fallback.  It is a persistent kernel: CTAs of 64 threads take (PE, 16 x 4
 // pixel tile) work items from an atomic counter (the paper used 16 x 16
 // work-groups); each warp is an 8 x 4 pixel block so its rays read
 // neighbouring cells.  Every thread owns a fixed slot of the sample cache in
@@ -63,7 +63,9 @@ struct GenArgs {
     OwnerDev own;  // non-convex ownership (own.map != nullptr): b[e] is the bounding box of PE e's blocks
 };
 
-constexpr int kTileW = 16, kTileH = 8, kGenThreads = 128;
+// gen_count_kernel: CTAs of two warps on 16 x 4 tiles, eight per SM (128 registers), so that a
+// tile's barrier waits on one other warp's searches; gen_emit_kernel: four warps on 16 x 8 tiles
+constexpr int kTileW = 16, kCountTileH = 4, kCountThreads = 64, kEmitTileH = 8, kEmitThreads = 128;
 constexpr int kCacheCap = 640;  // cached non-transparent samples per (PE, ray)
 
 // Work census (VDI_FLAG_CENSUS): kept in registers; the kernel variant
@@ -92,11 +94,12 @@ __device__ __forceinline__ void load_lut(const GenArgs& a, float4* lut2) {
     __syncthreads();
 }
 
-__device__ __forceinline__ void tile_pixel(int tiles_x, int tile, int& i, int& j) {
+// pixel of this thread in tile `tile` (th rows): warps are 8 x 4 blocks, two per row of blocks
+__device__ __forceinline__ void tile_pixel(int tiles_x, int tile, int th, int& i, int& j) {
     int tx = tile % tiles_x, ty = tile / tiles_x;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     i = tx * kTileW + (warp & 1) * 8 + (lane & 7);
-    j = ty * kTileH + (warp >> 1) * 4 + (lane >> 3);
+    j = ty * th + (warp >> 1) * 4 + (lane >> 3);
 }
 
 // PE owning the cell of fixed-point midpoint P (clamped to the volume's cells).
@@ -506,7 +509,7 @@ __device__ __noinline__ float search_call(const Ray& r, int k0, int k1, const Br
 // The learned-gamma refinement (mode 3) is compiled only into the LEARNED
 // instantiation so that the search kernel keeps its register budget.
 template <bool CENSUS, bool LEARNED, bool OWNED = false>
-__global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_constant__ GenArgs a) {
+__global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     __shared__ unsigned int s_item;
     load_lut(a, lut2);
@@ -529,7 +532,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_count_kernel(const __grid_
         if (item >= total) break;
         const int e = (int)(item / tiles);
         int i, j;
-        tile_pixel(a.tiles_x, (int)(item % tiles), i, j);
+        tile_pixel(a.tiles_x, (int)(item % tiles), kCountTileH, i, j);
         if (i >= a.cam.W || j >= a.cam.H) continue;
         const BrickDev& b = a.b[e];
         const CompactDev& o = a.out[e];
@@ -629,10 +632,10 @@ __device__ __forceinline__ void store_record(const GenArgs& a, const CompactDev&
 // compact path carries none of it (as a run-time flag it cost the compact
 // emission 70%).
 template <bool OWNED, bool REGULAR>
-__global__ void __launch_bounds__(kGenThreads, 4) gen_emit_kernel(const __grid_constant__ GenArgs a) {
+__global__ void __launch_bounds__(kEmitThreads, 4) gen_emit_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     int i, j;
-    tile_pixel(a.tiles_x, blockIdx.x, i, j);
+    tile_pixel(a.tiles_x, blockIdx.x, kEmitTileH, i, j);
     const bool inside = i < a.cam.W && j < a.cam.H;
     const int e = blockIdx.y;
     const BrickDev& b = a.b[e];
@@ -749,7 +752,7 @@ static void fill_args(GenArgs& a, const BrickDev* bricks, int k, const float* lu
     a.n_s = n_s;
     a.status = status;
     a.tiles_x = (cam.W + kTileW - 1) / kTileW;
-    a.tiles_y = (cam.H + kTileH - 1) / kTileH;
+    a.tiles_y = (cam.H + kCountTileH - 1) / kCountTileH;  // the count kernel's; the emit launch sets its own
     a.counter = nullptr;
     a.cache_a = nullptr;
     a.cache_b = nullptr;
@@ -769,7 +772,7 @@ vdi_status gen_count_grid(int& ctas) {
                                          gen_count_kernel<false, true>,  gen_count_kernel<true, true>,
                                          gen_count_kernel<false, false, true>, gen_count_kernel<true, false, true>};
     for (int q = 0; q < 6; ++q) {
-        s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, kernels[q], kGenThreads, 0),
+        s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, kernels[q], kCountThreads, 0),
                        "occupancy");
         if (s != VDI_OK) return s;
         if (per_sm_c > per_sm) per_sm = per_sm_c;
@@ -779,7 +782,7 @@ vdi_status gen_count_grid(int& ctas) {
 }
 
 size_t gen_cache_bytes(int ctas) {
-    return (size_t)ctas * kGenThreads * kCacheCap * (sizeof(float4) + sizeof(float2));
+    return (size_t)ctas * kCountThreads * kCacheCap * (sizeof(float4) + sizeof(float2));
 }
 
 vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
@@ -800,7 +803,7 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
     const unsigned items = (unsigned)(a.tiles_x * a.tiles_y) * (unsigned)k;
     if (items == 0) return VDI_OK;
     if (cache && cache_bytes >= gen_cache_bytes(ctas)) {
-        a.slots = ctas * kGenThreads;
+        a.slots = ctas * kCountThreads;
         a.cache_cap = kCacheCap;
         a.cache_a = reinterpret_cast<float4*>(cache);
         a.cache_b = reinterpret_cast<float2*>(static_cast<char*>(cache) +
@@ -809,12 +812,12 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
     if ((unsigned)ctas > items) ctas = (int)items;
     const bool learned = a.mode == 3;
     if (a.own.map && learned) return set_error(VDI_ERR_UNSUPPORTED, "learned gamma with an ownership map");
-    if (a.own.map && census) gen_count_kernel<true, false, true><<<ctas, kGenThreads, 0, st>>>(a);
-    else if (a.own.map) gen_count_kernel<false, false, true><<<ctas, kGenThreads, 0, st>>>(a);
-    else if (census && learned) gen_count_kernel<true, true><<<ctas, kGenThreads, 0, st>>>(a);
-    else if (census) gen_count_kernel<true, false><<<ctas, kGenThreads, 0, st>>>(a);
-    else if (learned) gen_count_kernel<false, true><<<ctas, kGenThreads, 0, st>>>(a);
-    else gen_count_kernel<false, false><<<ctas, kGenThreads, 0, st>>>(a);
+    if (a.own.map && census) gen_count_kernel<true, false, true><<<ctas, kCountThreads, 0, st>>>(a);
+    else if (a.own.map) gen_count_kernel<false, false, true><<<ctas, kCountThreads, 0, st>>>(a);
+    else if (census && learned) gen_count_kernel<true, true><<<ctas, kCountThreads, 0, st>>>(a);
+    else if (census) gen_count_kernel<true, false><<<ctas, kCountThreads, 0, st>>>(a);
+    else if (learned) gen_count_kernel<false, true><<<ctas, kCountThreads, 0, st>>>(a);
+    else gen_count_kernel<false, false><<<ctas, kCountThreads, 0, st>>>(a);
     return cuda_check(cudaGetLastError(), "gen_count_kernel launch");
 }
 
@@ -828,11 +831,12 @@ vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, cons
     a.gamma = 0.f;
     a.mode = 0;
     a.prec = prec;
+    a.tiles_y = (cam.H + kEmitTileH - 1) / kEmitTileH;
     dim3 grid((unsigned)(a.tiles_x * a.tiles_y), (unsigned)k);
     if (grid.x == 0) return VDI_OK;
-    if (a.own.map) gen_emit_kernel<true, false><<<grid, kGenThreads, 0, st>>>(a);
-    else if (regular) gen_emit_kernel<false, true><<<grid, kGenThreads, 0, st>>>(a);
-    else gen_emit_kernel<false, false><<<grid, kGenThreads, 0, st>>>(a);
+    if (a.own.map) gen_emit_kernel<true, false><<<grid, kEmitThreads, 0, st>>>(a);
+    else if (regular) gen_emit_kernel<false, true><<<grid, kEmitThreads, 0, st>>>(a);
+    else gen_emit_kernel<false, false><<<grid, kEmitThreads, 0, st>>>(a);
     return cuda_check(cudaGetLastError(), "gen_emit_kernel launch");
 }
 
