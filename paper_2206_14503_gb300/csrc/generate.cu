@@ -330,9 +330,6 @@ __device__ __forceinline__ void cached_march(const CacheRef& c, int nt, const fl
     for (int q = 0; q < 3; ++q) cnt[q] = st[q].cnt;
 }
 
-__device__ __noinline__ void cached_march_call(const CacheRef& c, int nt, const float g2[3], int cnt[3], Census& cs) {
-    cached_march(c, nt, g2, cnt, cs);
-}
 
 // Bisection march over the volume: three candidates.
 template <bool OWNED = false>
@@ -426,7 +423,7 @@ __device__ __forceinline__ bool bracket_refine(const CacheRef& c, int nt, float 
             g[q] = exp2f(x[q]);
             g2[q] = __fmul_rn(g[q], g[q]);
         }
-        cached_march_call(c, nt, g2, cc, cs);
+        cached_march<false>(c, nt, g2, cc, cs);
         cs.cached += 1;
         if (cc[0] > n_s) return false;
         lo = lg;
@@ -464,7 +461,7 @@ __device__ __forceinline__ bool bracket_refine(const CacheRef& c, int nt, float 
             g[q] = exp2f(x[q]);
             g2[q] = __fmul_rn(g[q], g[q]);
         }
-        cached_march_call(c, nt, g2, cc, cs);
+        cached_march<false>(c, nt, g2, cc, cs);
         cs.cached += 1;
         ++it;
         int child;
@@ -493,21 +490,11 @@ __device__ __forceinline__ bool bracket_refine(const CacheRef& c, int nt, float 
     return true;
 }
 
-// Out-of-line copies for the learned instantiation, whose extra refinement
-// path would otherwise spill.
-__device__ __noinline__ bool bracket_refine_call(const CacheRef& c, int nt, float gp, int cp, int n_s, float& gamma,
-                                                    int& count, Census& cs) {
-    return bracket_refine(c, nt, gp, cp, n_s, gamma, count, cs);
-}
-
-__device__ __noinline__ float search_call(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
-                                             float scale255, int n_s, int iters, int nt, const CacheRef* c,
-                                             int& count, Census& cs) {
-    return search(r, k0, k1, b, lut2, scale255, n_s, iters, nt, c, count, cs);
-}
-
 // The learned-gamma refinement (mode 3) is compiled only into the LEARNED
-// instantiation so that the search kernel keeps its register budget.
+// instantiation so that the search kernel keeps its register budget.  Every
+// march is inlined: out-of-line calls in this persistent loop cost far more
+// than the spills inlining brings (the learned choice took 80.6 ms with the
+// refinement, its marches and the search fallback out of line, 65.6 ms inlined).
 template <bool CENSUS, bool LEARNED, bool OWNED = false>
 __global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
@@ -566,7 +553,7 @@ __global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __gri
                             searched = false;
                         }
                     } else if (LEARNED && nt > a.n_s && use_cache && nt <= a.cache_cap) {
-                        searched = !bracket_refine_call(cref, nt, gamma, c[0], a.n_s, gamma, count, cs);
+                        searched = !bracket_refine(cref, nt, gamma, c[0], a.n_s, gamma, count, cs);
                     }
                 } else {
                     int dummy[1];
@@ -581,8 +568,7 @@ __global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __gri
                         const CacheRef* c = (use_cache && nt <= a.cache_cap) ? &cref : nullptr;
                         cs.searched += 1;
                         cs.overflow += c ? 0 : 1;
-                        gamma = LEARNED ? search_call(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count, cs)
-                                        : search<OWNED>(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count,
+                        gamma = search<OWNED>(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count,
                                                         cs, &a, e, runs);
                     }
                 }
