@@ -237,6 +237,32 @@ __device__ __forceinline__ void gc_run(GenCount& s, float n, float g2, int cap) 
     }
 }
 
+// The same steps without branches, for the cached marches (every cached sample
+// is non-transparent, no budget): both outcomes are computed with the same
+// rounded operations and one is selected, so the decisions are gc_run's and
+// gc_step's bit for bit, and the three candidates of a march form straight-line
+// code whose dependency chains the compiler can interleave.
+__device__ __forceinline__ void gc_run_select(GenCount& s, float n, float g2) {
+    const float zero[3] = {0.f, 0.f, 0.f};
+    const bool open = s.m != 0.f;
+    const bool close = open && criterion(s.P, s.A, s.L2, rcp_approx(open ? s.m : 1.f), zero, g2);
+    s.m = close ? 0.f : (open ? __fadd_rn(s.m, n) : s.m);
+    s.run = open && !close;
+}
+
+__device__ __forceinline__ void gc_step_opaque_select(GenCount& s, const float P[3], float a, float lgT, float g2) {
+    const bool open = s.m != 0.f;
+    const bool fresh = !open || criterion(s.P, s.A, s.L2, rcp_approx(open ? s.m : 1.f), P, g2);
+    const float T = __fsub_rn(1.f, s.A);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s.P[c] = fresh ? P[c] : __fmaf_rn(T, P[c], s.P[c]);
+    s.A = fresh ? a : __fmaf_rn(T, a, s.A);
+    s.L2 = fresh ? lgT : __fadd_rn(s.L2, lgT);
+    s.m = fresh ? 1.f : __fadd_rn(s.m, 1.f);
+    s.cnt += fresh ? 1 : 0;
+    s.run = false;
+}
+
 // ---------------------------------------------------------------------------
 // Marches
 // ---------------------------------------------------------------------------
@@ -319,12 +345,16 @@ __device__ __forceinline__ void cached_march(const CacheRef& c, int nt, const fl
             y1 = __ldcg(c.b + c.at(j + 2));
         }
         const float P[3] = {x.x, x.y, x.z};
+        if (OWNED && y.y < 0.f) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            if (OWNED && y.y < 0.f) st[q].m = 0.f;
-            if (y.y > 0.f) gc_run(st[q], y.y, g2[q], INT_MAX);
-            gc_step(st[q], P, x.w, y.x, g2[q], INT_MAX);
+            for (int q = 0; q < 3; ++q) st[q].m = 0.f;
         }
+        if (y.y > 0.f) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) gc_run_select(st[q], y.y, g2[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) gc_step_opaque_select(st[q], P, x.w, y.x, g2[q]);
     }
 #pragma unroll
     for (int q = 0; q < 3; ++q) cnt[q] = st[q].cnt;
