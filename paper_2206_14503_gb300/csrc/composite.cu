@@ -584,31 +584,6 @@ struct CompCount {
     bool open;
 };
 
-__device__ __forceinline__ void cc_step(CompCount& s, const Piece& x, float g2, int cap) {
-    if (!s.open) {
-        if (x.a > 0.f) {
-            s.P[0] = x.P[0]; s.P[1] = x.P[1]; s.P[2] = x.P[2];
-            s.A = x.a; s.L2 = x.lgT; s.fS = x.f; s.bS = x.b; s.open = true;
-            ++s.cnt;
-        }
-        return;
-    }
-    float lx = __fsub_rn(x.b, x.f), lS = __fsub_rn(s.bS, s.fS);
-    float r = (lx > 0.f && lS > 0.f) ? __fmul_rn(lx, rcp_approx(lS)) : 1.f;
-    if (s.cnt < cap && criterion(s.P, s.A, s.L2, r, x.P, g2)) {
-        if (x.a > 0.f) {
-            s.P[0] = x.P[0]; s.P[1] = x.P[1]; s.P[2] = x.P[2];
-            s.A = x.a; s.L2 = x.lgT; s.fS = x.f; s.bS = x.b;
-            ++s.cnt;
-        } else {
-            s.open = false;
-        }
-    } else {
-        absorb(s.P, s.A, s.L2, x.P, x.a, x.lgT);
-        s.bS = x.b;
-    }
-}
-
 // Counting with decision intervals (see GenCountQ): qlo / qhi bound the
 // gamma^2 for which every decision of the march repeats.
 struct CompCountQ {
@@ -646,7 +621,7 @@ __device__ __forceinline__ void cq_step(CompCountQ& s, const Piece& x, float g2)
     }
 }
 
-// cc_step / cq_step without the budget, written without branches: every outcome
+// cq_step written without branches: every outcome
 // is computed with the same rounded operations and selected, so the decisions
 // are bit for bit those of the branchy steps, and a visitor's candidates form
 // straight-line code whose dependency chains interleave.
@@ -672,12 +647,6 @@ template <typename S>
 __device__ __forceinline__ float piece_ratio(const S& s, const Piece& x) {
     const float lx = __fsub_rn(x.b, x.f), lS = __fsub_rn(s.bS, s.fS);
     return (lx > 0.f && lS > 0.f) ? __fmul_rn(lx, rcp_approx(lS)) : 1.f;
-}
-
-__device__ __forceinline__ void cc_step_select(CompCount& s, const Piece& x, float g2) {
-    const bool crit = s.open && criterion(s.P, s.A, s.L2, piece_ratio(s, x), x.P, g2);
-    const bool opaque = x.a > 0.f;
-    apply_step(s, x, StepSel{opaque && (!s.open || crit), crit && !opaque, s.open && !crit});
 }
 
 __device__ __forceinline__ void cq_step_select(CompCountQ& s, const Piece& x, float g2) {
@@ -713,29 +682,6 @@ struct CountVisitorQ {
         for (int c = 0; c < NC; ++c) {
             if constexpr (SELECT) cq_step_select(st[c], x, g2[c]);
             else cq_step(st[c], x, g2[c]);
-        }
-    }
-};
-
-template <int NC, bool SELECT>
-struct CountVisitor {
-    CompCount st[NC];
-    float g2[NC];
-    int nt;
-    __device__ __forceinline__ void reset() {
-        nt = 0;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            st[c].cnt = 0;
-            st[c].open = false;
-        }
-    }
-    __device__ __forceinline__ void operator()(const Piece& x) {
-        nt += x.a > 0.f;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            if constexpr (SELECT) cc_step_select(st[c], x, g2[c]);
-            else cc_step(st[c], x, g2[c], INT_MAX);
         }
     }
 };
