@@ -26,23 +26,26 @@ __device__ __forceinline__ float node_value(const BrickBuildArgs& a, int x, int 
     return __ldg(reinterpret_cast<const float*>(a.vol) + i);
 }
 
+// A brick holds fewer than 2^31 cells (vdi_brick_build checks), so cell indices
+// and the grid stride fit 32-bit unsigned arithmetic (64-bit division per cell
+// was a large part of this HBM-bound kernel's instructions).
 __global__ void brick_build_kernel(const __grid_constant__ BrickBuildArgs a) {
     int e = blockIdx.y;
-    const int nx = a.n[e][0], ny = a.n[e][1], nz = a.n[e][2];
-    const size_t total = (size_t)nx * ny * nz;
+    const unsigned nx = (unsigned)a.n[e][0], ny = (unsigned)a.n[e][1], nz = (unsigned)a.n[e][2];
+    const unsigned total = nx * ny * nz;
     float4* out = reinterpret_cast<float4*>(a.cells[e]);
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        int lx = (int)(idx % nx);
-        int ly = (int)((idx / nx) % ny);
-        int lz = (int)(idx / ((size_t)nx * ny));
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const unsigned row = idx / nx;
+        int lx = (int)(idx - row * nx);
+        int ly = (int)(row % ny);
+        int lz = (int)(row / ny);
         int x = a.lo[e][0] - 1 + lx, y = a.lo[e][1] - 1 + ly, z = a.lo[e][2] - 1 + lz;
         float4 lo = make_float4(node_value(a, x, y, z), node_value(a, x + 1, y, z), node_value(a, x, y + 1, z),
                                 node_value(a, x + 1, y + 1, z));
         float4 hi = make_float4(node_value(a, x, y, z + 1), node_value(a, x + 1, y, z + 1),
                                 node_value(a, x, y + 1, z + 1), node_value(a, x + 1, y + 1, z + 1));
-        out[2 * idx] = lo;
-        out[2 * idx + 1] = hi;
+        out[2 * (size_t)idx] = lo;
+        out[2 * (size_t)idx + 1] = hi;
     }
 }
 
