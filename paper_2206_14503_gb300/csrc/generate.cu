@@ -648,7 +648,7 @@ __device__ __forceinline__ void store_record(const GenArgs& a, const CompactDev&
 // compact path carries none of it (as a run-time flag it cost the compact
 // emission 70%).
 template <bool OWNED, bool REGULAR>
-__global__ void __launch_bounds__(kEmitThreads, 4) gen_emit_kernel(const __grid_constant__ GenArgs a) {
+__global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     int i, j;
     tile_pixel(a.tiles_x, blockIdx.x, kEmitTileH, i, j);
