@@ -144,6 +144,28 @@ def test_nonconvex_checkerboard_ownership(tiny_workload):
                 assert f1 >= b0
 
 
+def test_nonconvex_lists_beyond_the_budget(tiny_workload):
+    # sec. 5.3 with a budget smaller than a ray's domain runs: every re-entry still opens a
+    # supersegment, so lists exceed N_S, the search ends at gamma = 2 for them, and the composite
+    # of the sub-VDIs is still the DVR image
+    w = tiny_workload
+    cells = [d - 1 for d in w["dims"]]
+    zz, yy, xx = np.meshgrid(*[np.arange(c) // 8 for c in cells[::-1]], indexing="ij")
+    owner = ((xx + yy + zz) % 3).astype(np.int32)
+    cam = w["cams"][4]
+    npx = cam.width * cam.height
+    boxes = [((0, 0, 0), (1, 1, 1))] * 3
+    n_s = 2
+    cnt, gam, recs, _ = oracle.generate(w["vol"], boxes, w["lut"], cam, w["step"], w["ref_len"], n_s, -1.0,
+                                        owner_map=owner, maxrec=64)
+    over = cnt > n_s
+    assert over.any()
+    assert np.all(gam[over] == 2.0)
+    cc, _, cr, _ = oracle.composite(oracle.lists_from_recs(cnt, recs), n_s, n_pix=npx)
+    ref = oracle.dvr(w["vol"], w["lut"], cam, w["step"], w["ref_len"])
+    assert np.abs(oracle.flatten(cc, cr) - ref).max() < 1e-12
+
+
 def test_flat_dvr_limit_case(tiny_workload):
     # sec. 5.3: one sub-supersegment per domain intersection (gamma = 2), composited into a
     # single supersegment per ray, is distributed DVR

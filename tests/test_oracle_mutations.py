@@ -37,6 +37,8 @@ MUTANTS = [
     ("aspect dropped", "* th * (double)c->width / (double)c->height;", "* th;"),
     ("sample at front not midpoint", "double tm = tin + ((double)kk + 0.5) * step;\n        if (!(tm < tout)) break;\n        if (n >= max_s)", "double tm = tin + ((double)kk) * step;\n        if (!(tm < tout)) break;\n        if (n >= max_s)"),
     ("domain exit ignored", "if (p->brk) { /* sec. 5.3", "if (0) { /* sec. 5.3"),
+    ("re-entry held to the budget", "if (p->a > 0.0) OPEN(p);\n            continue;",
+     "if (p->a > 0.0 && count < cap) OPEN(p);\n            continue;"),
     ("back depth includes gaps", "if (p->a > 0.0) bt = p->b;", "bt = p->b;"),
     ("cap off by one", "if (d >= gamma && count < cap)", "if (d >= gamma && count <= cap)"),
     ("ownership closed box", "c[0] >= bx->lo[0] && c[0] < bx->hi[0]", "c[0] >= bx->lo[0] && c[0] <= bx->hi[0]"),
