@@ -75,3 +75,27 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     args = types.SimpleNamespace(dims=512, width=1920, height=1080, steps=2, warmup=3, gpus=2)
     assert bench.run_reference(args) is None
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
+    # the bench reports the committed DRAM-traffic capture only for the workload it was taken on and
+    # only while the kernel's sources hash to the captured ones
+    import json
+    import shutil
+    import types
+
+    import bench
+
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "gen_count_traffic.json")))
+    wl = types.SimpleNamespace(name=rec["workload"])
+    assert bench.gen_traffic(wl) == rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    assert bench.gen_traffic(types.SimpleNamespace(name="another workload")) is None
+    # a copy of the tree whose kernel source differs by one byte
+    fake = tmp_path / "root"
+    for f in rec["sources"] + ["profiles/gen_count_traffic.json"]:
+        (fake / os.path.dirname(f)).mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(bench.ROOT, f), fake / f)
+    src = fake / rec["sources"][0]
+    src.write_bytes(src.read_bytes() + b"\n")
+    monkeypatch.setattr(bench, "ROOT", str(fake))
+    assert bench.gen_traffic(wl) is None
