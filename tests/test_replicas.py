@@ -1,8 +1,10 @@
-"""The N > 1 path of bench.py on CPU: two ranks over gloo (127.0.0.1).
+"""Host logic of bench.py on CPU: the N > 1 path over gloo (127.0.0.1) and the traffic record.
 
 The hot path does not shard (replicas only): each rank renders whole frames of its own views
 and the job's rate is all ranks' rays over the slowest rank's time.  Checks the helpers bench.py
-uses for that: the per-rank view assignment, the max-over-ranks reduction and the aggregate rate.
+uses for that (the per-rank view assignment, the max-over-ranks reduction, the aggregate rate,
+the reference arm's rank-0 rule) and the rule that ties the reported DRAM traffic to the
+kernel sources it was captured on.
 """
 import multiprocessing as mp
 import os
