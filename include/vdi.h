@@ -487,7 +487,9 @@ size_t vdi_pipeline_arena_bytes(const vdi_pipeline_desc* desc);
 /* Creates a pipeline on the current device.  arena: caller-allocated device
  * memory of vdi_pipeline_arena_bytes(desc) bytes, 256-byte aligned, owned by
  * the caller and used until vdi_pipeline_destroy.  tf_lut (device
- * float[256*4]) is copied into the arena.  The pipeline creates three
+ * float[256*4]) is copied into the arena after a device-wide synchronisation
+ * (so the table and the arena may come from any stream); creation is not
+ * stream-ordered and must not be captured in a graph.  The pipeline creates three
  * non-blocking streams, its events and a small page-locked status mirror;
  * *out receives the handle.  One host thread at a time may use a pipeline. */
 vdi_status vdi_pipeline_create(const vdi_pipeline_desc* desc, void* arena, size_t arena_bytes, const float* tf_lut,
