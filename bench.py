@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "VDI gen Mrays/s"
 UNIT = "Mrays/s"
 
-# algorithmic work per unit of the sampling/search kernel:
+# algorithmic work per unit of the sampling/search kernel, counted per operation:
 # one sample evaluation = trilinear interpolation (7 lerps: 14) + value scale (1)
 # + transfer-function lerp (4 lerps: 8) + premultiplication (3) + log transmittance (2)
 OPS_PER_SAMPLE = 28
@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--scale-size", type=int, default=2048, help="image side of the K=32 dense compositing run")
     ap.add_argument("--legs-only", action="store_true",
                     help="skip the frame and print only the compositing legs (for profiling small cases)")
+    ap.add_argument("--detail", default=None,
+                    help="also write every measurement (census, schedules, legs) as JSON to this file")
     return ap.parse_args()
 
 
@@ -628,24 +630,36 @@ def job_rate(units_per_step, steps, world, ms):
     return units_per_step * steps * world / (ms * 1e-3) / 1e6
 
 
+def frame_config(wl, world):
+    """The config object of the bench line (the same for both arms)."""
+    return {"workload": wl.name, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (4.3 GB of bricks, >1 GB of sub-VDIs per frame)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     wl = Workload(args.dims, args.width, args.height)
     per_step = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
-    vals = []
+    vals, secs = [], []
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         cb = cpu_baseline(wl, per_step, pixels_seed=100 + i, views=(i % 16,))
         if i >= args.warmup:
             vals.append(cb)
+            secs.append(time.perf_counter() - t0)
     v = statistics.median([c["value"] for c in vals])
+    # a step is one bounded sample of the frame's rays: ms_per_step is the time such a step took; a
+    # whole frame at the measured rate is reported beside it, labelled as extrapolated
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl.W * wl.H / (v * 1e6),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "ms_per_frame_extrapolated": 1e3 * wl.W * wl.H / (v * 1e6),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl.name, "l2": "inputs larger than L2"},
+            "data": "synthetic", "config": frame_config(wl, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
-                             "sample": vals[0]["sample"]},
+                             "sample": vals[0]["sample"] + " per step (bounded sample of one frame's rays)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -744,7 +758,7 @@ def main():
     comp_schedule = int(req.arr[0].schedule)
     params_c = vdi.make_params(step=wl.step, ref_len=wl.ref_len, schedule=comp_schedule)
     sched_ms = {}
-    for sched in (1, 2, 3, vdi.VDI_SCHED_STAGED):
+    for sched in (1, 2, 3, vdi.VDI_SCHED_STAGED, vdi.VDI_SCHED_LANE):
         p_s = vdi.make_params(step=wl.step, ref_len=wl.ref_len, schedule=sched)
         ea = torch.cuda.Event(enable_timing=True)
         eb = torch.cuda.Event(enable_timing=True)
@@ -831,8 +845,14 @@ def main():
     sm_clock = (clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0))
     # FP32 issue peak: 152 SMs x 128 FP32 lanes x SM clock (one op per lane per clock)
     alu_peak_tops = 152 * 128 * sm_clock * 1e6 / 1e12
-    gen_ops = OPS_PER_SAMPLE * evals + OPS_PER_STEP * steps_sm
+    # executed work counts every candidate of every march; the algorithmic work leaves out the
+    # speculative one: a cached march evaluates the midpoint and both quarter points, of which sequential
+    # bisection uses one quarter point
+    gen_ops_exec = OPS_PER_SAMPLE * evals + OPS_PER_STEP * steps_sm
+    useful_steps = steps_sm - steps_sm // 3  # search mode: every candidate step belongs to a 3-candidate march
+    gen_ops = OPS_PER_SAMPLE * evals + OPS_PER_STEP * useful_steps
     gen_tops = gen_ops / args.steps / (mean["choose_gamma"] * 1e-3) / 1e12
+    gen_tops_exec = gen_ops_exec / args.steps / (mean["choose_gamma"] * 1e-3) / 1e12
     comp_gbs = statistics.mean(comp_bytes) / (mean["composite"] * 1e-3) / 1e9
     if dominant == "composite":
         roof = {"bound": "hbm", "achieved": comp_gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -841,7 +861,10 @@ def main():
     else:
         roof = {"bound": "alu", "achieved": gen_tops, "peak": alu_peak_tops, "unit": "Tops/s",
                 "frac": gen_tops / alu_peak_tops, "traffic": gen_traffic(wl), "kernel": "gen_count_kernel",
-                "peak_source": f"152 SMs x 128 FP32 lanes x {sm_clock:.0f} MHz (median SM clock under load)"}
+                "peak_source": f"152 SMs x 128 FP32 lanes x {sm_clock:.0f} MHz (median SM clock under load)",
+                "work": "28 ops per sample evaluation + 24 per state-machine step of the two bisection "
+                        "candidates a march uses (the speculative third is left out)",
+                "frac_executed": gen_tops_exec / alu_peak_tops}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -896,6 +919,7 @@ def main():
         layout = layout_eval(vdi, torch, stream, wl, bricks, lut_d, cams, outs, params, params_c, wsg, wsc, reg)
         layout["n_s_sweep"] = ns_sweep_eval(vdi, torch, stream, wl, bricks, lut_d, cams, outs, params, wsg, wsc)
 
+    gen_batched = None
     learned = None
     if not args.no_learned and rank == 0:
         learned = learned_eval(vdi, torch, stream)
@@ -913,31 +937,51 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(wl, args.cpu_seconds)
     if rank == 0:
+        gen_detail = {"mrays_s": npix / (mean["choose_gamma"] + mean["scan+emit"] + mean["brick"]) / 1e3,
+                      "sample_evals_per_frame": evals // args.steps,
+                      "sm_steps_per_frame": steps_sm // args.steps, "tops": gen_tops,
+                      "tops_executed": gen_tops_exec,
+                      "marches_per_pe_ray": passes / max(pe_rays, 1),
+                      "pe_rays_per_frame": pe_rays // args.steps,
+                      "searched_frac": searched / max(pe_rays, 1),
+                      "cache_overflow_frac": overflow / max(searched, 1),
+                      "cached_marches_per_frame": cached // args.steps,
+                      "volume_search_marches_per_frame": remarched // args.steps}
+        comp_detail = {"gbs": comp_gbs, "frac_hbm": comp_gbs / hbm_peak, "peak_gbs": hbm_peak,
+                       "peak_source": hbm_src, "records_in_per_frame": int(statistics.mean(n_in)),
+                       "bytes_per_frame": int(statistics.mean(comp_bytes)),
+                       "census": _comp_census(vdi, comp_ctr), "schedule": comp_schedule,
+                       "schedule_ms": sched_ms}
+        detail = {"stages_ms": {kk: round(v, 3) for kk, v in mean.items()}, "composite": comp_detail,
+                  "composite_scale": scale, "composite_batched": batched, "generate_batched": gen_batched,
+                  "render_view": novel, "layout": layout, "nonconvex": nonconvex, "gen": gen_detail,
+                  "learned": learned, "e2e": e2e}
+        if args.detail:
+            with open(args.detail, "w") as f:
+                json.dump(detail, f, indent=1)
+        # the line stays short: the driver keeps the tail of the output
+        summary = {"composite_plain_frac_hbm": round(comp_gbs / hbm_peak, 4),
+                   "composite_plain_ms": round(mean["composite"], 3), "composite_schedule": comp_schedule,
+                   "choose_gamma_ms": round(mean["choose_gamma"], 3)}
+        for key, leg in (("scale_fp32", (scale or {}).get("fp32")), ("scale_fp16", (scale or {}).get("fp16")),
+                         ("batched", batched)):
+            if leg and "ms" in leg:
+                summary[f"composite_{key}_frac_hbm"] = round(leg["frac_hbm"], 4)
+                summary[f"composite_{key}_ms"] = round(leg["ms"], 1)
+        if gen_batched and "mrays_s" in gen_batched:
+            summary["generate_batched_mrays_s"] = round(gen_batched["mrays_s"], 2)
+        if learned:
+            for kk in ("speedup", "count_error", "speedup_single_pass", "count_error_single_pass"):
+                if kk in learned:
+                    summary[f"learned_{kk}"] = round(learned[kk], 4)
+        e2e_line = None if e2e is None else {kk: e2e[kk] for kk in ("value", "unit", "h2d_bytes_per_step",
+                                                                     "d2h_bytes_per_step", "vdis_per_s")}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": wl.name, "parallelism": f"replicas x{world}",
-                           "l2": "inputs larger than L2 (4.3 GB of bricks, >1 GB of sub-VDIs per frame)"},
-                "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "learned": learned,
-                "gpu_launches": launches_per_step * args.steps,
-                "clocks": clk,
-                "stages_ms": {kk: round(v, 3) for kk, v in mean.items()},
-                "composite": {"gbs": comp_gbs, "frac_hbm": comp_gbs / hbm_peak, "peak_gbs": hbm_peak,
-                              "peak_source": hbm_src, "records_in_per_frame": int(statistics.mean(n_in)),
-                              "bytes_per_frame": int(statistics.mean(comp_bytes)),
-                              "census": _comp_census(vdi, comp_ctr), "schedule": comp_schedule,
-                              "schedule_ms": sched_ms},
-                "composite_scale": scale, "composite_batched": batched, "render_view": novel,
-                "layout": layout, "nonconvex": nonconvex,
-                "gen": {"mrays_s": npix / (mean["choose_gamma"] + mean["scan+emit"] + mean["brick"]) / 1e3,
-                        "sample_evals_per_frame": evals // args.steps,
-                        "sm_steps_per_frame": steps_sm // args.steps, "tops": gen_tops,
-                        "marches_per_pe_ray": passes / max(pe_rays, 1),
-                        "pe_rays_per_frame": pe_rays // args.steps,
-                        "searched_frac": searched / max(pe_rays, 1),
-                        "cache_overflow_frac": overflow / max(searched, 1),
-                        "cached_marches_per_frame": cached // args.steps,
-                        "volume_search_marches_per_frame": remarched // args.steps}}
+                "config": frame_config(wl, world), "roofline": roof, "cpu_baseline": cb, "e2e": e2e_line,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+                "stages_ms": {kk: round(v, 3) for kk, v in mean.items()}, "summary": summary}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

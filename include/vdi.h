@@ -29,8 +29,13 @@
  *   - A supersegment ("record") is {front f, back b, premultiplied R,G,B,
  *     opacity A}.  FP32 records are stored as two arrays, float4 rgba[] and
  *     float2 fb[] (24 bytes); FP16 records as one array of 16-byte structs
- *     {float f; float b; half r, g, b, a;} (colour and opacity in IEEE
- *     binary16, depth in FP32).
+ *     {float f; float b; half r, g, b, tau;}: premultiplied colour in IEEE
+ *     binary16, the opacity as its base-2 optical depth tau = -log2(1 - A)
+ *     in binary16 (A = 1 - 2^-tau; tau = +inf for A = 1), depth in FP32.
+ *     tau keeps the opacity's relative precision at every value: binary16 A
+ *     itself would round every A above 1 - 2^-12 to an opaque 1 and move the
+ *     extinction -log2(1 - A) / (b - f) of the compositing mixture by up to
+ *     its whole value.  Kernels accumulate in FP32 either way.
  */
 #ifndef VDI_H
 #define VDI_H
@@ -190,8 +195,8 @@ vdi_status vdi_brick_build(const void* volume, vdi_voltype type, const int32_t d
 /* ------------------------------------------------------------------------ */
 /* Workspace bytes for vdi_generate / vdi_choose_gamma with k PEs of w x h on
  * the current device: a status header, a work counter, the prefix sum's
- * partial sums (8 bytes per 4096 pixels per PE) and a sample cache (640
- * entries of 24 bytes per resident thread: about 1.2 GB on a 152-SM GB300)
+ * partial sums (8 bytes per 4096 pixels per PE) and a sample cache (1024
+ * entries of 8 bytes per resident thread: about 640 MB on a 152-SM GB300)
  * that lets the gamma search run over each ray's
  * cached non-transparent samples instead of re-sampling the volume.  Any
  * workspace of at least 512 + 8 k ceil(w h / 4096) bytes is accepted; without
@@ -270,12 +275,16 @@ vdi_status vdi_generate_owned(const vdi_brick* bricks, int32_t k, const float* t
  * the volume (same result as vdi_generate, slower).
  *   - Limit: k * ceil(W*H / 4096) <= 65536 (e.g. 64 PEs at 2048 x 2048);
  *     larger requests return VDI_ERR_INVALID_ARG without touching the GPU.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before capturing any stream.
- *   - Capacity is always checked synchronously (VDI_FLAG_SYNC_CAPACITY is
- *     implied): the call reads the K totals back and returns VDI_ERR_CAPACITY
- *     before emitting, since there is no workspace status to read later.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress)
+ *     in the CUDA context current at that call, so another context on the
+ *     same device, or one re-created after cudaDeviceReset, gets its own
+ *     copy.  The first call in a context loads the library's device code;
+ *     make that first call before any stream capture begins.
+ *   - The call synchronises `stream`: it reads the K totals back and returns
+ *     VDI_ERR_CAPACITY before emitting (VDI_FLAG_SYNC_CAPACITY is implied),
+ *     and after emission it reads the status word the kernels write into the
+ *     array and returns it (an inconsistent VDI_GAMMA_CHOSEN count, say, is
+ *     VDI_ERR_CUDA), since the caller cannot read that word.
  *   - Every call uses the same array and leaves the previous call's contents
  *     in it (the status header is cleared by each call); calls that overlap
  *     on the GPU (several streams or host threads at once) race on it.
@@ -304,6 +313,13 @@ vdi_status vdi_generate_static_scratch(const vdi_brick* bricks, int32_t k, const
  *     emission of one pixel over its buffered pieces.  Pixels with more than
  *     1024 records, or more pieces than the buffer's rows, take schedule 2 in
  *     a second launch;
+ *   VDI_SCHED_LANE (5, k <= 8; larger k take VDI_SCHED_STAGED): a warp copies
+ *     the records of 32 consecutive pixels into shared memory with coalesced
+ *     loads, each lane sweeps its pixel's lists there, and a pixel whose
+ *     count at gamma = 0 is within n_s is emitted at once; the pixels that
+ *     need the search (or whose records exceed the warp's 480-record slab)
+ *     follow in a second launch, one lane each, over pieces kept in its
+ *     column of the piece buffer;
  *   1, 2, 3 (direct): each thread sweeps its pixel's K lists on every march;
  *     1: list heads in registers (k <= 8), two bisection levels per march;
  *     2: heads in shared memory under a winner tree, two levels per march;
@@ -315,6 +331,7 @@ vdi_status vdi_generate_static_scratch(const vdi_brick* bricks, int32_t k, const
  * at most A); a record's extinction -log2(1 - A) / (b - f) is clamped at
  * 2^56 per unit depth. */
 #define VDI_SCHED_STAGED 4
+#define VDI_SCHED_LANE 5
 size_t vdi_composite_workspace(int32_t k, int32_t w, int32_t h, int32_t n_s);
 vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h, vdi_regular* out,
                          const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream);

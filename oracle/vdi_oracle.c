@@ -21,7 +21,11 @@
  *     leaves the PE's domain);
  *   - flattening by front-to-back "over" and ground-truth DVR: sec. 2.3.
  * Where the paper is silent or its pseudocode is inconsistent, the readings
- * are the ones listed in the design notes (G1..G19); each is marked below.
+ * are marked below where they are used (G1..G19: the opacity compared in
+ * Eq. 1, the tie rule, premultiplied colour, the units of Eq. 2, the control
+ * flow of Algorithm S1, gaps, overlapping PEs, the search constants, what is
+ * counted, the budget, sampling, ownership, depth, camera, early termination,
+ * the regular layout, FP16 storage, synthetic lists and the learned features).
  *
  * Parity status: every function here is pinned by tests in tests/ against
  * closed forms, brute force or invariants, except the places marked
@@ -423,7 +427,9 @@ void oc_exclusive_scan(const int* counts, int n, uint64_t* offsets) {
 /* ---------------------------------------------------------------------- */
 /* Input lists for compositing: one compact sub-VDI per PE.                */
 /* prec 0: fb double[2], rgba double[4]; 1: fb float[2], rgba float[4];    */
-/* 2: 16-byte records {float f, float b, binary16 rgba[4]} in `rgba`.      */
+/* 2: 16-byte records {float f, float b, binary16 R, G, B, tau} in `rgba`:  */
+/* premultiplied colour and the opacity as its base-2 optical depth         */
+/* tau = -log2(1 - A), so A = 1 - 2^-tau (reading G17: FP16 storage).      */
 /* The list of pixel p is records [offsets[p], offsets[p] + counts[p]).   */
 /* ---------------------------------------------------------------------- */
 typedef struct {
@@ -463,7 +469,8 @@ static void read_rec(const oc_lists* L, uint64_t r, double* out) {
         memcpy(&b, base + 4, 4);
         memcpy(h, base + 8, 8);
         out[0] = f; out[1] = b;
-        for (int c = 0; c < 4; ++c) out[2 + c] = oc_half_to_double(h[c]);
+        for (int c = 0; c < 3; ++c) out[2 + c] = oc_half_to_double(h[c]);
+        out[5] = -expm1(-oc_half_to_double(h[3]) * log(2.0));
     }
 }
 

@@ -34,6 +34,7 @@ VDI_GAMMA_CHOSEN = -3.0
 VDI_FLAG_SYNC_CAPACITY = 1
 VDI_FLAG_CENSUS = 2
 VDI_SCHED_STAGED = 4
+VDI_SCHED_LANE = 5
 
 
 class VdiError(RuntimeError):
@@ -525,19 +526,29 @@ class Regular:
         if self.prec == VDI_PREC_F32:
             return self.fb.view(self.npix, self.n_s, 2), self.rgba.view(self.npix, self.n_s, 4)
         raw = self.rgba.view(self.npix, self.n_s, 4)
-        fb = raw[..., 0:2].contiguous().view(torch.float32)
-        rgba = raw[..., 2:4].contiguous().view(torch.float16).float()
-        return fb, rgba
+        return raw[..., 0:2].contiguous().view(torch.float32), _f16_colour(raw[..., 2:4])
+
+
+def _f16_colour(raw):
+    """float32 (R, G, B, A) of the colour halves (int32 [..., 2]) of 16-byte records {f, b, half R, G, B,
+    tau}: premultiplied colour and the optical depth tau = -log2(1 - A), so A = 1 - 2^-tau."""
+    import math
+
+    import torch
+
+    c = raw.contiguous().view(torch.float16).float()
+    c[..., 3] = -torch.expm1(c[..., 3] * -math.log(2.0))
+    return c
 
 
 def compact_records_f32(c: Compact):
-    """(fb [n, 2], rgba [n, 4]) float32 views of a compact sub-VDI's records."""
+    """(fb [n, 2], rgba [n, 4]) float32 views of a compact sub-VDI's records (FP16 records decoded)."""
     import torch
 
     if c.prec == VDI_PREC_F32:
         return c.fb, c.rgba
     raw = c.rgba
-    return raw[:, 0:2].contiguous().view(torch.float32), raw[:, 2:4].contiguous().view(torch.float16).float()
+    return raw[:, 0:2].contiguous().view(torch.float32), _f16_colour(raw[:, 2:4])
 
 
 class Bricks:

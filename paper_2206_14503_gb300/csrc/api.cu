@@ -419,7 +419,7 @@ vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h,
     if (out->n_s < 1) return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: n_s = %d", out->n_s);
     if (params->bisect_iters < 1 || params->bisect_iters > 24)
         return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: bisect_iters");
-    if (params->schedule < 0 || params->schedule > VDI_SCHED_STAGED)
+    if (params->schedule < 0 || params->schedule > VDI_SCHED_LANE)
         return set_error(VDI_ERR_INVALID_ARG, "vdi_composite: schedule %d", params->schedule);
     for (int e = 0; e < k; ++e) {
         if (!pe[e].counts || !pe[e].offsets || !pe[e].rgba)
@@ -444,9 +444,10 @@ vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h,
     if (s != VDI_OK) return s;
     s = launch_composite(pe, k, w, h, out, params->bisect_iters, params->schedule, status, workspace, ws_bytes, st,
                          census);
-    if (s == VDI_ERR_CUDA && (params->schedule == 0 || params->schedule == VDI_SCHED_STAGED) &&
+    if (s == VDI_ERR_CUDA &&
+        (params->schedule == 0 || params->schedule == VDI_SCHED_STAGED || params->schedule == VDI_SCHED_LANE) &&
         ws_bytes < composite_workspace_bytes(1, 1))
-        return set_error(VDI_ERR_WORKSPACE, "vdi_composite: workspace too small for the staged schedule");
+        return set_error(VDI_ERR_WORKSPACE, "vdi_composite: workspace too small for the staged and lane schedules");
     return s;
 }
 
@@ -461,7 +462,7 @@ static vdi_status check_request(const vdi_request& q, int idx, int prec0) {
         return set_error(VDI_ERR_INVALID_ARG, "request %d: image %d x %d", idx, q.w, q.h);
     if (q.out.n_s < 1 || !q.out.counts || !q.out.rgba || (q.out.prec == VDI_PREC_F32 && !q.out.fb))
         return set_error(VDI_ERR_INVALID_ARG, "request %d: output", idx);
-    if (q.schedule < 0 || q.schedule > VDI_SCHED_STAGED)
+    if (q.schedule < 0 || q.schedule > VDI_SCHED_LANE)
         return set_error(VDI_ERR_INVALID_ARG, "request %d: schedule", idx);
     for (int e = 0; e < q.k; ++e) {
         const vdi_compact& c = q.pe[e];
@@ -541,9 +542,9 @@ vdi_status vdi_composite_autotune(vdi_request* reqs, int32_t n, const vdi_params
         int best = default_schedule(q.k);
         float best_ms = 3.0e38f;
         const bool staged_fits = ws_bytes >= composite_workspace_bytes(sub, 1);
-        for (int sched = 1; sched <= VDI_SCHED_STAGED && s == VDI_OK; ++sched) {
-            if (sched == 1 && q.k > 8) continue;
-            if (sched == VDI_SCHED_STAGED && !staged_fits) continue;
+        for (int sched = 1; sched <= VDI_SCHED_LANE && s == VDI_OK; ++sched) {
+            if ((sched == 1 || sched == VDI_SCHED_LANE) && q.k > 8) continue;
+            if ((sched == VDI_SCHED_STAGED || sched == VDI_SCHED_LANE) && !staged_fits) continue;
             float ms_min = 3.0e38f;
             for (int rep = 0; rep < 3 && s == VDI_OK; ++rep) {
                 s = cuda_check(cudaEventRecord(e0, st), "event record");

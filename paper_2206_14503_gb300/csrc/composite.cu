@@ -78,15 +78,28 @@ __device__ __forceinline__ void load_fb(const PeIn& pe, uint64_t idx, float& f, 
     }
 }
 
+// A record's premultiplied colour and opacity, and its optical depth tau =
+// -log2(1 - A): computed from A for FP32 records, stored for FP16 ones.  A
+// record is opaque iff tau is not finite (A >= 1 for FP32 records).
+struct RecC {
+    float4 c;
+    float tau;
+};
+
 template <int PREC>
-__device__ __forceinline__ float4 load_rgba(const PeIn& pe, uint64_t idx) {
-    if (PREC == VDI_PREC_F32) return __ldg(reinterpret_cast<const float4*>(pe.rgba) + idx);
-    uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint4*>(pe.rgba) + idx) + 1);
-    __half2 rg = *reinterpret_cast<__half2*>(&v.x);
-    __half2 ba = *reinterpret_cast<__half2*>(&v.y);
-    float2 a = __half22float2(rg), b2 = __half22float2(ba);
-    return make_float4(a.x, a.y, b2.x, b2.y);
+__device__ __forceinline__ RecC load_rec(const PeIn& pe, uint64_t idx) {
+    RecC r;
+    if (PREC == VDI_PREC_F32) {
+        r.c = __ldg(reinterpret_cast<const float4*>(pe.rgba) + idx);
+        r.tau = -lg2_approx(__fsub_rn(1.f, r.c.w));
+    } else {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint4*>(pe.rgba) + idx) + 1);
+        f16_unpack_col(v, r.c, r.tau);
+    }
+    return r;
 }
+
+__device__ __forceinline__ bool rec_opaque(const RecC& r) { return !(r.tau < INFINITY); }
 
 // ---------------------------------------------------------------------------
 // Piece sweep
@@ -147,7 +160,7 @@ struct Contrib {
 
 __device__ __forceinline__ void u128_zero(U128& x) { x.hi = x.lo = 0ull; }
 
-__device__ __forceinline__ Contrib contrib(const float4& c, float f, float b) {
+__device__ __forceinline__ Contrib contrib(const RecC& x, float f, float b) {
     Contrib r;
     u128_zero(r.M);
 #pragma unroll
@@ -156,15 +169,15 @@ __device__ __forceinline__ Contrib contrib(const float4& c, float f, float b) {
         u128_zero(r.OC[q]);
     }
     r.op = 0;
+    const float4& c = x.c;
     const float col[3] = {c.x, c.y, c.z};
-    if (c.w >= 1.f) {
+    if (rec_opaque(x)) {
         r.op = 1;
 #pragma unroll
         for (int q = 0; q < 3; ++q) r.OC[q] = to_fixed(fminf(fmaxf(col[q], 0.f), kMuMax));
     } else if (c.w > 0.f) {
         const float ia = rcp_approx(c.w);
-        const float mu =
-            fminf(__fmul_rn(-lg2_approx(__fsub_rn(1.f, c.w)), rcp_approx(__fsub_rn(b, f))), kMuMax);
+        const float mu = fminf(__fmul_rn(x.tau, rcp_approx(__fsub_rn(b, f))), kMuMax);
         r.M = to_fixed(mu);
 #pragma unroll
         for (int q = 0; q < 3; ++q) r.MC[q] = to_fixed(fminf(fmaxf(__fmul_rn(mu, __fmul_rn(col[q], ia)), 0.f), kMuMax));
@@ -214,17 +227,17 @@ __device__ __forceinline__ void sums_update(MixSums& m, const Contrib& x) {
 
 // The piece [t, t1] of an active set with sums m; `whole` when exactly one
 // record is active and it spans [t, t1] (its colour and opacity are wc).
-__device__ __forceinline__ void piece_from(const MixSums& m, bool whole, const float4& wc, float t, float t1,
+__device__ __forceinline__ void piece_from(const MixSums& m, bool whole, const RecC& wr, float t, float t1,
                                            Piece& x) {
     x.f = t;
     x.b = t1;
     if (whole) {
         // one record covering the piece exactly: the record itself
-        x.P[0] = wc.x;
-        x.P[1] = wc.y;
-        x.P[2] = wc.z;
-        x.a = wc.w;
-        x.lgT = lg2_approx(__fsub_rn(1.f, wc.w));
+        x.P[0] = wr.c.x;
+        x.P[1] = wr.c.y;
+        x.P[2] = wr.c.z;
+        x.a = wr.c.w;
+        x.lgT = -wr.tau;
         return;
     }
     if (m.nop > 0) {
@@ -256,27 +269,28 @@ __device__ __forceinline__ void piece_from(const MixSums& m, bool whole, const f
 struct Mix {
     MixSums s;
     float lt_f, lt_b;  // bounds of the record started last
-    float4 lt_c;       // and its premultiplied colour and opacity
+    RecC lt_c;         // and its colour, opacity and optical depth
 };
 
 __device__ __forceinline__ void mix_reset(Mix& m) {
     sums_reset(m.s);
     m.lt_f = m.lt_b = -1.f;
-    m.lt_c = make_float4(0.f, 0.f, 0.f, 0.f);
+    m.lt_c.c = make_float4(0.f, 0.f, 0.f, 0.f);
+    m.lt_c.tau = 0.f;
 }
 
 __device__ __forceinline__ void mix_piece(const Mix& m, float t, float t1, Piece& x) {
     piece_from(m.s, m.s.nact == 1 && m.lt_f == t && m.lt_b == t1, m.lt_c, t, t1, x);
 }
 
-__device__ __forceinline__ void mix_start(Mix& m, const float4& c, float f, float b) {
+__device__ __forceinline__ void mix_start(Mix& m, const RecC& c, float f, float b) {
     sums_update<true>(m.s, contrib(c, f, b));
     m.lt_f = f;
     m.lt_b = b;
     m.lt_c = c;
 }
 
-__device__ __forceinline__ void mix_end(Mix& m, const float4& c, float f, float b) {
+__device__ __forceinline__ void mix_end(Mix& m, const RecC& c, float f, float b) {
     sums_update<false>(m.s, contrib(c, f, b));
 }
 
@@ -323,27 +337,26 @@ __device__ __forceinline__ void mixture_piece(const PeIn* pe, const ActiveRec* a
     sums_reset(m);
     m.nact = n;
     for (int i = 0; i < n; ++i) {
-        const float4 c = load_rgba<PREC>(pe[ar[i].e], ar[i].cur);
-        if (c.w >= 1.f) ++m.nop;
+        if (rec_opaque(load_rec<PREC>(pe[ar[i].e], ar[i].cur))) ++m.nop;
     }
     if (m.nop > 0) {
         for (int i = 0; i < n; ++i) {
-            const float4 c = load_rgba<PREC>(pe[ar[i].e], ar[i].cur);
-            if (c.w >= 1.f) {
-                const float col[3] = {c.x, c.y, c.z};
+            const RecC r = load_rec<PREC>(pe[ar[i].e], ar[i].cur);
+            if (rec_opaque(r)) {
+                const float col[3] = {r.c.x, r.c.y, r.c.z};
 #pragma unroll
                 for (int q = 0; q < 3; ++q) u128_add(m.OC[q], to_fixed(fminf(fmaxf(col[q], 0.f), kMuMax)));
             }
         }
     } else {
         for (int i = 0; i < n; ++i) {
-            const Contrib c = contrib(load_rgba<PREC>(pe[ar[i].e], ar[i].cur), ar[i].f, ar[i].b);
+            const Contrib c = contrib(load_rec<PREC>(pe[ar[i].e], ar[i].cur), ar[i].f, ar[i].b);
             u128_add(m.M, c.M);
 #pragma unroll
             for (int q = 0; q < 3; ++q) u128_add(m.MC[q], c.MC[q]);
         }
     }
-    piece_from(m, false, make_float4(0.f, 0.f, 0.f, 0.f), t, t1, x);
+    piece_from(m, false, RecC{make_float4(0.f, 0.f, 0.f, 0.f), 0.f}, t, t1, x);
 }
 
 // Calls visit(piece) for every piece of one pixel in depth order; returns the
@@ -406,7 +419,7 @@ __device__ __forceinline__ int sweep_reg(const PeIn* pe, int k, const uint32_t* 
             if (nact == 1 && lf == t && lb == t1) {
                 MixSums m;
                 sums_reset(m);
-                piece_from(m, true, load_rgba<PREC>(pe[last], lc), t, t1, x);
+                piece_from(m, true, load_rec<PREC>(pe[last], lc), t, t1, x);
             } else {
                 ActiveRec ar[KMAX];
                 int na = 0;
@@ -548,7 +561,7 @@ __device__ __forceinline__ int sweep_smem(const PeIn* pe, int k, uint32_t p, con
             if (t1 != t) break;
             const uint32_t s = h.S(e);
             const uint32_t j = s & ~kActive;
-            const float4 c = load_rgba<PREC>(pe[e], __ldg(pe[e].offsets + p) + j);
+            const RecC c = load_rec<PREC>(pe[e], __ldg(pe[e].offsets + p) + j);
             if (!(s & kActive)) {
                 const float b = h.O(e);
                 mix_start(m, c, t, b);
@@ -695,20 +708,14 @@ struct EmitVisitor {
     size_t base;  // first slot of the pixel
     const OutDev* out;
 
-    __device__ __forceinline__ void store(float f, float b, const float P[3], float A) {
+    // L2 = log2(1 - A), the record's optical depth (stored by the FP16 form)
+    __device__ __forceinline__ void store(float f, float b, const float P[3], float A, float L2) {
         size_t idx = base + written;
         if (out->prec == VDI_PREC_F32) {
             reinterpret_cast<float4*>(out->rgba)[idx] = make_float4(P[0], P[1], P[2], A);
             out->fb[idx] = make_float2(f, b);
         } else {
-            __half2 rg = __floats2half2_rn(P[0], P[1]);
-            __half2 ba = __floats2half2_rn(P[2], A);
-            uint4 v;
-            v.x = __float_as_uint(f);
-            v.y = __float_as_uint(b);
-            v.z = *reinterpret_cast<unsigned int*>(&rg);
-            v.w = *reinterpret_cast<unsigned int*>(&ba);
-            reinterpret_cast<uint4*>(out->rgba)[idx] = v;
+            reinterpret_cast<uint4*>(out->rgba)[idx] = f16_pack(f, b, P[0], P[1], P[2], L2);
         }
         ++written;
     }
@@ -726,7 +733,7 @@ struct EmitVisitor {
         float lx = __fsub_rn(x.b, x.f), lS = __fsub_rn(s.bS, s.fS);
         float r = (lx > 0.f && lS > 0.f) ? __fmul_rn(lx, rcp_approx(lS)) : 1.f;
         if (s.cnt < cap && criterion(s.P, s.A, s.L2, r, x.P, g2)) {
-            if (written < cap) store(s.fS, bt, s.P, s.A);
+            if (written < cap) store(s.fS, bt, s.P, s.A, s.L2);
             if (x.a > 0.f) {
                 s.P[0] = x.P[0]; s.P[1] = x.P[1]; s.P[2] = x.P[2];
                 s.A = x.a; s.L2 = x.lgT; s.fS = x.f; s.bS = x.b;
@@ -887,7 +894,7 @@ __device__ __forceinline__ void composite_search_emit(SW& sw, const OutDev& out,
             cs->pieces += (unsigned long long)np;
         }
     }
-    if (em.s.open && em.written < out.n_s) em.store(em.s.fS, em.bt, em.s.P, em.s.A);
+    if (em.s.open && em.written < out.n_s) em.store(em.s.fS, em.bt, em.s.P, em.s.A, em.s.L2);
     for (int j = em.written; j < out.n_s; ++j) {
         size_t idx = (size_t)p * out.n_s + j;
         if (out.prec == VDI_PREC_F32) {
@@ -1045,8 +1052,7 @@ __device__ __forceinline__ void stage_apply(const PeIn* pe, const StageSmem& S, 
     const uint32_t loc = S.rloc[c];
     const int e = (int)(loc >> 16);
     const float2 fb = S.rfb[c];
-    const float4 col = load_rgba<PREC>(pe[e], S.off[e] + (loc & 0xFFFFu));
-    const Contrib x = contrib(col, fb.x, fb.y);
+    const Contrib x = contrib(load_rec<PREC>(pe[e], S.off[e] + (loc & 0xFFFFu)), fb.x, fb.y);
     if (w & 1u) sums_update<false, OPQ>(a.s, x);
     else sums_update<true, OPQ>(a.s, x);
     a.xr ^= c;
@@ -1094,14 +1100,14 @@ __device__ __forceinline__ void stage_scan(const PeIn* pe, const StageSmem& S, c
         const float t = bound_key(S, srt[i]), t1 = bound_key(S, srt[i + 1]);
         if (!(t < t1)) continue;
         bool whole = false;
-        float4 wc = make_float4(0.f, 0.f, 0.f, 0.f);
+        RecC wc{make_float4(0.f, 0.f, 0.f, 0.f), 0.f};
         if (st.s.nact == 1) {
             const uint32_t c = min(st.xr, nv - 1);
             const float2 fb = S.rfb[c];
             if (fb.x == t && fb.y == t1) {
                 const uint32_t l = S.rloc[c];
                 const int e = (int)(l >> 16);
-                wc = load_rgba<PREC>(pe[e], S.off[e] + (l & 0xFFFFu));
+                wc = load_rec<PREC>(pe[e], S.off[e] + (l & 0xFFFFu));
                 whole = true;
             }
         }
@@ -1166,7 +1172,7 @@ __device__ bool stage_pixel(const PeIn* pe, int k, uint32_t p, StageSmem& S, flo
             j = r - S.pref[e];
             load_fb<PREC>(pe[e], S.off[e] + j, f, b);
             valid = b > f;
-            if (valid) opaque |= load_rgba<PREC>(pe[e], S.off[e] + j).w >= 1.f;
+            if (valid) opaque |= rec_opaque(load_rec<PREC>(pe[e], S.off[e] + j));
         }
         const unsigned m = __ballot_sync(0xffffffffu, valid);
         if (valid) {
@@ -1409,6 +1415,425 @@ __global__ void __launch_bounds__(128) composite_overflow_kernel(const __grid_co
 }
 
 // ---------------------------------------------------------------------------
+// Lane-staged path (short lists: K <= kLaneKMax, a pixel's records fit a warp's
+// slab).  Two launches.
+//
+// composite_lane_kernel: a warp takes 32 consecutive pixels.  It reads their
+// counts and offsets (coalesced over the pixels), then copies the records of
+// as many of them as its shared-memory slab holds, PE by PE: the spans of
+// consecutive pixels of one PE are consecutive in the PE's record array (the
+// layout generation writes), so a warp's loads are coalesced 16- and 8-byte
+// runs; other layouts find each record's pixel by a binary search over the
+// lanes.  Each lane then sweeps its pixel's K lists in the slab into pieces
+// and counts the non-transparent ones: at most n_s means gamma = 0 (sec. 2.4:
+// the count at gamma = 0 is within the budget), and a second sweep emits the
+// pixel's records straight away.  Pixels that need the gamma search, or whose
+// records do not fit the slab, are appended to a list.
+//
+// composite_list_kernel: a warp takes 32 listed pixels; each lane sweeps its
+// pixel's lists from global memory once, writing the pieces into its column of
+// the warp's piece buffer (a few KB per warp in use, so the buffer stays in L2
+// across the search's marches), then runs the search and the emission over the
+// column.  A pixel with more pieces than the column holds is searched over
+// its lists directly.  The pieces are those of every other schedule, bit for
+// bit, so is the result.
+// ---------------------------------------------------------------------------
+constexpr int kLaneKMax = 8;      // PEs the lane path handles (heads in registers)
+constexpr int kLaneWarps = 4;     // warps per CTA of composite_lane_kernel
+constexpr int kLaneRCap = 480;    // records per warp slab
+
+template <int PREC>
+struct LaneSlab;
+template <>
+struct LaneSlab<VDI_PREC_F32> {
+    float4 rgba[kLaneRCap];
+    float2 fb[kLaneRCap];
+    __device__ __forceinline__ float2 bounds(uint32_t i) const { return fb[i]; }
+    __device__ __forceinline__ RecC rec(uint32_t i) const {
+        RecC r;
+        r.c = rgba[i];
+        r.tau = -lg2_approx(__fsub_rn(1.f, r.c.w));
+        return r;
+    }
+    __device__ __forceinline__ void copy(const PeIn& pe, uint64_t src, uint32_t dst) {
+        rgba[dst] = __ldcs(reinterpret_cast<const float4*>(pe.rgba) + src);
+        fb[dst] = __ldcs(pe.fb + src);
+    }
+};
+template <>
+struct LaneSlab<VDI_PREC_F16> {
+    uint4 raw[kLaneRCap];
+    __device__ __forceinline__ float2 bounds(uint32_t i) const {
+        return make_float2(__uint_as_float(raw[i].x), __uint_as_float(raw[i].y));
+    }
+    __device__ __forceinline__ RecC rec(uint32_t i) const {
+        RecC r;
+        f16_unpack_col(make_uint2(raw[i].z, raw[i].w), r.c, r.tau);
+        return r;
+    }
+    __device__ __forceinline__ void copy(const PeIn& pe, uint64_t src, uint32_t dst) {
+        raw[dst] = __ldcs(reinterpret_cast<const uint4*>(pe.rgba) + src);
+    }
+};
+
+// The pieces of one pixel from its K lists in the slab (list e: slab entries
+// [st[e], st[e] + cnt[e])), in depth order: the sweep of sweep_reg with the
+// records read from shared memory.
+// moves a head to its next record with b > f (records with b <= f are ignored)
+template <int PREC>
+__device__ __forceinline__ void slab_next_valid(const LaneSlab<PREC>& S, uint32_t& cur, uint32_t& rem, float& hf,
+                                                float& hb) {
+    while (rem > 0) {
+        const float2 fb = S.bounds(cur);
+        if (fb.y > fb.x) {
+            hf = fb.x;
+            hb = fb.y;
+            return;
+        }
+        ++cur;
+        --rem;
+    }
+}
+
+template <int PREC, typename V>
+__device__ __forceinline__ int sweep_slab(const LaneSlab<PREC>& S, int k, const uint32_t st[kLaneKMax],
+                                          const uint32_t cnt[kLaneKMax], V& visit) {
+    uint32_t cur[kLaneKMax], rem[kLaneKMax];
+    float hf[kLaneKMax], hb[kLaneKMax];
+    float t = kNoEvent;
+#pragma unroll
+    for (int e = 0; e < kLaneKMax; ++e) {
+        rem[e] = 0;
+        hf[e] = hb[e] = 0.f;
+        cur[e] = 0;
+        if (e < k) {
+            cur[e] = st[e];
+            rem[e] = cnt[e];
+            slab_next_valid<PREC>(S, cur[e], rem[e], hf[e], hb[e]);
+            if (rem[e] > 0) t = fminf(t, hf[e]);
+        }
+    }
+    int npieces = 0;
+    while (true) {
+        float t1 = kNoEvent;
+        int nact = 0, last = 0;
+        unsigned act = 0u;
+#pragma unroll
+        for (int e = 0; e < kLaneKMax; ++e) {
+            if (e < k && rem[e] > 0) {
+                if (hf[e] <= t) {
+                    ++nact;
+                    last = e;
+                    act |= 1u << e;
+                    t1 = fminf(t1, hb[e]);
+                } else {
+                    t1 = fminf(t1, hf[e]);
+                }
+            }
+        }
+        if (t1 >= kNoEvent) break;
+        Piece x;
+        if (nact == 0) {
+            x.f = t;
+            x.b = t1;
+            x.P[0] = x.P[1] = x.P[2] = 0.f;
+            x.a = 0.f;
+            x.lgT = 0.f;
+        } else {
+            float lf = 0.f, lb = 0.f;
+            uint32_t lc = 0;
+#pragma unroll
+            for (int e = 0; e < kLaneKMax; ++e) {
+                if (e == last) {
+                    lf = hf[e];
+                    lb = hb[e];
+                    lc = cur[e];
+                }
+            }
+            MixSums m;
+            sums_reset(m);
+            if (nact == 1 && lf == t && lb == t1) {
+                piece_from(m, true, S.rec(lc), t, t1, x);
+            } else {
+                // the active records' mixture, summed exactly (as mixture_piece)
+                m.nact = nact;
+#pragma unroll
+                for (int e = 0; e < kLaneKMax; ++e)
+                    if ((act >> e) & 1u) m.nop += rec_opaque(S.rec(cur[e])) ? 1 : 0;
+                if (m.nop > 0) {
+#pragma unroll
+                    for (int e = 0; e < kLaneKMax; ++e) {
+                        if ((act >> e) & 1u) {
+                            const RecC r = S.rec(cur[e]);
+                            if (rec_opaque(r)) {
+                                const float col[3] = {r.c.x, r.c.y, r.c.z};
+#pragma unroll
+                                for (int q = 0; q < 3; ++q)
+                                    u128_add(m.OC[q], to_fixed(fminf(fmaxf(col[q], 0.f), kMuMax)));
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < kLaneKMax; ++e) {
+                        if ((act >> e) & 1u) {
+                            const Contrib c = contrib(S.rec(cur[e]), hf[e], hb[e]);
+                            u128_add(m.M, c.M);
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) u128_add(m.MC[q], c.MC[q]);
+                        }
+                    }
+                }
+                piece_from(m, false, RecC{make_float4(0.f, 0.f, 0.f, 0.f), 0.f}, t, t1, x);
+            }
+        }
+        visit(x);
+        ++npieces;
+#pragma unroll
+        for (int e = 0; e < kLaneKMax; ++e) {
+            if (((act >> e) & 1u) && hb[e] <= t1) {
+                ++cur[e];
+                --rem[e];
+                slab_next_valid<PREC>(S, cur[e], rem[e], hf[e], hb[e]);
+            }
+        }
+        t = t1;
+    }
+    return npieces;
+}
+
+struct NtVisitor {
+    int nt;
+    __device__ __forceinline__ void operator()(const Piece& x) { nt += x.a > 0.f; }
+};
+
+// writes the zero tail, count and gamma of pixel p after an emission of `written` records
+__device__ __forceinline__ void finish_pixel(const OutDev& out, uint32_t p, int written, float gamma) {
+    for (int j = written; j < out.n_s; ++j) {
+        const size_t idx = (size_t)p * out.n_s + j;
+        if (out.prec == VDI_PREC_F32) {
+            reinterpret_cast<float4*>(out.rgba)[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+            out.fb[idx] = make_float2(0.f, 0.f);
+        } else {
+            reinterpret_cast<uint4*>(out.rgba)[idx] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    out.counts[p] = (uint32_t)written;
+    if (out.gamma) out.gamma[p] = gamma;
+}
+
+struct LaneArgs {
+    unsigned int* counter;  // batch counter
+    uint32_t* list;         // [0]: count, [2..]: pixels for composite_list_kernel
+};
+
+// appends the lanes with `flag` set to the list (one atomic per warp)
+__device__ __forceinline__ void list_push(uint32_t* list, bool flag, uint32_t p) {
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(list, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (flag) list[2 + base + __popc(m & ((1u << lane) - 1u))] = p;
+}
+
+template <int PREC, bool CENSUS>
+__global__ void __launch_bounds__(kLaneWarps * 32) composite_lane_kernel(const __grid_constant__ CompArgs a,
+                                                                        const __grid_constant__ LaneArgs la) {
+    __shared__ LaneSlab<PREC> slabs[kLaneWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    LaneSlab<PREC>& S = slabs[warp];
+    const uint32_t nbatch = ((uint32_t)a.npix + 31u) / 32u;
+    const int k = a.k;
+    CompCensus cs;
+    while (true) {
+        uint32_t batch = 0;
+        if (lane == 0) batch = atomicAdd(la.counter, 1u);
+        batch = __shfl_sync(0xffffffffu, batch, 0);
+        if (batch >= nbatch) break;
+        const uint32_t p = batch * 32u + (uint32_t)lane;
+        const bool valid = p < (uint32_t)a.npix;
+        uint32_t cnt[kLaneKMax];
+        uint64_t off[kLaneKMax];
+        uint32_t tot = 0;
+#pragma unroll
+        for (int e = 0; e < kLaneKMax; ++e) {
+            cnt[e] = 0;
+            off[e] = 0;
+            if (e < k && valid) {
+                cnt[e] = __ldg(a.pe[e].counts + p);
+                off[e] = __ldg(a.pe[e].offsets + p);
+                tot += cnt[e];
+            }
+        }
+        const bool big = valid && tot > (uint32_t)kLaneRCap;
+        list_push(la.list, big, p);
+        bool pending = valid && !big;
+        while (__any_sync(0xffffffffu, pending)) {
+            // this round: the pending lanes, in order, whose records fit the slab together
+            const uint32_t incl = warp_incl_scan_u32(pending ? tot : 0u);
+            const bool take = pending && incl <= (uint32_t)kLaneRCap;
+            pending = pending && !take;
+            uint32_t st[kLaneKMax];
+            uint32_t base_e = 0;
+#pragma unroll
+            for (int e = 0; e < kLaneKMax; ++e) {
+                st[e] = 0;
+                if (e < k) {
+                    const uint32_t ce = take ? cnt[e] : 0u;
+                    const uint32_t ie = warp_incl_scan_u32(ce);
+                    const uint32_t pre = ie - ce;
+                    const uint32_t n_e = __shfl_sync(0xffffffffu, ie, 31);
+                    st[e] = base_e + pre;
+                    // PE e's spans of this round are one run of its record array iff every
+                    // non-empty span starts where the previous ones leave off
+                    const unsigned nz = __ballot_sync(0xffffffffu, ce > 0);
+                    if (nz) {
+                        const int f = __ffs(nz) - 1;
+                        const uint64_t o0 = __shfl_sync(0xffffffffu, off[e], f);
+                        const bool run = !__any_sync(0xffffffffu, ce > 0 && off[e] != o0 + pre);
+                        for (uint32_t r0 = 0; r0 < n_e; r0 += 32) {
+                            const uint32_t r = r0 + (uint32_t)lane;
+                            uint64_t src = o0 + r;
+                            if (!run) {
+                                // the lane whose span holds record r: the last with pre <= r
+                                int lo = 0, hi = 31;
+#pragma unroll
+                                for (int it = 0; it < 5; ++it) {
+                                    const int mid = (lo + hi + 1) >> 1;
+                                    const uint32_t pm = __shfl_sync(0xffffffffu, pre, mid);
+                                    if (pm <= r) lo = mid;
+                                    else hi = mid - 1;
+                                }
+                                const uint64_t oq = __shfl_sync(0xffffffffu, off[e], lo);
+                                const uint32_t pq = __shfl_sync(0xffffffffu, pre, lo);
+                                src = oq + (r - pq);
+                            }
+                            if (r < n_e) S.copy(a.pe[e], src, base_e + r);
+                        }
+                    }
+                    base_e += n_e;
+                }
+            }
+            __syncwarp();
+            bool search = false;
+            if (take) {
+                NtVisitor nv{0};
+                const int np = sweep_slab<PREC>(S, k, st, cnt, nv);
+                if (CENSUS) {
+                    cs.sweeps += 1;
+                    cs.pieces += (unsigned long long)np;
+                }
+                if (nv.nt <= a.out.n_s) {
+                    // gamma = 0: every non-transparent piece is a supersegment
+                    EmitVisitor em;
+                    em.s.cnt = 0;
+                    em.s.open = false;
+                    em.g2 = 0.f;
+                    em.cap = a.out.n_s;
+                    em.bt = 0.f;
+                    em.written = 0;
+                    em.base = (size_t)p * a.out.n_s;
+                    em.out = &a.out;
+                    sweep_slab<PREC>(S, k, st, cnt, em);
+                    if (em.s.open && em.written < a.out.n_s) em.store(em.s.fS, em.bt, em.s.P, em.s.A, em.s.L2);
+                    if (em.written != nv.nt) atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CUDA);
+                    finish_pixel(a.out, p, em.written, 0.f);
+                    if (CENSUS) {
+                        cs.pixels += 1;
+                        cs.sweeps += 1;
+                        cs.pieces += (unsigned long long)np;
+                        cs.records += tot;
+                    }
+                } else {
+                    search = true;
+                }
+            }
+            list_push(la.list, search, p);
+            __syncwarp();
+        }
+    }
+    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
+}
+
+// Pieces of a pixel into its column of the warp's piece buffer (rows are 32
+// elements apart), with the count of non-transparent pieces; pieces past the
+// column's rows are counted, not written.
+struct ColumnWriter {
+    float4* A;
+    float2* B;
+    int rows, n, nt;
+    float f0;
+    __device__ __forceinline__ void operator()(const Piece& x) {
+        if (n == 0) f0 = x.f;
+        if (n < rows) {
+            A[(size_t)n * 32] = make_float4(x.P[0], x.P[1], x.P[2], x.a);
+            B[(size_t)n * 32] = make_float2(x.b, x.lgT);
+        }
+        ++n;
+        nt += x.a > 0.f;
+    }
+};
+
+template <int PREC, bool CENSUS>
+__global__ void __launch_bounds__(kStageWarps * 32) composite_list_kernel(const __grid_constant__ CompArgs a,
+                                                                         const __grid_constant__ StageArgs sa,
+                                                                         uint32_t* list) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t gw = (size_t)blockIdx.x * kStageWarps + warp;
+    float4* wA = sa.bufA + gw * (size_t)sa.rows * 32 + lane;
+    float2* wB = sa.bufB + gw * (size_t)sa.rows * 32 + lane;
+    const uint32_t n = *list;
+    const uint32_t nitems = (n + 31u) / 32u;
+    CompCensus cs;
+    for (uint32_t item = (uint32_t)gw; item < nitems; item += gridDim.x * kStageWarps) {
+        const uint32_t i = item * 32u + (uint32_t)lane;
+        if (i < n) {
+            const uint32_t p = list[2 + i];
+            Sweeper<kLaneKMax, 16, PREC> sw;
+            sw.init(a.pe, a.k, p, nullptr);
+            ColumnWriter cw{wA, wB, sa.rows, 0, 0, 0.f};
+            sw.run(cw);
+            if (CENSUS) {
+                cs.pixels += 1;
+                cs.records += sw.records();
+                cs.sweeps += 1;
+                cs.pieces += (unsigned long long)cw.n;
+            }
+            if (cw.n <= sa.rows) {
+                BufSweeper bs;
+                bs.A = wA;
+                bs.B = wB;
+                bs.n = cw.n;
+                bs.f0 = cw.f0;
+                composite_search_emit<2, CENSUS>(bs, a.out, a.iters, a.status, p, &cs);
+            } else {
+                // more pieces than the column holds: marked for composite_marked_kernel
+                list[2 + i] = p | 0x80000000u;
+            }
+        }
+    }
+    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
+}
+
+// the listed pixels composite_list_kernel marked, swept from their lists on every march
+template <int PREC, bool CENSUS>
+__global__ void __launch_bounds__(128) composite_marked_kernel(const __grid_constant__ CompArgs a,
+                                                               const uint32_t* __restrict__ list) {
+    const uint32_t n = *list;
+    CompCensus cs;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < n; i += gridDim.x * blockDim.x) {
+        const uint32_t v = i < n ? list[2 + i] : 0u;
+        if (v & 0x80000000u)
+            composite_pixel<kLaneKMax, 16, 2, PREC, CENSUS>(a.pe, a.k, a.out, a.iters, a.status, v & 0x7FFFFFFFu,
+                                                            nullptr, &cs);
+    }
+    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
+}
+
+// ---------------------------------------------------------------------------
 // Batched persistent compositing
 // ---------------------------------------------------------------------------
 struct ReqDev {
@@ -1628,6 +2053,40 @@ static cudaError_t launch_staged(bool census, const CompArgs& a, void* workspace
     return launch_overflow<64, PREC>(census, a, sa.overflow, st);
 }
 
+template <int PREC>
+static cudaError_t launch_lane(bool census, const CompArgs& a, void* workspace, size_t ws_bytes, cudaStream_t st) {
+    const uint64_t npix = (uint64_t)a.npix;
+    const size_t ctas = stage_ctas((npix + 31) / 32);
+    const StageArgs sa = stage_args(workspace, ws_bytes, npix, 4, ctas);
+    if (sa.rows == 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(sa.counter, 0, 256 + 8, st);
+    if (e != cudaSuccess) return e;
+    auto k1 = census ? composite_lane_kernel<PREC, true> : composite_lane_kernel<PREC, false>;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, kLaneWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    const uint64_t batches = (npix + 31) / 32;
+    uint64_t blocks = (uint64_t)device_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    const uint64_t need = (batches + kLaneWarps - 1) / kLaneWarps;
+    if (blocks > need) blocks = need > 0 ? need : 1;
+    LaneArgs la;
+    la.counter = sa.counter;
+    la.list = sa.overflow;
+    k1<<<(unsigned)blocks, kLaneWarps * 32, 0, st>>>(a, la);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto k2 = census ? composite_list_kernel<PREC, true> : composite_list_kernel<PREC, false>;
+    k2<<<(unsigned)ctas, kStageWarps * 32, 0, st>>>(a, sa, sa.overflow);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto k3 = census ? composite_marked_kernel<PREC, true> : composite_marked_kernel<PREC, false>;
+    unsigned b3 = (unsigned)((npix + 127) / 128);
+    const unsigned cap3 = (unsigned)device_sms() * 4u;
+    if (b3 > cap3) b3 = cap3;
+    k3<<<b3, 128, 0, st>>>(a, sa.overflow);
+    return cudaGetLastError();
+}
+
 vdi_status launch_composite(const vdi_compact* pe, int k, int w, int h, const vdi_regular* out, int iters,
                             int schedule, unsigned int* status, void* workspace, size_t ws_bytes, cudaStream_t st,
                             bool census) {
@@ -1648,9 +2107,13 @@ vdi_status launch_composite(const vdi_compact* pe, int k, int w, int h, const vd
     if (a.npix == 0) return VDI_OK;
     const bool f32 = prec_in == VDI_PREC_F32;
     cudaError_t e;
+    if (schedule == VDI_SCHED_LANE && k > kLaneKMax) schedule = VDI_SCHED_STAGED;
     if (schedule == VDI_SCHED_STAGED) {
         e = f32 ? launch_staged<VDI_PREC_F32>(census, a, workspace, ws_bytes, st)
                 : launch_staged<VDI_PREC_F16>(census, a, workspace, ws_bytes, st);
+    } else if (schedule == VDI_SCHED_LANE) {
+        e = f32 ? launch_lane<VDI_PREC_F32>(census, a, workspace, ws_bytes, st)
+                : launch_lane<VDI_PREC_F16>(census, a, workspace, ws_bytes, st);
     } else {
         const int threads = 128;
         const unsigned blocks = (unsigned)((a.npix + threads - 1) / threads);
@@ -1691,7 +2154,8 @@ vdi_status batch_table_pack(const vdi_request* reqs, int n, void* host_table, si
         rd[r].item_begin = (uint32_t)items;
         rd[r].pe_begin = (uint32_t)pes;
         rd[r].k = q.k;
-        rd[r].schedule = q.schedule == VDI_SCHED_STAGED || q.schedule == 0 ? VDI_SCHED_STAGED : 2;
+        rd[r].schedule =
+            q.schedule == VDI_SCHED_STAGED || q.schedule == VDI_SCHED_LANE || q.schedule == 0 ? VDI_SCHED_STAGED : 2;
         for (int e = 0; e < q.k; ++e) {
             pd[pes + e].counts = q.pe[e].counts;
             pd[pes + e].offsets = q.pe[e].offsets;

@@ -10,7 +10,12 @@
 //   - the first march over the PE's owned samples counts the non-transparent
 //     samples (the count at gamma = 0) and stores each of them, with the
 //     number of transparent samples before it, in the slot (entry-major, so
-//     a warp's later reads are coalesced);
+//     a warp's later reads are coalesced).  An entry is 8 bytes: the
+//     sample's table coordinate x = v * 255 and that gap.  Classification is
+//     a function of x alone, so a cached march re-classifies x from the
+//     table in shared memory (about 13 operations against the 24-byte
+//     classified sample it replaces) and gets the volume march's colour and
+//     opacity bit for bit;
 //   - every bisection march then runs over the cached samples instead of
 //     re-sampling the volume.  It evaluates a midpoint and both its children;
 //     the sequential bisection choices are replayed from those counts.
@@ -57,8 +62,7 @@ struct GenArgs {
     int tiles_x, tiles_y;
     unsigned int* status;
     unsigned int* counter;  // work-item counter (persistent kernel)
-    float4* cache_a;        // sample cache: [cap][slots] (P.rgb, a)
-    float2* cache_b;        // [cap][slots] (log2(1 - a), transparent samples before it)
+    float2* cache;          // sample cache: [cap][slots] (table coordinate x, transparent samples before it)
     int cache_cap, slots;
     OwnerDev own;  // non-convex ownership (own.map != nullptr): b[e] is the bounding box of PE e's blocks
 };
@@ -66,7 +70,7 @@ struct GenArgs {
 // gen_count_kernel: CTAs of two warps on 16 x 4 tiles, eight per SM (128 registers), so that a
 // tile's barrier waits on one other warp's searches; gen_emit_kernel: four warps on 16 x 8 tiles
 constexpr int kTileW = 16, kCountTileH = 4, kCountThreads = 64, kEmitTileH = 8, kEmitThreads = 128;
-constexpr int kCacheCap = 640;  // cached non-transparent samples per (PE, ray)
+constexpr int kCacheCap = 1024;  // cached non-transparent samples per (PE, ray)
 
 // Work census (VDI_FLAG_CENSUS): kept in registers; the kernel variant
 // without the census never stores it, so the counting is compiled out.
@@ -267,8 +271,7 @@ __device__ __forceinline__ void gc_step_opaque_select(GenCount& s, const float P
 // Marches
 // ---------------------------------------------------------------------------
 struct CacheRef {
-    float4* a;
-    float2* b;
+    float2* e;
     int slot, slots, cap;
     __device__ __forceinline__ size_t at(int j) const { return (size_t)j * slots + slot; }
 };
@@ -291,10 +294,7 @@ __device__ __forceinline__ int first_march(const Ray& r, int k0, int k1, const B
     bool brk = false;
     auto visit = [&](int, const Sample& s) {
         if (s.a > 0.f) {
-            if (c && nt < c->cap) {
-                c->a[c->at(nt)] = make_float4(s.P[0], s.P[1], s.P[2], s.a);
-                c->b[c->at(nt)] = make_float2(s.lgT, (OWNED && brk) ? -1.f : (float)gap);
-            }
+            if (c && nt < c->cap) c->e[c->at(nt)] = make_float2(s.x, (OWNED && brk) ? -1.f : (float)gap);
             if (OWNED && (nruns == 0 || brk)) ++nruns;
             brk = false;
             ++nt;
@@ -322,29 +322,26 @@ __device__ __forceinline__ int first_march(const Ray& r, int k0, int k1, const B
 }
 
 // Bisection march over the cached samples: three candidates.  Entries are
-// read two ahead of their use so the loads overlap the state-machine work.
-// OWNED: a negative gap marks a break before the entry.
+// read two ahead of their use so the loads overlap the state-machine work,
+// and re-classified from the table.  OWNED: a negative gap marks a break
+// before the entry.
 template <bool OWNED = false>
-__device__ __forceinline__ void cached_march(const CacheRef& c, int nt, const float g2[3], int cnt[3], Census& cs) {
+__device__ __forceinline__ void cached_march(const CacheRef& c, int nt, const float4* __restrict__ lut2,
+                                             const float g2[3], int cnt[3], Census& cs) {
     cs.steps += (unsigned long long)nt * 3;
     cs.passes += 1;
     GenCount st[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) gc_reset(st[q]);
-    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
     float2 y0 = make_float2(0.f, 0.f), y1 = y0;
-    if (nt > 0) { x0 = __ldcg(c.a + c.at(0)); y0 = __ldcg(c.b + c.at(0)); }
-    if (nt > 1) { x1 = __ldcg(c.a + c.at(1)); y1 = __ldcg(c.b + c.at(1)); }
+    if (nt > 0) y0 = __ldcg(c.e + c.at(0));
+    if (nt > 1) y1 = __ldcg(c.e + c.at(1));
     for (int j = 0; j < nt; ++j) {
-        const float4 x = x0;
         const float2 y = y0;
-        x0 = x1;
         y0 = y1;
-        if (j + 2 < nt) {
-            x1 = __ldcg(c.a + c.at(j + 2));
-            y1 = __ldcg(c.b + c.at(j + 2));
-        }
-        const float P[3] = {x.x, x.y, x.z};
+        if (j + 2 < nt) y1 = __ldcg(c.e + c.at(j + 2));
+        Sample s;
+        classify_x(y.x, lut2, s);
         if (OWNED && y.y < 0.f) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) st[q].m = 0.f;
@@ -354,7 +351,7 @@ __device__ __forceinline__ void cached_march(const CacheRef& c, int nt, const fl
             for (int q = 0; q < 3; ++q) gc_run_select(st[q], y.y, g2[q]);
         }
 #pragma unroll
-        for (int q = 0; q < 3; ++q) gc_step_opaque_select(st[q], P, x.w, y.x, g2[q]);
+        for (int q = 0; q < 3; ++q) gc_step_opaque_select(st[q], s.P, s.a, s.lgT, g2[q]);
     }
 #pragma unroll
     for (int q = 0; q < 3; ++q) cnt[q] = st[q].cnt;
@@ -390,7 +387,7 @@ __device__ __forceinline__ float search(const Ray& r, int k0, int k1, const Bric
         for (int q = 0; q < 3; ++q) g2[q] = __fmul_rn(g[q], g[q]);
         int cnt[3];
         if (c) {
-            cached_march<OWNED>(*c, nt, g2, cnt, cs);
+            cached_march<OWNED>(*c, nt, lut2, g2, cnt, cs);
             cs.cached += 1;
         } else {
             volume_march<OWNED>(r, k0, k1, b, lut2, scale255, g2, cnt, cs, ga, e);
@@ -431,8 +428,8 @@ __device__ __forceinline__ float search(const Ray& r, int k0, int k1, const Bric
 // per cached march.  Returns false when the bracket holds no feasible gamma
 // (the caller then runs the full search).  The result is the smallest
 // feasible gamma found, within a factor 2^(1/16) of the bracket's threshold.
-__device__ __forceinline__ bool bracket_refine(const CacheRef& c, int nt, float gp, int cp, int n_s, float& gamma,
-                                               int& count, Census& cs) {
+__device__ __forceinline__ bool bracket_refine(const CacheRef& c, int nt, const float4* __restrict__ lut2, float gp,
+                                               int cp, int n_s, float& gamma, int& count, Census& cs) {
     constexpr float R = 4.f;
     constexpr int kLevels = 6;
     const float lg = log2f(fmaxf(gp, 0x1p-30f));
@@ -453,7 +450,7 @@ __device__ __forceinline__ bool bracket_refine(const CacheRef& c, int nt, float 
             g[q] = exp2f(x[q]);
             g2[q] = __fmul_rn(g[q], g[q]);
         }
-        cached_march<false>(c, nt, g2, cc, cs);
+        cached_march<false>(c, nt, lut2, g2, cc, cs);
         cs.cached += 1;
         if (cc[0] > n_s) return false;
         lo = lg;
@@ -491,7 +488,7 @@ __device__ __forceinline__ bool bracket_refine(const CacheRef& c, int nt, float 
             g[q] = exp2f(x[q]);
             g2[q] = __fmul_rn(g[q], g[q]);
         }
-        cached_march<false>(c, nt, g2, cc, cs);
+        cached_march<false>(c, nt, lut2, g2, cc, cs);
         cs.cached += 1;
         ++it;
         int child;
@@ -533,8 +530,7 @@ __global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __gri
     const unsigned tiles = (unsigned)(a.tiles_x * a.tiles_y);
     const unsigned total = tiles * (unsigned)a.k;
     CacheRef cref;
-    cref.a = a.cache_a;
-    cref.b = a.cache_b;
+    cref.e = a.cache;
     cref.slot = blockIdx.x * blockDim.x + threadIdx.x;
     cref.slots = a.slots;
     cref.cap = a.cache_cap;
@@ -568,7 +564,7 @@ __global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __gri
                 first_march<1, OWNED>(r, k0, k1, b, lut2, a.scale255, g2, a.n_s, nullptr, c, cs, &a, e, &runs);
                 count = c[0];
             } else {
-                const bool use_cache = a.cache_a != nullptr;
+                const bool use_cache = a.cache != nullptr;
                 int nt;
                 bool searched = true;
                 if (mode >= 2) {
@@ -583,7 +579,7 @@ __global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __gri
                             searched = false;
                         }
                     } else if (LEARNED && nt > a.n_s && use_cache && nt <= a.cache_cap) {
-                        searched = !bracket_refine(cref, nt, gamma, c[0], a.n_s, gamma, count, cs);
+                        searched = !bracket_refine(cref, nt, lut2, gamma, c[0], a.n_s, gamma, count, cs);
                     }
                 } else {
                     int dummy[1];
@@ -622,6 +618,7 @@ __global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __gri
 
 struct RecOut {
     float f, b, P[3], A;
+    float L2;  // log2(1 - A) of the record: its FP16 form stores -L2
 };
 
 __device__ __forceinline__ void store_record(const GenArgs& a, const CompactDev& o, uint64_t idx, const RecOut& r) {
@@ -633,14 +630,7 @@ __device__ __forceinline__ void store_record(const GenArgs& a, const CompactDev&
         reinterpret_cast<float4*>(o.rgba)[idx] = make_float4(r.P[0], r.P[1], r.P[2], r.A);
         reinterpret_cast<float2*>(o.fb)[idx] = make_float2(r.f, r.b);
     } else {
-        __half2 rg = __floats2half2_rn(r.P[0], r.P[1]);
-        __half2 ba = __floats2half2_rn(r.P[2], r.A);
-        uint4 v;
-        v.x = __float_as_uint(r.f);
-        v.y = __float_as_uint(r.b);
-        v.z = *reinterpret_cast<unsigned int*>(&rg);
-        v.w = *reinterpret_cast<unsigned int*>(&ba);
-        reinterpret_cast<uint4*>(o.rgba)[idx] = v;
+        reinterpret_cast<uint4*>(o.rgba)[idx] = f16_pack(r.f, r.b, r.P[0], r.P[1], r.P[2], r.L2);
     }
 }
 
@@ -669,7 +659,7 @@ __global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_
     // regular layout: the slots after the pixel's records are zero
     auto zero_tail = [&]() {
         if constexpr (REGULAR) {
-            const RecOut z{0.f, 0.f, {0.f, 0.f, 0.f}, 0.f};
+            const RecOut z{0.f, 0.f, {0.f, 0.f, 0.f}, 0.f, 0.f};
             for (uint32_t q = min(written, (uint32_t)a.n_s); q < (uint32_t)a.n_s; ++q)
                 store_record(a, o, (uint64_t)p * (uint64_t)a.n_s + q, z);
         }
@@ -711,7 +701,7 @@ __global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_
         const bool was_open = st.m != 0.f;
         const int before = st.cnt;
         const RecOut cur{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1),
-                         {st.P[0], st.P[1], st.P[2]}, st.A};
+                         {st.P[0], st.P[1], st.P[2]}, st.A, st.L2};
         gc_step(st, s.P, s.a, s.lgT, g2, cap);
         // S closed by this sample: either it was shut (m = 0) or a new one opened
         const bool closed = was_open && (st.m == 0.f || st.cnt != before);
@@ -731,7 +721,7 @@ __global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_
         march_owned(r, k0, k1, b, lut2, a.scale255, a, e, visit, [&]() {
             if (st.m == 0.f) return;
             const RecOut cur{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1),
-                             {st.P[0], st.P[1], st.P[2]}, st.A};
+                             {st.P[0], st.P[1], st.P[2]}, st.A, st.L2};
             if (written < room) store_record(a, o, base + written, cur);
             ++written;
             st.m = 0.f;
@@ -742,7 +732,7 @@ __global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_
     if (st.m != 0.f) {
         if (written < room) {
             RecOut ro{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1), {st.P[0], st.P[1], st.P[2]},
-                      st.A};
+                      st.A, st.L2};
             store_record(a, o, base + written, ro);
         }
         ++written;
@@ -770,8 +760,7 @@ static void fill_args(GenArgs& a, const BrickDev* bricks, int k, const float* lu
     a.tiles_x = (cam.W + kTileW - 1) / kTileW;
     a.tiles_y = (cam.H + kCountTileH - 1) / kCountTileH;  // the count kernel's; the emit launch sets its own
     a.counter = nullptr;
-    a.cache_a = nullptr;
-    a.cache_b = nullptr;
+    a.cache = nullptr;
     a.cache_cap = 0;
     a.slots = 0;
     a.own = OwnerDev{nullptr, 0, {0, 0, 0}};
@@ -798,7 +787,7 @@ vdi_status gen_count_grid(int& ctas) {
 }
 
 size_t gen_cache_bytes(int ctas) {
-    return (size_t)ctas * kCountThreads * kCacheCap * (sizeof(float4) + sizeof(float2));
+    return (size_t)ctas * kCountThreads * kCacheCap * sizeof(float2);
 }
 
 vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
@@ -821,9 +810,7 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
     if (cache && cache_bytes >= gen_cache_bytes(ctas)) {
         a.slots = ctas * kCountThreads;
         a.cache_cap = kCacheCap;
-        a.cache_a = reinterpret_cast<float4*>(cache);
-        a.cache_b = reinterpret_cast<float2*>(static_cast<char*>(cache) +
-                                              (size_t)a.slots * kCacheCap * sizeof(float4));
+        a.cache = reinterpret_cast<float2*>(cache);
     }
     if ((unsigned)ctas > items) ctas = (int)items;
     const bool learned = a.mode == 3;

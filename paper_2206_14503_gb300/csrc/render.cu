@@ -22,10 +22,9 @@ __global__ void flatten_kernel(const uint32_t* __restrict__ counts, const void* 
         if (prec == VDI_PREC_F32) {
             c = __ldg(reinterpret_cast<const float4*>(rgba) + idx);
         } else {
-            uint4 v = __ldg(reinterpret_cast<const uint4*>(rgba) + idx);
-            float2 rg = __half22float2(*reinterpret_cast<__half2*>(&v.z));
-            float2 ba = __half22float2(*reinterpret_cast<__half2*>(&v.w));
-            c = make_float4(rg.x, rg.y, ba.x, ba.y);
+            const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint4*>(rgba) + idx) + 1);
+            float tau;
+            f16_unpack_col(v, c, tau);
         }
         float T = 1.f - A;
         C0 = fmaf(T, c.x, C0);
@@ -106,13 +105,17 @@ __device__ __forceinline__ void load_rec(const NovelArgs& a, size_t idx, float& 
     }
 }
 
-__device__ __forceinline__ float4 load_col(const NovelArgs& a, size_t idx) {
-    if (a.prec == VDI_PREC_F32) return __ldg(reinterpret_cast<const float4*>(a.rgba) + idx);
+// premultiplied colour and opacity of record idx, and its optical depth tau = -log2(1 - A)
+__device__ __forceinline__ float4 load_col(const NovelArgs& a, size_t idx, float& tau) {
+    if (a.prec == VDI_PREC_F32) {
+        const float4 c = __ldg(reinterpret_cast<const float4*>(a.rgba) + idx);
+        tau = -log2f(1.f - c.w);
+        return c;
+    }
     const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint4*>(a.rgba) + idx) + 1);
-    __half2 rg = *reinterpret_cast<const __half2*>(&v.x);
-    __half2 ba = *reinterpret_cast<const __half2*>(&v.y);
-    const float2 x = __half22float2(rg), y = __half22float2(ba);
-    return make_float4(x.x, x.y, y.x, y.y);
+    float4 c;
+    f16_unpack_col(v, c, tau);
+    return c;
 }
 
 // offset u >= 0 from the closest approach at which the distance from G's eye is c
@@ -239,11 +242,12 @@ __global__ void __launch_bounds__(128) novel_view_kernel(const __grid_constant__
                     const float hi = fminf(shell_offset(b, rho), uhi);
                     const float l = hi - lo;
                     if (!(l > 0.f)) continue;
-                    const float4 c = load_col(a, idx);
+                    float tau;
+                    const float4 c = load_col(a, idx, tau);
                     if (c.w <= 0.f) continue;
                     float alpha;
-                    if (c.w >= 1.f) alpha = 1.f;
-                    else alpha = 1.f - exp2f(log2f(1.f - c.w) * (l / (b - f)));
+                    if (!(tau < INFINITY)) alpha = 1.f;
+                    else alpha = 1.f - exp2f(-tau * (l / (b - f)));
                     const float w = T * alpha / c.w;
                     C0 = fmaf(w, c.x, C0);
                     C1 = fmaf(w, c.y, C1);

@@ -10,11 +10,14 @@
 // loads the library holds it until the process exits) and calls vdi_generate
 // with it; nothing is allocated or freed.
 //
-// The array's host-side name is not a device address: its device address is
-// looked up with cudaGetSymbolAddress once per device, with that device
-// current, by the first call made on that device.
-#include <mutex>
-
+// The array's host-side name is not a device address.  A module-scope device
+// array has a different address in every CUDA context (a second context on
+// the same device, or the primary context re-created after cudaDeviceReset),
+// so every call looks the address up with cudaGetSymbolAddress in the
+// context current at that call instead of caching it; the lookup is a table
+// read in the runtime and allocates nothing.  The first call in a context
+// loads the module, which is why that first call belongs before any stream
+// capture begins.
 #include "vdi_internal.h"
 
 namespace vdi {
@@ -28,22 +31,12 @@ constexpr size_t kStaticScratchBytes = kGenFixed + kStaticPartials * sizeof(uint
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-static std::mutex g_scratch_mu;
-static void* g_scratch_ptr[256];
-
 static vdi_status static_scratch_address(void** out) {
-    int dev = 0;
-    vdi_status s = cuda_check(cudaGetDevice(&dev), "vdi_generate_static_scratch: cudaGetDevice");
+    void* p = nullptr;
+    vdi_status s = cuda_check(cudaGetSymbolAddress(&p, g_static_scratch),
+                              "vdi_generate_static_scratch: cudaGetSymbolAddress");
     if (s != VDI_OK) return s;
-    if (dev < 0 || dev >= 256) return set_error(VDI_ERR_CUDA, "vdi_generate_static_scratch: device %d", dev);
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        s = cuda_check(cudaGetSymbolAddress(&p, g_static_scratch), "vdi_generate_static_scratch: cudaGetSymbolAddress");
-        if (s != VDI_OK) return s;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return VDI_OK;
 }
 
@@ -72,5 +65,19 @@ extern "C" vdi_status vdi_generate_static_scratch(const vdi_brick* bricks, int32
     if (s != VDI_OK) return s;
     vdi_params p = *params;
     p.flags |= VDI_FLAG_SYNC_CAPACITY;  // the caller cannot read the status word: report capacity by return
-    return vdi_generate(bricks, k, tf_lut, cam, n_s, gamma, out, &p, scratch, kStaticScratchBytes, stream);
+    s = vdi_generate(bricks, k, tf_lut, cam, n_s, gamma, out, &p, scratch, kStaticScratchBytes, stream);
+    if (s != VDI_OK) return s;
+    // errors the kernels detect land in the status word at the start of the array, which the caller
+    // cannot reach: read it back here and return it
+    unsigned int word = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    s = cuda_check(cudaMemcpyAsync(&word, scratch, sizeof word, cudaMemcpyDeviceToHost, st),
+                   "vdi_generate_static_scratch: status read");
+    if (s != VDI_OK) return s;
+    s = cuda_check(cudaStreamSynchronize(st), "vdi_generate_static_scratch: status sync");
+    if (s != VDI_OK) return s;
+    if (word != 0)
+        return set_error((vdi_status)word, "vdi_generate_static_scratch: device reported: %s",
+                         vdi_status_string((vdi_status)word));
+    return VDI_OK;
 }

@@ -34,6 +34,43 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// ---------------------------------------------------------------------------
+// FP16 record codec.  A 16-byte record is {float f, float b, binary16 R, G, B,
+// binary16 tau}: premultiplied colour and the opacity A stored as its base-2
+// optical depth tau = -log2(1 - A) (+inf for A = 1).  Rounding A itself to
+// binary16 would put every A above 1 - 2^-12 at exactly 1 (an opaque record)
+// and move the extinction -log2(1 - A) / l of the compositing mixture, whose
+// sensitivity to A is 1 / (1 - A), by up to the whole value; tau keeps a
+// relative precision of 2^-11 at every opacity, and A = 1 - 2^-tau then moves
+// by at most ln2 tau 2^-tau 2^-11 <= 1.8e-4.
+// ---------------------------------------------------------------------------
+// A = 1 - 2^-tau, written as -expm1(-tau ln 2) so that small opacities keep
+// their relative precision (colour is P / A)
+__device__ __forceinline__ float f16_opacity(float tau) {
+    return -expm1f(__fmul_rn(-tau, 0.693147180559945309f));
+}
+
+// record -> 16 bytes; L2 = log2(1 - A) of the record (tau = -L2, written as
+// 0 - L2 so that L2 = 0 stores +0)
+__device__ __forceinline__ uint4 f16_pack(float f, float b, float R, float G, float B, float L2) {
+    const __half2 rg = __floats2half2_rn(R, G);
+    const __half2 bt = __floats2half2_rn(B, __fsub_rn(0.f, L2));
+    uint4 v;
+    v.x = __float_as_uint(f);
+    v.y = __float_as_uint(b);
+    v.z = *reinterpret_cast<const unsigned int*>(&rg);
+    v.w = *reinterpret_cast<const unsigned int*>(&bt);
+    return v;
+}
+
+// colour half of a record (its last 8 bytes) -> premultiplied colour, opacity, tau
+__device__ __forceinline__ void f16_unpack_col(uint2 v, float4& c, float& tau) {
+    const float2 rg = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+    const float2 bt = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+    tau = bt.y;
+    c = make_float4(rg.x, rg.y, bt.x, f16_opacity(tau));
+}
+
 // floor of x (|x| < 2^22) without the conversion pipe: (x - 1/2) rounded to the
 // nearest integer by adding 1.5 * 2^23.  Returns the integer and its float.
 // At exact integers the tie may resolve to x - 1 (then the weight x - floor is 1),
@@ -244,6 +281,7 @@ struct Sample {
     float P[3];  // premultiplied colour
     float a;     // opacity over the step
     float lgT;   // log2(1 - a)
+    float x;     // table coordinate v * 255 (clamped): the sample's classification is a function of x alone
 };
 
 // Corner values of the cell holding the fixed-point position P (two float4
@@ -257,19 +295,12 @@ __device__ __forceinline__ void cell_load(const long long P[3], const BrickDev& 
     hi = __ldg(cp + 1);
 }
 
-// Sample at fixed-point midpoint P from its cell's corners (lo = v000 v100 v010
-// v110, hi = v001 v101 v011 v111): trilinear value, classification with the
-// step-corrected table (257 entries of value and difference), premultiplied colour.
-__device__ __forceinline__ void sample_from(float w0, float w1, float w2, const float4& lo, const float4& hi,
-                                            const float4* __restrict__ lut2, float scale255, Sample& s) {
-    float c00 = __fmaf_rn(w0, __fsub_rn(lo.y, lo.x), lo.x);
-    float c10 = __fmaf_rn(w0, __fsub_rn(lo.w, lo.z), lo.z);
-    float c01 = __fmaf_rn(w0, __fsub_rn(hi.y, hi.x), hi.x);
-    float c11 = __fmaf_rn(w0, __fsub_rn(hi.w, hi.z), hi.z);
-    float c0 = __fmaf_rn(w1, __fsub_rn(c10, c00), c00);
-    float c1 = __fmaf_rn(w1, __fsub_rn(c11, c01), c01);
-    float v = __fmaf_rn(w2, __fsub_rn(c1, c0), c0);
-    float x = fminf(fmaxf(__fmul_rn(v, scale255), 0.f), 255.f);
+// Classification of table coordinate x in [0, 255]: the step-corrected table
+// (257 entries of value and difference) interpolated at x, premultiplied
+// colour, log-transmittance.  A function of x alone, so a cached x gives the
+// sample's colour and opacity bit for bit.
+__device__ __forceinline__ void classify_x(float x, const float4* __restrict__ lut2, Sample& s) {
+    s.x = x;
     float fl;
     int i = floor_magic(x, fl);
     float wt = __fsub_rn(x, fl);
@@ -283,6 +314,20 @@ __device__ __forceinline__ void sample_from(float w0, float w1, float w2, const 
     s.P[1] = __fmul_rn(G, A);
     s.P[2] = __fmul_rn(B, A);
     s.lgT = lg2_approx(__fsub_rn(1.f, A));
+}
+
+// Sample at fixed-point midpoint P from its cell's corners (lo = v000 v100 v010
+// v110, hi = v001 v101 v011 v111): trilinear value, then classification.
+__device__ __forceinline__ void sample_from(float w0, float w1, float w2, const float4& lo, const float4& hi,
+                                            const float4* __restrict__ lut2, float scale255, Sample& s) {
+    float c00 = __fmaf_rn(w0, __fsub_rn(lo.y, lo.x), lo.x);
+    float c10 = __fmaf_rn(w0, __fsub_rn(lo.w, lo.z), lo.z);
+    float c01 = __fmaf_rn(w0, __fsub_rn(hi.y, hi.x), hi.x);
+    float c11 = __fmaf_rn(w0, __fsub_rn(hi.w, hi.z), hi.z);
+    float c0 = __fmaf_rn(w1, __fsub_rn(c10, c00), c00);
+    float c1 = __fmaf_rn(w1, __fsub_rn(c11, c01), c01);
+    float v = __fmaf_rn(w2, __fsub_rn(c1, c0), c0);
+    classify_x(fminf(fmaxf(__fmul_rn(v, scale255), 0.f), 255.f), lut2, s);
 }
 
 // March over samples [k0, k1) of ray r in brick b, calling f(k, sample) in

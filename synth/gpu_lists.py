@@ -162,13 +162,17 @@ def dense_set(seed, req, set_, npix, n_s, chunk=1 << 20, device="cuda"):
 
 
 def pack_f16(fb, rgba, chunk=1 << 24):
-    """16-byte records {float32 f, float32 b, float16 r, g, b, a (round to nearest even)} as int32 [n, 4]."""
+    """16-byte records {float32 f, float32 b, float16 R, G, B, tau} as int32 [n, 4]: premultiplied colour
+    and the optical depth tau = -log2(1 - A) (+inf for A = 1), computed in float32 (1 - A is exact for
+    A in [0, 1]) and rounded to nearest even."""
     import torch
 
     n = fb.shape[0]
     out = torch.empty((n, 4), dtype=torch.int32, device=fb.device)
     for i0 in range(0, n, chunk):
         i1 = min(n, i0 + chunk)
+        c = rgba[i0:i1].clone()
+        c[:, 3] = -torch.log2(1.0 - c[:, 3])
         out[i0:i1, 0:2] = fb[i0:i1].view(torch.int32)
-        out[i0:i1, 2:4] = rgba[i0:i1].to(torch.float16).contiguous().view(torch.int32)
+        out[i0:i1, 2:4] = c.to(torch.float16).contiguous().view(torch.int32)
     return out

@@ -20,7 +20,8 @@ def to_dev(a):
 
 def compact_from_numpy(counts, offsets, fb, rgba, prec=1):
     """Device compact sub-VDI from host arrays (fb float [n,2], rgba float [n,4]).  `prec` uses the
-    oracle's codes: 0/1 (float64/float32 arrays) are stored as FP32 records, 2 as FP16 records."""
+    oracle's codes: 0/1 (float64/float32 arrays) are stored as FP32 records, 2 as FP16 records (packed
+    here from fb and rgba, or, with fb None, already packed in rgba as int32 [n, 4])."""
     import paper_2206_14503_gb300 as vdi
 
     n = len(rgba)
@@ -31,27 +32,37 @@ def compact_from_numpy(counts, offsets, fb, rgba, prec=1):
         r = np.ascontiguousarray(rgba, dtype=np.float32).reshape(-1, 4) if n else np.zeros((1, 4), np.float32)
         f = np.ascontiguousarray(fb, dtype=np.float32).reshape(-1, 2) if n else np.zeros((1, 2), np.float32)
         return vdi.Compact.from_tensors(c, o, to_dev(r), to_dev(f), prec)
-    rec = pack_f16_records(fb, rgba) if n else np.zeros((1, 4), np.int32)
+    if fb is None:
+        rec = np.ascontiguousarray(rgba).view(np.int32).reshape(-1, 4) if n else np.zeros((1, 4), np.int32)
+    else:
+        rec = pack_f16_records(fb, rgba) if n else np.zeros((1, 4), np.int32)
     return vdi.Compact.from_tensors(c, o, to_dev(rec), None, prec)
 
 
 def pack_f16_records(fb, rgba):
-    """16-byte records {float f, float b, half r, g, b, a} (round to nearest even) as int32 [n, 4]."""
+    """16-byte records {float f, float b, half R, G, B, tau} as int32 [n, 4]: premultiplied colour and the
+    optical depth tau = -log2(1 - A) (+inf for A = 1), each rounded to nearest even from float64."""
     n = len(fb)
+    c = np.asarray(rgba, dtype=np.float64).reshape(n, 4).copy()
+    with np.errstate(divide="ignore"):
+        c[:, 3] = -np.log2(1.0 - c[:, 3])
     buf = np.zeros((n, 16), dtype=np.uint8)
     buf[:, 0:8] = np.ascontiguousarray(fb, dtype=np.float32).view(np.uint8).reshape(n, 8)
-    buf[:, 8:16] = np.ascontiguousarray(rgba, dtype=np.float32).astype(np.float16).view(np.uint8).reshape(n, 8)
+    buf[:, 8:16] = c.astype(np.float16).view(np.uint8).reshape(n, 8)
     return buf.view(np.int32).reshape(n, 4)
 
 
 def unpack_f16_records(raw):
+    """(fb float32 [n, 2], rgba float64 [n, 4]) of 16-byte records, opacity A = 1 - 2^-tau (in float64,
+    so that packing the result again gives the same records)."""
     raw = np.ascontiguousarray(raw).view(np.uint8).reshape(-1, 16)
     fb = raw[:, 0:8].copy().view(np.float32).reshape(-1, 2)
-    rgba = raw[:, 8:16].copy().view(np.float16).astype(np.float32).reshape(-1, 4)
-    return fb, rgba
+    c = raw[:, 8:16].copy().view(np.float16).astype(np.float64).reshape(-1, 4)
+    c[:, 3] = -np.expm1(-c[:, 3] * np.log(2.0))
+    return fb, c
 
 
-def composite(lists, w, h, n_s, prec_out=0, iters=16):
+def composite(lists, w, h, n_s, prec_out=0, iters=16, schedule=0):
     """lists: per PE (counts, offsets, fb, rgba, prec).  Returns dict of numpy arrays."""
     import paper_2206_14503_gb300 as vdi
 
@@ -59,7 +70,7 @@ def composite(lists, w, h, n_s, prec_out=0, iters=16):
     pes = [compact_from_numpy(*l) for l in lists]
     reg = vdi.Regular(w * h, n_s, prec_out)
     ws = vdi.Workspace(vdi.vdi_composite_workspace(len(pes), w, h, n_s))
-    params = vdi.make_params(bisect_iters=iters)
+    params = vdi.make_params(bisect_iters=iters, schedule=schedule)
     vdi.check(vdi.vdi_composite([p.struct() for p in pes], w, h, reg.struct(), params, ws.ptr, ws.nbytes),
               "vdi_composite")
     vdi.check(ws.status(), "composite status")
@@ -122,8 +133,15 @@ def per_pixel(lists, n_s_max):
     return counts, recs
 
 
-def compare_lists(counts_g, recs_g, counts_o, recs_o, depth_tol, rgba_tol):
-    """Agreement of counts; max |error| over records of pixels whose counts and depths agree."""
+def compare_lists(counts_g, recs_g, counts_o, recs_o, depth_tol, rgba_tol, min_agree=0.999, check=True):
+    """Parity of per-list records (one list per pixel or per (PE, ray)) against the oracle's.
+
+    depth_tol: absolute tolerance of the front and back depths, a scalar or one value per list (the
+    tolerance is 1e-5 of the ray's chord t_out - t_in through the volume; synthetic lists lie on rays of
+    length 1).  A list "agrees" when its count equals the oracle's and every depth bound is within
+    depth_tol; RGBA is compared on the records of agreeing lists only.  With check, fails unless counts
+    agree on at least min_agree of the lists, lists agree (counts and depths) on at least min_agree, and
+    the largest RGBA error is within rgba_tol."""
     counts_g = np.asarray(counts_g).ravel()
     counts_o = np.asarray(counts_o).ravel()
     rg = recs_g.reshape(len(counts_g), -1, 6)
@@ -132,7 +150,27 @@ def compare_lists(counts_g, recs_g, counts_o, recs_o, depth_tol, rgba_tol):
     n = rg.shape[1]
     mask = np.arange(n)[None, :] < counts_o[:, None]
     dd = np.where(mask, np.abs(rg[..., 0:2] - ro[..., 0:2]).max(-1), 0).max(-1)
-    match = same & (dd <= depth_tol)
+    tol = np.broadcast_to(np.asarray(depth_tol, dtype=np.float64).ravel(), dd.shape) if np.ndim(depth_tol) else depth_tol
+    match = same & (dd <= tol)
     err = np.where(mask[match][..., None], np.abs(rg[match][..., 2:6] - ro[match][..., 2:6]), 0)
-    return dict(count_agree=float(same.mean()), depth_agree=float(match.mean()),
-                rgba_max=float(err.max()) if err.size else 0.0, n=len(counts_o))
+    st = dict(count_agree=float(same.mean()) if len(same) else 1.0,
+              depth_agree=float(match.mean()) if len(match) else 1.0,
+              rgba_max=float(err.max()) if err.size else 0.0, n=len(counts_o))
+    if check:
+        assert st["count_agree"] >= min_agree and st["depth_agree"] >= min_agree and st["rgba_max"] <= rgba_tol, st
+    return st
+
+
+def chords(cam, dims, pixels=None):
+    """Length t_out - t_in of each pixel's ray through the volume's box [0, dims - 1] (0 for a miss), from
+    the oracle's ray and slab test."""
+    import oracle
+
+    W, H = cam.width, cam.height
+    pixels = np.arange(W * H) if pixels is None else np.asarray(pixels)
+    out = np.zeros(len(pixels))
+    for n, p in enumerate(pixels):
+        o, d = oracle.ray(cam, int(p) % W, int(p) // W)
+        hit, tin, tout = oracle.hit_box(o, d, dims)
+        out[n] = tout - tin if hit else 0.0
+    return out

@@ -2,10 +2,13 @@
 
 Inputs are seeded synthetic lists (sorted, non-overlapping within a PE,
 overlapping across PEs: premultiplied colour, opacity ~ U[0,1)) and sub-VDIs
-generated by the oracle.  Tolerances: RGBA 1e-5 absolute with FP32 records,
-2e-3 with FP16 colour storage; depth bounds 1e-5; per-pixel counts identical
-on at least 99.9% of pixels; per-record values compared where counts and
-depth bounds agree; flattened images compared on every pixel.
+generated by the oracle.  Tolerances (the benchmark spec's): RGBA 1e-5 absolute
+with FP32 records, 2e-3 with FP16 storage against the FP64 composite of the
+unrounded inputs; depth bounds within 1e-5 of the ray length (synthetic
+depths lie in [0, 1]); per-pixel counts, and counts plus depth bounds,
+identical on at least 99.9% of pixels; per-record values compared where
+counts and depth bounds agree; flattened images compared on every pixel.
+Every schedule is run on the same inputs and must give the same bits.
 """
 import numpy as np
 import pytest
@@ -13,9 +16,16 @@ import pytest
 import oracle
 import synth
 
-from gpu_run import compare_lists, composite, pack_f16_records, unpack_f16_records
+from gpu_run import chords, compare_lists, composite, pack_f16_records
 
 pytestmark = pytest.mark.gpu
+
+
+def _schedules(k):
+    import paper_2206_14503_gb300 as vdi
+
+    return [s for s in (1, 2, 3, vdi.VDI_SCHED_STAGED, vdi.VDI_SCHED_LANE)
+            if not (s in (1, vdi.VDI_SCHED_LANE) and k > 8)]
 
 
 def synth_lists(seed, req, k, npix, n_s, dense=False):
@@ -38,9 +48,7 @@ def test_composite_matches_oracle_synthetic(k, n_s, w, h):
     lists = synth_lists(101 + k, 0, k, npix, n_s)
     g = composite(lists, w, h, n_s)
     cnt, gam, recs = oracle_composite(lists, n_s, npix)
-    st = compare_lists(g["counts"], np.concatenate([g["fb"], g["rgba"]], -1), cnt, recs, 1e-5, 1e-5)
-    assert st["count_agree"] >= 0.999, st
-    assert st["rgba_max"] <= 1e-5, st
+    compare_lists(g["counts"], np.concatenate([g["fb"], g["rgba"]], -1), cnt, recs, 1e-5, 1e-5)
     ref = oracle.flatten(cnt, recs)
     assert np.abs(g["image"] - ref).max() <= 1e-5
     # zero tail
@@ -49,7 +57,12 @@ def test_composite_matches_oracle_synthetic(k, n_s, w, h):
     assert np.all(g["rgba"][tail] == 0) and np.all(g["fb"][tail] == 0)
     # gamma agrees where the counts agree
     same = g["counts"] == cnt
-    assert np.mean(g["gamma"][same] == gam[same]) >= 0.99
+    assert np.mean(g["gamma"][same] == gam[same]) >= 0.999
+    # every schedule gives the same bits
+    for sched in _schedules(k):
+        gs = composite(lists, w, h, n_s, schedule=sched)
+        for key in ("counts", "gamma", "fb", "rgba"):
+            assert np.array_equal(gs[key], g[key]), (sched, key)
 
 
 def test_single_pe_identity_bit_exact():
@@ -76,34 +89,36 @@ def test_composite_of_generated_subvdis(tiny_workload):
         lists.append((c, o, fb.astype(np.float32), rgba.astype(np.float32), 1))
     g = composite(lists, cam.width, cam.height, w["n_s"])
     oc, _, orecs = oracle_composite(lists, w["n_s"], npix)
-    st = compare_lists(g["counts"], np.concatenate([g["fb"], g["rgba"]], -1), oc, orecs, 1e-5, 1e-5)
-    assert st["count_agree"] >= 0.999 and st["rgba_max"] <= 1e-5, st
+    compare_lists(g["counts"], np.concatenate([g["fb"], g["rgba"]], -1), oc, orecs,
+                  1e-5 * chords(cam, w["dims"]), 1e-5)
     # and flattening gives the volume rendering (associativity of over)
     ref = oracle.dvr(w["vol"], w["lut"], cam, w["step"], w["ref_len"])
     assert np.abs(g["image"] - ref).max() <= 1e-5
 
 
 def test_dense_fp16_storage_error():
-    # precision configuration in small: dense lists (n = N_S for every PE and pixel), K = 32, N_S = 32
+    # precision configuration in small: dense lists (n = N_S for every PE and pixel), K = 32, N_S = 32.
+    # FP16 storage (colour and optical depth in binary16) on input and output against the FP64
+    # composite of the unrounded inputs: the benchmark spec's 2e-3
     w, h, k, n_s = 24, 16, 32, 32
     npix = w * h
     lists = synth_lists(0xF16, 0, k, npix, n_s, dense=True)
-    f16 = []
-    for c, o, fb, rgba, _ in lists:
-        raw = pack_f16_records(fb, rgba)
-        f16.append((c, o, None, raw, 2))
-    g16 = composite([(c, o, *unpack_f16_records(raw), 2) for c, o, _, raw, _ in f16], w, h, n_s, prec_out=1)
-    # oracle on the FP16-stored inputs (decoded exactly), FP64 arithmetic
-    cnt, gam, recs = oracle_composite(f16, n_s, npix)
-    st = compare_lists(g16["counts"], np.concatenate([g16["fb"], g16["rgba"]], -1), cnt, recs, 1e-5, 2e-3)
-    assert st["count_agree"] >= 0.99, st
+    f16 = [(c, o, None, pack_f16_records(fb, rgba), 2) for c, o, fb, rgba, _ in lists]
+    g16 = composite(f16, w, h, n_s, prec_out=1)
+    cnt, gam, recs = oracle_composite(lists, n_s, npix)
+    st = compare_lists(g16["counts"], np.concatenate([g16["fb"], g16["rgba"]], -1), cnt, recs, 1e-5, 2e-3,
+                       check=False)
+    print("FP16 storage vs FP64 of the unrounded inputs:", st)
     assert st["rgba_max"] <= 2e-3, st
     assert np.abs(g16["image"] - oracle.flatten(cnt, recs)).max() <= 2e-3
+    # the oracle on the FP16-stored inputs (decoded exactly): the kernels' arithmetic, at 1e-5 on the
+    # colour and the FP16 output's rounding (half an ulp of colour, 1.8e-4 of opacity) on top
+    cnt16, _, recs16 = oracle_composite(f16, n_s, npix)
+    compare_lists(g16["counts"], np.concatenate([g16["fb"], g16["rgba"]], -1), cnt16, recs16, 1e-5, 5e-4)
     # FP32 path on the FP32 inputs
     g32 = composite(lists, w, h, n_s)
     cnt32, _, recs32 = oracle_composite(lists, n_s, npix)
-    st32 = compare_lists(g32["counts"], np.concatenate([g32["fb"], g32["rgba"]], -1), cnt32, recs32, 1e-5, 1e-5)
-    assert st32["count_agree"] >= 0.99 and st32["rgba_max"] <= 1e-5, st32
+    compare_lists(g32["counts"], np.concatenate([g32["fb"], g32["rgba"]], -1), cnt32, recs32, 1e-5, 1e-5)
 
 
 def test_empty_and_degenerate_inputs():
@@ -138,6 +153,5 @@ def test_full_size_sampled_pixels_dense_k32():
     pix = np.sort(rng.choice(npix, 2000, replace=False)).astype(np.int32)
     cnt, gam, recs = oracle_composite(lists, n_s, npix, pixels=pix)
     gr = np.concatenate([g["fb"], g["rgba"]], -1)[pix]
-    st = compare_lists(g["counts"][pix], gr, cnt, recs, 1e-5, 1e-5)
-    assert st["count_agree"] >= 0.99 and st["rgba_max"] <= 1e-5, st
+    compare_lists(g["counts"][pix], gr, cnt, recs, 1e-5, 1e-5)
     assert np.abs(g["image"][pix] - oracle.flatten(cnt, recs)).max() <= 1e-5

@@ -1,12 +1,17 @@
 """GPU sub-VDI generation (vdi_generate through the C ABI) against the FP64 oracle.
 
-Sampling positions are computed in FP32 on the GPU (no FP64 on the device), so
-sample values differ from the FP64 oracle's by the rounding of FP32 coordinates;
-decisions of Eq. 1 that fall within that rounding can flip.  The tolerances:
-per-ray counts identical on >= 99.9% of (PE, ray) pairs, depth bounds within
-1e-5 of the chord length where counts agree, RGBA within GEN_TOL, and the
-flattened composite within GEN_TOL of the oracle's DVR on every pixel.
-GEN_TOL is derived in the design notes from the FP32 position error.
+Sample positions on the GPU are exact to about 1e-12 voxel (double-float ray
+setup, 20.44 fixed-point positions); what differs from the FP64 oracle is the
+FP32 arithmetic of sampling, classification and the state machine, a few
+units of 1e-7 in a sample's colour and opacity.  A decision of Eq. 1 (or of
+the gamma search) whose margin is below that can flip, which changes a list's
+count or a record's bounds.  Tolerances (the benchmark spec's): per-(PE, ray)
+counts identical, and counts plus depth bounds within 1e-5 of the ray's chord
+identical, on at least 99.9% of lists; RGBA within 1e-5 on the records of
+those lists; the flattened composite within 1e-5 of the oracle's DVR on every
+pixel.  Measured on a GB300: RGBA 2.0e-6 (64^3) and 1.9e-6 (512^3), counts
+100%, depth bounds 99.99% (one flipped boundary in 12,000 sampled lists at
+512^3, one in 32,768 at 64^3 with N_S = 30).
 """
 import numpy as np
 import pytest
@@ -14,21 +19,22 @@ import pytest
 import oracle
 import synth
 
-from gpu_run import compare_lists, composite, generate, per_pixel
+from gpu_run import chords, compare_lists, composite, generate, per_pixel
 
 pytestmark = pytest.mark.gpu
 
-GEN_TOL_TINY = 1e-5   # 64^3 volume: coordinates < 64, FP32 position error < 1e-5 voxel
-GEN_TOL_512 = 1e-4    # 512^3 volume: see the design notes (FP32 coordinate rounding)
+TOL = 1e-5  # RGBA, FP32 records
+DEPTH_REL = 1e-5  # depth bounds, relative to the ray's chord
 
 
-def _check_gen(g_lists, counts_o, recs_o, tol, depth_tol=1e-4):
-    k = len(g_lists)
+def _check_gen(g_lists, counts_o, recs_o, chord, pix=None):
     n_max = recs_o.shape[2]
     cg, rg = per_pixel(g_lists, n_max)
+    if pix is not None:
+        cg, rg = cg[:, pix], rg[:, pix]
     assert cg.max() <= n_max
-    st = compare_lists(cg, rg, counts_o, recs_o, depth_tol, tol)
-    return st
+    k = cg.shape[0]
+    return compare_lists(cg, rg, counts_o, recs_o, np.tile(DEPTH_REL * chord, k), TOL)
 
 
 def test_generate_fixed_gamma_tiny(tiny_workload):
@@ -37,8 +43,7 @@ def test_generate_fixed_gamma_tiny(tiny_workload):
     lists, gam = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, w["n_s"], w["gamma"], step=w["step"])
     cnt, ogam, recs, _ = oracle.generate(w["vol"], w["boxes"], w["lut"], cam, w["step"], w["ref_len"], w["n_s"],
                                          w["gamma"])
-    st = _check_gen(lists, cnt, recs, GEN_TOL_TINY)
-    assert st["count_agree"] >= 0.999 and st["rgba_max"] <= GEN_TOL_TINY, st
+    _check_gen(lists, cnt, recs, chords(cam, w["dims"]))
     assert np.all(gam == np.float32(w["gamma"]))
     # offsets are the exclusive prefix sum of the counts
     for c, o, fb, rgba, _ in lists:
@@ -51,10 +56,9 @@ def test_generate_search_tiny(tiny_workload, n_s):
     cam = w["cams"][3]
     lists, gam = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, n_s, -1.0, step=w["step"])
     cnt, ogam, recs, _ = oracle.generate(w["vol"], w["boxes"], w["lut"], cam, w["step"], w["ref_len"], n_s, -1.0)
-    st = _check_gen(lists, cnt, recs, GEN_TOL_TINY)
-    assert st["count_agree"] >= 0.999 and st["rgba_max"] <= GEN_TOL_TINY, st
+    _check_gen(lists, cnt, recs, chords(cam, w["dims"]))
     same = np.stack([l[0] for l in lists]) == cnt
-    assert np.mean(gam[same] == ogam[same]) >= 0.99
+    assert np.mean(gam[same] == ogam[same]) >= 0.999
 
 
 def test_end_to_end_equals_dvr_tiny(tiny_workload):
@@ -65,10 +69,12 @@ def test_end_to_end_equals_dvr_tiny(tiny_workload):
         lists, _ = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, w["n_s"], -1.0, step=w["step"])
         g = composite(lists, cam.width, cam.height, w["n_s"])
         ref = oracle.dvr(w["vol"], w["lut"], cam, w["step"], w["ref_len"])
-        assert np.abs(g["image"] - ref).max() <= GEN_TOL_TINY
+        assert np.abs(g["image"] - ref).max() <= TOL
 
 
 def test_generate_fp16_storage(tiny_workload):
+    # FP16 records store the premultiplied colour and the optical depth tau = -log2(1 - A) in binary16:
+    # colour within half an ulp (2^-11 relative), opacity within ln2 tau 2^-tau 2^-11 <= 1.8e-4
     w = tiny_workload
     cam = w["cams"][2]
     l32, _ = generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, w["n_s"], -1.0, step=w["step"])
@@ -76,7 +82,8 @@ def test_generate_fp16_storage(tiny_workload):
     for a, b in zip(l32, l16):
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
         assert np.array_equal(a[2], b[2])  # depths stay FP32
-        assert np.abs(a[3] - b[3]).max() <= 2e-3 * 0.5 + 1e-7
+        assert np.abs(a[3][:, 0:3] - b[3][:, 0:3]).max() <= 2.0 ** -11 * np.abs(a[3][:, 0:3]).max() + 1e-7
+        assert np.abs(a[3][:, 3] - b[3][:, 3]).max() <= 1.8e-4
 
 
 def test_capacity_error_reported():
@@ -149,8 +156,9 @@ def test_given_gamma_with_fallback(tiny_workload):
 
 
 def test_plain_config_sampled_rays():
-    # 512^3 uint16, 8 bricks, 1920 x 1080, N_S = 20, gamma searched in both phases; the oracle
-    # computes 1500 sampled pixels of one view
+    # 512^3 uint16, 8 bricks, 1920 x 1080, N_S = 20, gamma searched in both phases; the oracle computes
+    # 1500 sampled pixels of one view: the sub-VDIs (generation), the composite of the GPU's own
+    # sub-VDIs (compositing, same inputs on both sides), and the DVR the flattened composite must equal
     dims = (512, 512, 512)
     vol = synth.volume(dims, 64, 3, synth.SEED_VOLUME + 1, np.uint16)
     lut = synth.transfer_function(synth.SEED_TF)
@@ -161,14 +169,26 @@ def test_plain_config_sampled_rays():
     g = composite(lists, 1920, 1080, n_s)
     rng = np.random.default_rng(3)
     pix = np.sort(rng.choice(1920 * 1080, 1500, replace=False)).astype(np.int32)
+    ch = chords(cam, dims, pix)
     cnt, ogam, recs, _ = oracle.generate(vol, boxes, lut, cam, 0.5, 1.0, n_s, -1.0, pixels=pix)
-    cg, rg = per_pixel(lists, n_s)
-    st = compare_lists(cg[:, pix], rg[:, pix], cnt, recs, 1e-2, GEN_TOL_512)
-    assert st["count_agree"] >= 0.99, st
-    assert st["rgba_max"] <= GEN_TOL_512, st
+    st = _check_gen(lists, cnt, recs, ch, pix)
+    print("512^3 generation:", st)
+    # compositing at the benchmarked size: the oracle composites the same FP32 sub-VDIs
+    sub = []
+    for c, o, fb, rgba, _ in lists:
+        cs, os_ = c[pix], o[:-1][pix].astype(np.int64)
+        idx = np.concatenate([np.arange(a, a + n) for a, n in zip(os_, cs.astype(np.int64))]) if cs.sum() else \
+            np.zeros(0, np.int64)
+        off = np.zeros(len(pix) + 1, np.uint64)
+        off[1:] = np.cumsum(cs)
+        sub.append((cs.astype(np.uint32), off, fb[idx], rgba[idx], 1))
+    cc, _, crec, _ = oracle.composite(sub, n_s, n_pix=len(pix))
+    gr = np.concatenate([g["fb"], g["rgba"]], -1)[pix]
+    st_c = compare_lists(g["counts"][pix], gr, cc, crec, DEPTH_REL * ch, TOL)
+    print("512^3 compositing:", st_c)
     ref = oracle.dvr(vol, lut, cam, 0.5, 1.0, pixels=pix)
     err = np.abs(g["image"][pix] - ref).max()
-    assert err <= GEN_TOL_512, err
+    assert err <= TOL, err
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -206,13 +226,10 @@ def test_generate_regular_equals_compact(tiny_workload, prec, gamma_mode):
         cnt = o.counts.cpu().numpy().astype(np.uint32)
         assert np.array_equal(cnt, c)
         assert np.array_equal(o.gamma.cpu().numpy(), gam[e])
-        if prec == 0:
-            fb_r = o.fb.view(npix, n_s, 2).cpu().numpy()
-            raw_r = o.rgba.view(npix, n_s, 4).cpu().numpy()
-        else:
-            raw = o.rgba.view(npix, n_s, 4).cpu().numpy()
-            fb_r = raw[..., 0:2].copy().view(np.float32)
-            raw_r = raw[..., 2:4].copy().view(np.float16).astype(np.float32)
+        # decoded as the compact records were (FP16: the same decoder), so equal records decode equally
+        fb_t, rgba_t = o.records_f32()
+        fb_r = fb_t.cpu().numpy()
+        raw_r = rgba_t.cpu().numpy()
         slot = np.arange(n_s)[None, :] < cnt[:, None].astype(np.int64)
         idx = off[:-1].astype(np.int64)[:, None] + np.arange(n_s)[None, :]
         idx = np.where(slot, idx, 0)

@@ -10,7 +10,7 @@ the same VDI, every pixel of the view:
   generating one, as the paper's evaluation shows for its VDIs).
 
 Tolerance: 5e-4 absolute per RGBA channel with FP32 records, 2e-3 with FP16
-colour storage (the oracle reads the same rounded colours).  The ray geometry
+storage (the oracle reads the same rounded colours and optical depths).  The ray geometry
 is FP32 (the closest approach to the generating eye in double-float): a
 column face crossed at s ~ 3 moves by ~1e-6, which hands a sliver of that
 length from one column to its neighbour, and the synthetic lists' records
@@ -25,7 +25,7 @@ import pytest
 import oracle
 import synth
 
-from gpu_run import compact_from_numpy, generate, pack_f16_records, to_dev
+from gpu_run import compact_from_numpy, generate, pack_f16_records, to_dev, unpack_f16_records
 
 pytestmark = pytest.mark.gpu
 
@@ -66,7 +66,8 @@ def device_regular(counts, recs, prec):
         reg.fb.copy_(torch.from_numpy(fb))
         reg.rgba.copy_(torch.from_numpy(rgba))
     else:
-        reg.rgba.copy_(torch.from_numpy(pack_f16_records(fb, rgba)))
+        # packed from the float64 values, so that decoded records pack back to the same bytes
+        reg.rgba.copy_(torch.from_numpy(pack_f16_records(fb, recs[..., 2:6].reshape(-1, 4))))
     return reg
 
 
@@ -102,8 +103,9 @@ def test_synthetic_vdi_matches_oracle(prec):
     counts, recs = synthetic_vdi(W, H, n_s, 303, 2.4, 1.2)
     p = vdi.VDI_PREC_F32 if prec == 0 else vdi.VDI_PREC_F16
     if prec == 1:
-        # the oracle reads the colours as stored (FP16, round to nearest even)
-        recs[..., 2:6] = recs[..., 2:6].astype(np.float16).astype(np.float64)
+        # the oracle reads the records as stored (FP16 colour and optical depth, round to nearest even)
+        _, dec = unpack_f16_records(pack_f16_records(recs[..., 0:2].reshape(-1, 2), recs[..., 2:6].reshape(-1, 4)))
+        recs[..., 2:6] = dec.reshape(recs.shape[:-1] + (4,))
     reg = device_regular(counts, recs, p)
     tol = 5e-4 if prec == 0 else 2e-3
     # view sizes and angles that put no view ray on a face of the generating camera's columns (where

@@ -4,9 +4,11 @@ lists, regenerated on the host).
 
 - Precision and scale: 2048 x 2048, K = 32, N_S = 32, dense lists (every PE
   holds N_S records per pixel): first with FP32 records (103 GB of input),
-  then with FP16 colour and opacity storage (69 GB).  The FP16 path is held
-  to 2e-3 against the oracle run on the FP16-stored inputs, and its error
-  against the FP64 composite of the unrounded inputs is reported.
+  then with FP16 storage of colour and optical depth (69 GB).  The FP16 path
+  is held to 2e-3 against the FP64 composite of the unrounded inputs (the
+  the benchmark spec's bound for FP16 storage), and to the FP16 output's rounding
+  against the oracle run on the stored FP16 inputs (the same bytes the GPU
+  read).
 - Batched: 64 requests of the seeded request table (W ~ U{256..1920},
   H ~ U{256..1080}, K ~ U{2..32}, N_S ~ U{8..64}, list lengths ~ U{0..N_S})
   in one persistent launch, captured in a CUDA graph and replayed, with the
@@ -23,7 +25,7 @@ import pytest
 import oracle
 import synth
 
-from gpu_run import compare_lists, pack_f16_records, unpack_f16_records
+from gpu_run import compare_lists
 
 pytestmark = pytest.mark.gpu
 
@@ -44,9 +46,7 @@ def _host_lists(per_pixel, prec):
     offsets[1:] = np.cumsum(counts)
     fb = np.concatenate([fb for fb, _ in per_pixel]) if counts.sum() else np.zeros((0, 2), np.float32)
     rgba = np.concatenate([c for _, c in per_pixel]) if counts.sum() else np.zeros((0, 4), np.float32)
-    if prec == 2:
-        return (counts, offsets, None, pack_f16_records(fb, rgba), 2)
-    return (counts, offsets, fb, rgba, 1)
+    return (counts, offsets, fb, rgba, prec)
 
 
 def _gpu_records(out, pix):
@@ -95,9 +95,8 @@ def test_precision_scale_full_size():
     cnt_o, _, rec_o, _ = oracle.composite(lists32, NS, n_pix=len(pix))
     st32 = compare_lists(cnt_g, rec_g, cnt_o, rec_o, 1e-5, 1e-5)
     print("precision/scale FP32:", st32)
-    assert st32["count_agree"] >= 0.999 and st32["depth_agree"] >= 0.999 and st32["rgba_max"] <= 1e-5, st32
     del out
-    # FP16 colour/opacity storage (FP32 depth), converted PE by PE
+    # FP16 storage of colour and optical depth (FP32 depth), converted PE by PE
     for e in range(K):
         rec = gpu_lists.pack_f16(pes[e].fb, pes[e].rgba)
         pes[e] = vdi.Compact.from_tensors(pes[e].counts, pes[e].offsets, rec, None, vdi.VDI_PREC_F16)
@@ -107,16 +106,23 @@ def test_precision_scale_full_size():
                                 ws.nbytes), "composite f16")
     vdi.check(ws.status(), "composite f16 status")
     cnt_g, rec_g = _gpu_records(out16, pix)
-    lists16 = [(c, o, None, pack_f16_records(fb, rgba), 2) for c, o, fb, rgba, _ in lists32]
-    cnt_o16, _, rec_o16, _ = oracle.composite(lists16, NS, n_pix=len(pix))
-    st16 = compare_lists(cnt_g, rec_g, cnt_o16, rec_o16, 1e-5, 2e-3)
-    # error of the FP16 path against the FP64 composite of the unrounded inputs (reported)
-    st16_vs_64 = compare_lists(cnt_g, rec_g, cnt_o, rec_o, 1e-5, 1.0)
+    # against the FP64 composite of the unrounded inputs: the storage error the benchmark spec bounds
+    st16_vs_64 = compare_lists(cnt_g, rec_g, cnt_o, rec_o, 1e-5, 2e-3, check=False)
     img16 = oracle.flatten(cnt_g, rec_g)
     img64 = oracle.flatten(cnt_o, rec_o)
-    print("precision/scale FP16:", st16, "vs FP64 of FP32 inputs:", st16_vs_64,
-          "image max err", float(np.abs(img16 - img64).max()))
-    assert st16["count_agree"] >= 0.999 and st16["rgba_max"] <= 2e-3, st16
+    img_err = float(np.abs(img16 - img64).max())
+    # against the oracle on the stored FP16 inputs of the sampled pixels (the bytes the GPU read)
+    idx = torch.from_numpy((pix[:, None] * NS + np.arange(NS)[None, :]).ravel()).cuda()
+    lists16 = []
+    for e in range(K):
+        raw = pes[e].rgba[idx].cpu().numpy()
+        off = np.arange(len(pix) + 1, dtype=np.uint64) * NS
+        lists16.append((np.full(len(pix), NS, np.uint32), off, None, raw, 2))
+    cnt_o16, _, rec_o16, _ = oracle.composite(lists16, NS, n_pix=len(pix))
+    st16 = compare_lists(cnt_g, rec_g, cnt_o16, rec_o16, 1e-5, 5e-4)
+    print("precision/scale FP16: vs FP64 of the unrounded inputs", st16_vs_64, "image max err", img_err,
+          "; vs the oracle on the stored inputs", st16)
+    assert st16_vs_64["rgba_max"] <= 2e-3 and img_err <= 2e-3, (st16_vs_64, img_err)
     del pes, out16
     torch.cuda.empty_cache()
 
@@ -171,19 +177,21 @@ def test_batched_full_size():
             assert torch.equal(a, b)
     # FP64 oracle on sampled pixels of every request
     rng = np.random.default_rng(3)
-    agree = tot = 0
+    agree = agree_d = tot = 0
     worst = 0.0
     for i, ((w, h, k, n_s, pes), o) in enumerate(zip(reqs, outs)):
         pix = np.sort(rng.choice(w * h, 24, replace=False)).astype(np.int64)
         lists = [_host_lists(synth.pooled_lists(synth.SEED_REQUESTS, i, e, pix, n_s, runs), 1) for e in range(k)]
         cnt_o, _, rec_o, _ = oracle.composite(lists, n_s, n_pix=len(pix))
         cnt_g, rec_g = _gpu_records(o, pix)
-        st = compare_lists(cnt_g, rec_g, cnt_o, rec_o, 1e-5, 1e-5)
+        st = compare_lists(cnt_g, rec_g, cnt_o, rec_o, 1e-5, 1e-5, check=False)
         agree += int(round(st["count_agree"] * len(pix)))
+        agree_d += int(round(st["depth_agree"] * len(pix)))
         tot += len(pix)
         worst = max(worst, st["rgba_max"])
         assert st["rgba_max"] <= 1e-5, (i, st)
-    print(f"batched full size: counts agree on {agree}/{tot}, rgba max err {worst:.2e}")
-    assert agree >= 0.999 * tot
+    print(f"batched full size: counts agree on {agree}/{tot}, counts and depths on {agree_d}/{tot}, "
+          f"rgba max err {worst:.2e}")
+    assert agree >= 0.999 * tot and agree_d >= 0.999 * tot
     del reqs, outs, pool_fb, pool_rgba
     torch.cuda.empty_cache()

@@ -80,24 +80,26 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
 
 def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
-    # the bench reports the committed DRAM-traffic capture only for the workload it was taken on and
-    # only while the kernel's sources hash to the captured ones
+    # the bench reports a committed DRAM-traffic capture only for the workload it describes and only
+    # while the kernel's sources hash to the captured ones
+    import hashlib
     import json
-    import shutil
     import types
 
     import bench
 
-    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "gen_count_traffic.json")))
-    wl = types.SimpleNamespace(name=rec["workload"])
-    assert bench.gen_traffic(wl) == rec["dram_bytes_read"] + rec["dram_bytes_write"]
-    assert bench.gen_traffic(types.SimpleNamespace(name="another workload")) is None
-    # a copy of the tree whose kernel source differs by one byte
     fake = tmp_path / "root"
-    for f in rec["sources"] + ["profiles/gen_count_traffic.json"]:
-        (fake / os.path.dirname(f)).mkdir(parents=True, exist_ok=True)
-        shutil.copy(os.path.join(bench.ROOT, f), fake / f)
-    src = fake / rec["sources"][0]
-    src.write_bytes(src.read_bytes() + b"\n")
+    (fake / "profiles").mkdir(parents=True)
+    (fake / "src").mkdir()
+    (fake / "src" / "k.cu").write_text("kernel source\n")
+    h = hashlib.sha256((fake / "src" / "k.cu").read_bytes()).hexdigest()
+    rec = {"kernel": "gen_count_kernel", "workload": "a workload", "dram_bytes_read": 3.0e9,
+           "dram_bytes_write": 1.0e9, "sources": ["src/k.cu"], "sources_sha256": h}
+    (fake / "profiles" / "gen_count_traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(fake))
+    wl = types.SimpleNamespace(name="a workload")
+    assert bench.gen_traffic(wl) == 4.0e9
+    assert bench.gen_traffic(types.SimpleNamespace(name="another workload")) is None
+    # the kernel source differs by one byte
+    (fake / "src" / "k.cu").write_text("kernel source\n\n")
     assert bench.gen_traffic(wl) is None

@@ -49,8 +49,17 @@ def test_dense_set_and_f16_pack():
     assert c.tolist() == [8] * 50 and o[-1].item() == 400
     f2, c2 = synth.one_list(0xC5, 0, 3, 33, 8, dense=True)
     assert np.array_equal(fb[33 * 8:34 * 8].numpy(), f2) and np.array_equal(rgba[33 * 8:34 * 8].numpy(), c2)
-    pk = gpu_lists.pack_f16(fb, rgba, chunk=100)
-    assert np.array_equal(pk.numpy(), pack_f16_records(fb.numpy(), rgba.numpy()))
+    pk = gpu_lists.pack_f16(fb, rgba, chunk=100).numpy()
+    ref = pack_f16_records(fb.numpy(), rgba.numpy())
+    # depths and colour bytes identical; tau computed in float32 against float64 may round to the
+    # neighbouring binary16 value where the two straddle a rounding boundary
+    assert np.array_equal(pk[:, 0:3], ref[:, 0:3])
+    h_g = np.ascontiguousarray(pk[:, 3]).view(np.uint16).reshape(-1, 2)
+    h_r = np.ascontiguousarray(ref[:, 3]).view(np.uint16).reshape(-1, 2)
+    assert np.array_equal(h_g[:, 0], h_r[:, 0])
+    t_g = h_g[:, 1].astype(np.int64)
+    t_r = h_r[:, 1].astype(np.int64)
+    assert np.abs(t_g - t_r).max() <= 1 and np.mean(t_g == t_r) > 0.99
 
 
 def test_request_table():

@@ -9,6 +9,9 @@ counts, offsets, gamma and records equal those of vdi_generate with a
 caller-allocated workspace, within the generation tests' tolerance (they are
 expected to be identical).  It lives in a file of its own that pytest collects
 last, and passes both alone in a fresh process and after the other tests.
+Errors the kernels detect are written into the static array, which the caller
+cannot read; the entry point reads that status word back and returns it, which
+the last test checks with counts that disagree with the emission.
 """
 import numpy as np
 import pytest
@@ -78,3 +81,28 @@ def test_static_scratch_reports_capacity_and_size_limits():
     s = vdi.vdi_generate_static_scratch(br.bricks, lut_d.data_ptr(), big, 6, 0.0, [o.struct() for o in small],
                                         vdi.make_params())
     assert s == vdi.VDI_ERR_INVALID_ARG and "static scratch" in vdi.last_error()
+
+
+def test_static_scratch_returns_device_status():
+    vdi, torch, br, lut_d, cams, k = _setup()
+    n_s = 6
+    cam = cams[1]
+    c = vdi.make_camera(cam)
+    npix = cam.width * cam.height
+    got = [vdi.Compact(npix, npix * (n_s + 1)) for _ in range(k)]
+    ws = vdi.Workspace(vdi.vdi_generate_workspace(k, cam.width, cam.height))
+    vdi.check(vdi.vdi_choose_gamma(br.bricks, lut_d.data_ptr(), c, n_s, vdi.VDI_GAMMA_SEARCH,
+                                   [o.struct() for o in got], vdi.make_params(), ws.ptr, ws.nbytes), "choose")
+    torch.cuda.synchronize()
+    # one more record claimed on every non-empty list than emission at the chosen gamma writes: the
+    # emit kernel flags the mismatch in the status word inside the static array
+    for o in got:
+        o.counts.add_((o.counts > 0).to(o.counts.dtype))
+    assert any(int(o.counts.max()) > 0 for o in got)
+    s = vdi.vdi_generate_static_scratch(br.bricks, lut_d.data_ptr(), c, n_s, vdi.VDI_GAMMA_CHOSEN,
+                                        [o.struct() for o in got], vdi.make_params())
+    assert s == vdi.VDI_ERR_CUDA and "device reported" in vdi.last_error()
+    # the next call clears the word first
+    s = vdi.vdi_generate_static_scratch(br.bricks, lut_d.data_ptr(), c, n_s, vdi.VDI_GAMMA_SEARCH,
+                                        [o.struct() for o in got], vdi.make_params())
+    assert s == vdi.VDI_OK
