@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-nonconvex", action="store_true", help="skip the checkerboard-ownership frame")
     ap.add_argument("--no-scale", action="store_true", help="skip the 2048^2 K=32 dense compositing runs")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-request batched compositing run")
+    ap.add_argument("--no-gen-batched", action="store_true", help="skip the batched generation run")
     ap.add_argument("--scale-size", type=int, default=2048, help="image side of the K=32 dense compositing run")
     ap.add_argument("--legs-only", action="store_true",
                     help="skip the frame and print only the compositing legs (for profiling small cases)")
@@ -197,49 +198,71 @@ def learned_eval(vdi, torch, stream, views=3, warmup=1):
     vdi.check(vdi.vdi_model_load(model.data_ptr(), LEARNED_CKPT, stream), "model load")
     cams = [vdi.make_camera(c) for c in synth.orbit(dims, 16, W, H, synth.SEED_ORBIT)]
     cap = npix * n_s // 4
-    outs_s = [vdi.Compact(npix, cap) for _ in range(k)]
-    outs_l = [vdi.Compact(npix, cap) for _ in range(k)]
+    outs = {m: [vdi.Compact(npix, cap) for _ in range(k)] for m in ("search", "learned", "single")}
     ws = vdi.Workspace(vdi.vdi_generate_workspace(k, W, H))
     lws = vdi.Workspace(vdi.vdi_learned_workspace(k, W, H))
     params = vdi.make_params()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-    t_search, t_learned, t_cs, t_cl, diff, tot = [], [], [], [], 0, 0
+    flags = {"learned": 0, "single": vdi.VDI_FLAG_LEARNED_SINGLE_PASS}
+    t_choose = {m: [] for m in outs}
+    t_gen = {m: [] for m in outs}
+    diff = {m: 0 for m in ("learned", "single")}
+    tot = 0
+
+    def choose(m, c, p):
+        if m == "search":
+            return vdi.vdi_choose_gamma(bricks.bricks, lut.data_ptr(), c, n_s, vdi.VDI_GAMMA_SEARCH,
+                                        [o.struct() for o in outs[m]], p, ws.ptr, ws.nbytes, stream)
+        return vdi.vdi_choose_gamma_learned(bricks.bricks, lut.data_ptr(), c, n_s, model.data_ptr(), offset,
+                                            [o.struct() for o in outs[m]], p, lws.ptr, lws.nbytes, stream)
+
     for i in range(warmup + views):
         c = cams[(2 * i + 1) % 16]
-        ev[0].record(stream)
-        vdi.check(vdi.vdi_choose_gamma(bricks.bricks, lut.data_ptr(), c, n_s, vdi.VDI_GAMMA_SEARCH,
-                                       [o.struct() for o in outs_s], params, ws.ptr, ws.nbytes, stream), "search")
-        ev[1].record(stream)
-        vdi.check(vdi.vdi_generate(bricks.bricks, lut.data_ptr(), c, n_s, vdi.VDI_GAMMA_CHOSEN,
-                                   [o.struct() for o in outs_s], params, ws.ptr, ws.nbytes, stream), "emit")
-        ev[2].record(stream)
-        ev[3].record(stream)
-        vdi.check(vdi.vdi_choose_gamma_learned(bricks.bricks, lut.data_ptr(), c, n_s, model.data_ptr(), offset,
-                                               [o.struct() for o in outs_l], params, lws.ptr, lws.nbytes, stream),
-                  "learned")
-        ev[4].record(stream)
-        vdi.check(vdi.vdi_generate(bricks.bricks, lut.data_ptr(), c, n_s, vdi.VDI_GAMMA_CHOSEN,
-                                   [o.struct() for o in outs_l], params, ws.ptr, ws.nbytes, stream), "emit")
-        ev[5].record(stream)
-        stream.synchronize()
-        vdi.check(ws.status(stream), "status")
+        for m in outs:
+            p = vdi.make_params(flags=flags.get(m, 0))
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            vdi.check(choose(m, c, p), m)
+            ev[1].record(stream)
+            vdi.check(vdi.vdi_generate(bricks.bricks, lut.data_ptr(), c, n_s, vdi.VDI_GAMMA_CHOSEN,
+                                       [o.struct() for o in outs[m]], params, ws.ptr, ws.nbytes, stream), "emit")
+            ev[2].record(stream)
+            stream.synchronize()
+            vdi.check(ws.status(stream), "status")
+            if i >= warmup:
+                t_choose[m].append(ev[0].elapsed_time(ev[1]))
+                t_gen[m].append(ev[0].elapsed_time(ev[2]))
         if i < warmup:
             continue
-        t_cs.append(ev[0].elapsed_time(ev[1]))
-        t_search.append(ev[0].elapsed_time(ev[2]))
-        t_cl.append(ev[3].elapsed_time(ev[4]))
-        t_learned.append(ev[3].elapsed_time(ev[5]))
-        cs = torch.stack([o.counts for o in outs_s]).long()
-        cl = torch.stack([o.counts for o in outs_l]).long()
+        cs = torch.stack([o.counts for o in outs["search"]]).long()
         nz = cs > 0
-        diff += int((cl - cs).abs()[nz].sum())
         tot += int(cs[nz].sum())
-    ms_s, ms_l = statistics.mean(t_search), statistics.mean(t_learned)
+        for m in diff:
+            cl = torch.stack([o.counts for o in outs[m]]).long()
+            diff[m] += int((cl - cs).abs()[nz].sum())
+    # the work each choice does on the last view, from the census: cached marches and volume marches
+    census = {}
+    c = cams[(2 * (warmup + views - 1) + 1) % 16]
+    for m in outs:
+        vdi.check(choose(m, c, vdi.make_params(flags=flags.get(m, 0) | vdi.VDI_FLAG_CENSUS)), "census")
+        ctr = vdi.vdi_workspace_counters(ws.ptr if m == "search" else lws.ptr + lws_gen_offset(vdi, k, W, H),
+                                         stream)
+        census[m] = {"marches": ctr[2], "cached_marches": ctr[6], "volume_search_marches": ctr[7],
+                     "sample_evals": ctr[0], "searched_rays": ctr[4]}
+    ms = {m: statistics.mean(t_gen[m]) for m in outs}
     return {"workload": "learned: 1024^3 u16 (128 blobs, 4 octaves), K=16 (4x2x2), 1920x1080, N_S=32",
-            "views": views, "offset": offset, "search_gen_ms": ms_s, "learned_gen_ms": ms_l,
-            "speedup": ms_s / ms_l, "choose_search_ms": statistics.mean(t_cs),
-            "choose_learned_ms": statistics.mean(t_cl), "count_error": diff / max(tot, 1),
-            "mrays_s_search": npix / ms_s / 1e3, "mrays_s_learned": npix / ms_l / 1e3}
+            "views": views, "offset": offset, "search_gen_ms": ms["search"], "learned_gen_ms": ms["learned"],
+            "single_gen_ms": ms["single"], "speedup": ms["search"] / ms["learned"],
+            "speedup_single_pass": ms["search"] / ms["single"],
+            "choose_ms": {m: statistics.mean(t_choose[m]) for m in outs},
+            "count_error": diff["learned"] / max(tot, 1), "count_error_single_pass": diff["single"] / max(tot, 1),
+            "census_last_view": census,
+            "mrays_s": {m: npix / ms[m] / 1e3 for m in outs}}
+
+
+def lws_gen_offset(vdi, k, W, H):
+    """Offset of the generation workspace inside the learned-gamma workspace (its status and census
+    counters come after the features, predictions and tile flags)."""
+    return vdi.vdi_learned_workspace(k, W, H) - vdi.vdi_generate_workspace(k, W, H)
 
 
 def _comp_census(vdi, counters):
@@ -364,6 +387,74 @@ def batched_eval(vdi, torch, stream, hbm_peak, warmup=1, steps=3, runs=1 << 22):
     del keep, pool_fb, pool_rgba, g
     torch.cuda.empty_cache()
     return res
+
+
+def gen_batched_eval(vdi, torch, stream, n_req=16, warmup=1, steps=3):
+    """Uneven generation requests (synth.gen_requests: side^3 uint16 volumes, side in {128..384}, K in
+    {1, 2, 4, 8, 16}, W ~ U{256..1920}, H ~ U{256..1080}, N_S ~ U{8..64}, gamma searched) in one
+    vdi_generate_batched call captured in a CUDA graph, against the same requests generated one
+    vdi_generate call after another.  Rays = the requests' W x H summed."""
+    import synth
+    from synth import gpu_volume
+
+    table = synth.gen_requests(n_req)
+    lut = torch.from_numpy(synth.transfer_function(synth.SEED_TF)).cuda()
+    reqs, keep = [], []
+    rays = 0
+    params = vdi.make_params()
+    with torch.cuda.stream(stream):
+        for r, (side, grid, w, h, n_s) in enumerate(table):
+            dims = (side, side, side)
+            vol = gpu_volume.volume(dims, 32, 3, synth.SEED_VOLUME + 10 + r)
+            br = vdi.Bricks(vol, dims, vdi.vdi_split_boxes(dims, grid), stream)
+            cam = synth.orbit(dims, 16, w, h, synth.SEED_ORBIT)[r % 16]
+            outs = [vdi.Compact(w * h, w * h * n_s // 2) for _ in range(grid[0] * grid[1] * grid[2])]
+            keep.append((vol, br, outs))
+            reqs.append((br.bricks, lut.data_ptr(), vdi.make_camera(cam), n_s, vdi.VDI_GAMMA_SEARCH,
+                         [o.struct() for o in outs]))
+            rays += w * h
+        stream.synchronize()
+    R = vdi.GenRequests(reqs)
+    host = vdi.vdi_gen_batch_table_pack(R, params)
+    dev_t = torch.frombuffer(bytearray(host), dtype=torch.uint8).cuda()
+    ws = vdi.Workspace(vdi.vdi_generate_batched_workspace(host))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            vdi.check(vdi.vdi_generate_batched(dev_t.data_ptr(), host, ws.ptr, ws.nbytes, stream), "capture")
+        for _ in range(warmup):
+            g.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            g.replay()
+        e1.record(stream)
+    stream.synchronize()
+    vdi.check(ws.status(stream), "batched generation status")
+    ms = e0.elapsed_time(e1) / steps
+    # the same requests, one vdi_generate call each
+    ws1 = vdi.Workspace(max(vdi.vdi_generate_workspace(len(q[5]), q[2].width, q[2].height) for q in reqs))
+
+    def one_by_one():
+        for br_, lut_p, cam, n_s, gamma, outs in reqs:
+            vdi.check(vdi.vdi_generate(br_, lut_p, cam, n_s, gamma, outs, params, ws1.ptr, ws1.nbytes, stream),
+                      "single")
+
+    one_by_one()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(steps):
+        one_by_one()
+    e3.record(stream)
+    stream.synchronize()
+    ms1 = e2.elapsed_time(e3) / steps
+    del keep, g, dev_t, ws, ws1
+    torch.cuda.empty_cache()
+    return {"workload": f"{n_req} generation requests (synth.gen_requests): side^3 u16 volumes, side in "
+                        "{128..384}, K in {1..16}, W~U{256..1920}, H~U{256..1080}, N_S~U{8..64}, search",
+            "ms": ms, "mrays_s": rays / (ms * 1e-3) / 1e6, "rays": rays, "one_by_one_ms": ms1,
+            "one_by_one_mrays_s": rays / (ms1 * 1e-3) / 1e6, "speedup": ms1 / ms}
 
 
 def novel_view_eval(vdi, torch, stream, wl, frame0, reg, W, H, reps=5):
@@ -920,6 +1011,8 @@ def main():
         layout["n_s_sweep"] = ns_sweep_eval(vdi, torch, stream, wl, bricks, lut_d, cams, outs, params, wsg, wsc)
 
     gen_batched = None
+    if rank == 0 and not args.no_gen_batched:
+        gen_batched = gen_batched_eval(vdi, torch, stream)
     learned = None
     if not args.no_learned and rank == 0:
         learned = learned_eval(vdi, torch, stream)

@@ -103,6 +103,7 @@ typedef struct {
 
 #define VDI_FLAG_SYNC_CAPACITY 1 /* vdi_generate: read totals back and return VDI_ERR_CAPACITY before emitting */
 #define VDI_FLAG_CENSUS 2        /* vdi_choose_gamma / vdi_generate / vdi_composite: count the work done (vdi_workspace_counters) */
+#define VDI_FLAG_LEARNED_SINGLE_PASS 4 /* vdi_choose_gamma_learned: no bracketed refinement (see there) */
 
 /* A sampling brick: one PE's cells in the library's cell-packed layout, built
  * by vdi_brick_build().  Opaque to the caller apart from its size. */
@@ -265,6 +266,50 @@ vdi_status vdi_generate_owned(const vdi_brick* bricks, int32_t k, const float* t
                               int32_t n_s, float gamma, const vdi_ownership* own, vdi_compact* out,
                               const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched generation: many generation requests (their own volumes, cameras, */
+/* image sizes, K, N_S and gamma modes) in one persistent launch.  No        */
+/* counterpart in the paper, where every PE generates its own sub-VDI for    */
+/* one frame (sec. 5.1); the per-(PE, ray) work is that of vdi_generate.     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const vdi_brick* bricks; /* host array of k bricks (device cells inside); one volume per request */
+    int32_t k;               /* PEs of the request, 1..VDI_MAX_PE */
+    const float* tf_lut;     /* device float[256*4] */
+    vdi_camera cam;          /* the request's camera and image size */
+    int32_t n_s;             /* supersegments per list */
+    float gamma;             /* >= 0 fixed, VDI_GAMMA_SEARCH or VDI_GAMMA_GIVEN */
+    vdi_compact* out;        /* host array of k sub-VDI descriptors (device arrays inside), one precision */
+} vdi_gen_request;
+
+/* Bytes of the table of n requests (host query). */
+size_t vdi_gen_batch_table_bytes(const vdi_gen_request* reqs, int32_t n);
+/* Checks the requests as vdi_generate checks its arguments and packs them,
+ * with params (step, ref_len, bisect_iters; flags and schedule unused), into
+ * host_table (host, vdi_gen_batch_table_bytes bytes).  The caller copies the
+ * table to device memory (dev_table); both are passed to
+ * vdi_generate_batched.  The table holds the requests' device pointers: a
+ * new table is needed when buffers move. */
+vdi_status vdi_gen_batch_table_pack(const vdi_gen_request* reqs, int32_t n, const vdi_params* params,
+                                    void* host_table, size_t bytes);
+/* Workspace bytes for a packed table: 512 bytes of status and counter, the
+ * prefix sums' partial sums (8 bytes per 4096 pixels per PE) and the sample
+ * cache of vdi_generate_workspace (the search re-marches the volume when the
+ * workspace has no room for it; same result). */
+size_t vdi_generate_batched_workspace(const void* host_table);
+/* Generates every request's k compact sub-VDIs: one persistent launch in
+ * which CTAs take (request, PE, 16 x 4-pixel tile) items from an atomic
+ * counter in the workspace (reset by this call with a stream-ordered memset)
+ * and choose gamma and the count of every ray of the item; one batched
+ * exclusive prefix sum of every (request, PE) list; one launch emitting the
+ * records.  The outputs equal those of one vdi_generate call per request,
+ * bit for bit.  Capacity overflows and emission errors are reported through
+ * the workspace status (vdi_workspace_status), as vdi_generate without
+ * VDI_FLAG_SYNC_CAPACITY; nothing is read back, so the memset and the
+ * launches can be captured in a CUDA graph and replayed. */
+vdi_status vdi_generate_batched(const void* dev_table, const void* host_table, void* workspace, size_t ws_bytes,
+                                vdi_stream stream);
+
 /* Generation for callers that cannot allocate device memory (an in-situ
  * simulation that reserves its whole device budget at start-up, a plugin with
  * no access to its host application's allocator).  The paper has no
@@ -318,8 +363,8 @@ vdi_status vdi_generate_static_scratch(const vdi_brick* bricks, int32_t k, const
  *     loads, each lane sweeps its pixel's lists there, and a pixel whose
  *     count at gamma = 0 is within n_s is emitted at once; the pixels that
  *     need the search (or whose records exceed the warp's 480-record slab)
- *     follow in a second launch, one lane each, over pieces kept in its
- *     column of the piece buffer;
+ *     are listed and follow in a second launch, one lane each, as schedule 1,
+ *     so that every lane of a warp searches;
  *   1, 2, 3 (direct): each thread sweeps its pixel's K lists on every march;
  *     1: list heads in registers (k <= 8), two bisection levels per march;
  *     2: heads in shared memory under a winner tree, two levels per march;
@@ -444,7 +489,11 @@ vdi_status vdi_mlp_train_step(void* model, const float* feats, const float* labe
  * take gamma = 0 as in the search.  Writes out[e].gamma and out[e].counts like
  * vdi_choose_gamma; follow with vdi_generate(..., VDI_GAMMA_CHOSEN, ...) to
  * emit.  The supersegment counts differ from the full search's only through
- * the bracket's resolution (a factor 2^(1/16) in gamma). */
+ * the bracket's resolution (a factor 2^(1/16) in gamma).
+ * With VDI_FLAG_LEARNED_SINGLE_PASS in params->flags the prediction is used
+ * as it is: one march per ray counts at gp, a ray within the budget keeps gp
+ * and its count, and only rays over the budget run the full bisection search
+ * (VDI_GAMMA_GIVEN with the predictions). */
 size_t vdi_learned_workspace(int32_t k, int32_t w, int32_t h);
 vdi_status vdi_choose_gamma_learned(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
                                     int32_t n_s, const void* model, float offset, vdi_compact* out,

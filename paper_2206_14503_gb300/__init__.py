@@ -33,6 +33,7 @@ VDI_GAMMA_GIVEN = -2.0
 VDI_GAMMA_CHOSEN = -3.0
 VDI_FLAG_SYNC_CAPACITY = 1
 VDI_FLAG_CENSUS = 2
+VDI_FLAG_LEARNED_SINGLE_PASS = 4
 VDI_SCHED_STAGED = 4
 VDI_SCHED_LANE = 5
 
@@ -86,6 +87,11 @@ class vdi_request(C.Structure):
                 ("schedule", C.c_int32)]
 
 
+class vdi_gen_request(C.Structure):
+    _fields_ = [("bricks", C.c_void_p), ("k", C.c_int32), ("tf_lut", C.c_void_p), ("cam", vdi_camera),
+                ("n_s", C.c_int32), ("gamma", C.c_float), ("out", C.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libvdi.so not built ({LIB_PATH}); run __graft_entry__.build()")
@@ -114,6 +120,10 @@ def _load():
         "vdi_composite_batched_workspace": ([vp], sz),
         "vdi_composite_batched": ([vp, vp, vp, vp, sz, vp], i32),
         "vdi_composite_autotune": ([vp, i32, vp, vp, sz, vp], i32),
+        "vdi_gen_batch_table_bytes": ([vp, i32], sz),
+        "vdi_gen_batch_table_pack": ([vp, i32, vp, vp, sz], i32),
+        "vdi_generate_batched_workspace": ([vp], sz),
+        "vdi_generate_batched": ([vp, vp, vp, sz, vp], i32),
         "vdi_model_bytes": ([], sz),
         "vdi_model_nparams": ([], i32),
         "vdi_model_init": ([vp, C.c_uint64, vp], i32),
@@ -150,6 +160,8 @@ SYMBOLS = ("vdi_version", "vdi_status_string", "vdi_last_error", "vdi_workspace_
            "vdi_generate_static_scratch", "vdi_generate_regular", "vdi_generate_owned",
            "vdi_composite_workspace", "vdi_composite", "vdi_render_view", "vdi_batch_table_bytes",
            "vdi_batch_table_pack", "vdi_composite_batched_workspace", "vdi_composite_batched", "vdi_composite_autotune",
+           "vdi_gen_batch_table_bytes", "vdi_gen_batch_table_pack", "vdi_generate_batched_workspace",
+           "vdi_generate_batched",
            "vdi_model_bytes", "vdi_model_nparams", "vdi_model_init", "vdi_model_save", "vdi_model_load",
            "vdi_tile_features", "vdi_tile_labels", "vdi_mlp_infer", "vdi_mlp_train_workspace", "vdi_mlp_grad",
            "vdi_mlp_train_step", "vdi_learned_workspace", "vdi_choose_gamma_learned",
@@ -335,6 +347,49 @@ def vdi_composite_batched(dev_table_ptr: int, host_table, params: vdi_params, ws
 def vdi_composite_autotune(reqs: Requests, params: vdi_params, ws_ptr, ws_bytes, stream=None) -> int:
     return _lib.vdi_composite_autotune(_arr(reqs.arr), len(reqs), _ref(params), C.c_void_p(ws_ptr), ws_bytes,
                                        _stream(stream))
+
+
+class GenRequests:
+    """A ctypes array of vdi_gen_request plus the brick and sub-VDI descriptor arrays it points to."""
+
+    def __init__(self, items):
+        """items: list of (bricks (ctypes array or list of vdi_brick), lut_ptr, vdi_camera, n_s, gamma,
+        list of vdi_compact)."""
+        self._keep = []
+        self.arr = (vdi_gen_request * len(items))()
+        for i, (bricks, lut_ptr, cam, n_s, gamma, outs) in enumerate(items):
+            ba = (vdi_brick * len(bricks))(*bricks)
+            oa = (vdi_compact * len(outs))(*outs)
+            self._keep += [ba, oa]
+            r = self.arr[i]
+            r.bricks = C.cast(ba, C.c_void_p)
+            r.k = len(bricks)
+            r.tf_lut = lut_ptr
+            r.cam = cam
+            r.n_s = n_s
+            r.gamma = gamma
+            r.out = C.cast(oa, C.c_void_p)
+
+    def __len__(self):
+        return len(self.arr)
+
+
+def vdi_gen_batch_table_pack(reqs: GenRequests, params: vdi_params):
+    """Checks and packs the generation requests; returns the table as a ctypes buffer (host)."""
+    n = _lib.vdi_gen_batch_table_bytes(_arr(reqs.arr), len(reqs))
+    buf = (C.c_uint8 * n)()
+    check(_lib.vdi_gen_batch_table_pack(_arr(reqs.arr), len(reqs), _ref(params), _arr(buf), n),
+          "vdi_gen_batch_table_pack")
+    return buf
+
+
+def vdi_generate_batched_workspace(host_table) -> int:
+    return _lib.vdi_generate_batched_workspace(_arr(host_table))
+
+
+def vdi_generate_batched(dev_table_ptr: int, host_table, ws_ptr, ws_bytes, stream=None) -> int:
+    return _lib.vdi_generate_batched(C.c_void_p(dev_table_ptr), _arr(host_table), C.c_void_p(ws_ptr), ws_bytes,
+                                     _stream(stream))
 
 
 # ---- learned gamma ----

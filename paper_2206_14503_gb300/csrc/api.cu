@@ -72,7 +72,7 @@ static bool params_ok(const vdi_params* p) {
     return p && p->step > 0.f && p->ref_len > 0.f && p->bisect_iters >= 1 && p->bisect_iters <= 24;
 }
 
-static BrickDev brick_dev(const vdi_brick& b) {
+BrickDev brick_dev(const vdi_brick& b) {
     BrickDev d;
     d.cells = b.cells;
     for (int a = 0; a < 3; ++a) {
@@ -211,9 +211,9 @@ size_t vdi_generate_workspace(int32_t k, int32_t w, int32_t h) {
     return gen_min_workspace(k, w, h) + align_up(cache, 256);
 }
 
-static vdi_status gen_common(const char* fn, const vdi_brick* bricks, int32_t k, const float* tf_lut,
-                             const vdi_camera* cam, int32_t n_s, float gamma, vdi_compact* out,
-                             const vdi_params* params, void* workspace, size_t ws_bytes, bool need_records) {
+static vdi_status gen_check(const char* fn, const vdi_brick* bricks, int32_t k, const float* tf_lut,
+                            const vdi_camera* cam, int32_t n_s, float gamma, const vdi_compact* out,
+                            const vdi_params* params, bool need_records) {
     if (!bricks || !tf_lut || !cam || !out || !params) return set_error(VDI_ERR_INVALID_ARG, "%s: NULL argument", fn);
     if (k < 1 || k > VDI_MAX_PE) return set_error(VDI_ERR_INVALID_ARG, "%s: k = %d", fn, k);
     if (n_s < 1) return set_error(VDI_ERR_INVALID_ARG, "%s: n_s = %d", fn, n_s);
@@ -245,6 +245,14 @@ static vdi_status gen_common(const char* fn, const vdi_brick* bricks, int32_t k,
                 return set_error(VDI_ERR_INVALID_ARG, "%s: out[%d] record arrays misaligned", fn, e);
         }
     }
+    return VDI_OK;
+}
+
+static vdi_status gen_common(const char* fn, const vdi_brick* bricks, int32_t k, const float* tf_lut,
+                             const vdi_camera* cam, int32_t n_s, float gamma, vdi_compact* out,
+                             const vdi_params* params, void* workspace, size_t ws_bytes, bool need_records) {
+    vdi_status s = gen_check(fn, bricks, k, tf_lut, cam, n_s, gamma, out, params, need_records);
+    if (s != VDI_OK) return s;
     if (!workspace || ws_bytes < gen_min_workspace(k, cam->width, cam->height))
         return set_error(VDI_ERR_WORKSPACE, "%s: workspace %zu < %zu bytes", fn, ws_bytes,
                          gen_min_workspace(k, cam->width, cam->height));
@@ -335,6 +343,42 @@ vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut,
                         vdi_stream stream) {
     return generate_compact("vdi_generate", bricks, k, tf_lut, cam, n_s, gamma, out, params, workspace, ws_bytes,
                             stream, nullptr);
+}
+
+size_t vdi_gen_batch_table_bytes(const vdi_gen_request* reqs, int32_t n) {
+    if (!reqs || n < 0) return 0;
+    return gen_batch_table_bytes(reqs, n);
+}
+
+vdi_status vdi_gen_batch_table_pack(const vdi_gen_request* reqs, int32_t n, const vdi_params* params,
+                                    void* host_table, size_t bytes) {
+    if (!reqs || n < 0 || !params || !host_table)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_gen_batch_table_pack: NULL argument");
+    char fn[64];
+    for (int q = 0; q < n; ++q) {
+        const vdi_gen_request& g = reqs[q];
+        snprintf(fn, sizeof fn, "vdi_gen_batch_table_pack: request %d", q);
+        if (g.gamma == VDI_GAMMA_CHOSEN) return set_error(VDI_ERR_INVALID_ARG, "%s: gamma", fn);
+        vdi_status s = gen_check(fn, g.bricks, g.k, g.tf_lut, &g.cam, g.n_s, g.gamma, g.out, params, true);
+        if (s != VDI_OK) return s;
+    }
+    return gen_batch_table_pack(reqs, n, params, host_table, bytes);
+}
+
+size_t vdi_generate_batched_workspace(const void* host_table) {
+    if (!host_table) return 0;
+    return gen_batched_workspace_bytes(host_table);
+}
+
+vdi_status vdi_generate_batched(const void* dev_table, const void* host_table, void* workspace, size_t ws_bytes,
+                                vdi_stream stream) {
+    if (!dev_table || !host_table || !workspace)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_batched: NULL argument");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_batched: workspace not 256-byte aligned");
+    if (reinterpret_cast<uintptr_t>(dev_table) & 63)
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_generate_batched: table not 64-byte aligned");
+    return launch_gen_batched(dev_table, host_table, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
 vdi_status vdi_generate_owned(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam,
@@ -701,8 +745,11 @@ vdi_status vdi_choose_gamma_learned(const vdi_brick* bricks, int32_t k, const fl
     s = cuda_check(cudaMemsetAsync(status, 0, kGenFixed, st), "status clear");
     if (s != VDI_OK) return s;
     const size_t fixed = gen_min_workspace(k, cam->width, cam->height);
-    return launch_gen_count(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s,
-                            kGammaLearnedBracket, params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0,
+    // single pass: the prediction is the ray's gamma unless its count exceeds n_s (then the search);
+    // default: the prediction brackets a short search over the cached samples
+    const float mode = (params->flags & VDI_FLAG_LEARNED_SINGLE_PASS) ? VDI_GAMMA_GIVEN : kGammaLearnedBracket;
+    return launch_gen_count(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s, mode,
+                            params->bisect_iters, od, status, (params->flags & VDI_FLAG_CENSUS) != 0,
                             reinterpret_cast<unsigned int*>(gws + kWsHeader), gws + fixed, gbytes - fixed, st);
 }
 

@@ -1,34 +1,49 @@
 // Phase 2: compositing of K compact sub-VDIs into one regular VDI (sec. 5.2,
 // Eq. 2, Algorithm S1).
 //
-// One thread per pixel.  The paper's all-to-all exchange becomes a gather: the
-// thread reads its K spans [offsets_e[p], offsets_e[p] + counts_e[p]) straight
-// from the K PEs' record arrays.  A depth sweep over the K list heads (each PE's
-// list is depth-sorted and non-overlapping, sec. 5.2) cuts the records at every
-// front and back depth and yields the pieces in order:
+// The paper's all-to-all exchange becomes a gather: pixel p's input is its K
+// spans [offsets_e[p], offsets_e[p] + counts_e[p]) in the K PEs' record
+// arrays.  A depth sweep over the K lists (each depth-sorted, sec. 5.2) cuts
+// the records at every front and back depth and yields the pieces in order:
 //   - a gap between records: a transparent sample;
 //   - an interval covered by one record whole: that record, unchanged;
 //   - part of one record: opacity by Eq. 2, 1 - (1 - A)^(dt / l);
 //   - an interval covered by several records: their emission-absorption
-//     mixture (extinctions add; colour is the extinction-weighted mean).
+//     mixture (extinctions add; colour is the extinction-weighted mean), summed
+//     exactly in 128-bit fixed point so that every schedule gets the same bits.
 // The pieces feed the supersegment state machine (Eq. 1) inside the per-pixel
-// bisection search for gamma.  A search march evaluates the next NLEV
-// bisection levels at once (the 2^NLEV - 1 midpoints of the subtree) and
-// records, per candidate, the interval of gamma over which all of its
-// decisions would repeat; the sequential bisection is replayed from the
-// recorded counts, marching again only for a midpoint no record covers, so
-// the result is that of plain bisection.  The first march also counts
-// non-transparent pieces, which is the count at gamma = 0.  A final march emits at most n_s
-// supersegments into the regular layout with a zero tail.
+// bisection search for gamma: a march evaluates the next two bisection levels
+// at once (midpoint and both children) and records, per candidate, the
+// interval of gamma over which all of its decisions repeat; the sequential
+// bisection is replayed from the recorded counts, marching again only for a
+// midpoint no record covers, so the result is that of plain bisection.  The
+// first march also counts non-transparent pieces (the count at gamma = 0).  A
+// final sweep emits at most n_s supersegments into the regular layout with a
+// zero tail.
 //
-// Schedules (chosen per request by the autotuner, vdi_composite_autotune):
-//   1: list heads in registers (K <= 8), 2 levels per march;
-//   2: list heads in local memory (K <= 64), 2 levels per march;
-//   3: list heads in local memory, 3 levels per march (7 candidates).
+// Schedules (the same result, bit for bit; chosen per request by the
+// autotuner, vdi_composite_autotune; the default is the lane schedule for
+// K <= 8 and the staged one above):
+//   VDI_SCHED_LANE (5, K <= 8): composite_lane_kernel copies a warp's 32
+//     pixels' records into shared memory with coalesced loads, sweeps each
+//     pixel there (a lane each), and emits the pixels whose gamma = 0 count is
+//     within n_s; the rest are listed and composite_list_kernel searches them,
+//     a lane each, so that no lane idles behind a searching neighbour;
+//   VDI_SCHED_STAGED (4): composite_staged_kernel, a persistent grid of
+//     8-warp CTAs, builds the pieces of 32 pixels a warp at a time (whole warp
+//     per pixel: coalesced span loads, merge-path sort of the bounds, exact
+//     prefix scan of the mixture terms) into a per-warp piece buffer, then
+//     each lane searches and emits its pixel from its column; pixels with more
+//     than 1024 records or more pieces than the buffer's rows are listed for
+//     composite_overflow_kernel (the direct schedule 2);
+//   1, 2, 3 (direct, composite_kernel): one thread per pixel re-sweeps its K
+//     lists on every march, heads in registers (1, K <= 8) or in shared memory
+//     under a winner tree (2; 3 with three levels per march).
 //
 // composite_batched_kernel runs many requests (different sizes, K, N_S) in one
-// persistent launch: CTAs pull (request, 128-pixel tile) items from an atomic
-// counter until none are left.
+// persistent launch: warps pull (request, 32-pixel batch) items from an atomic
+// counter and run the staged schedule; requests with a direct schedule and
+// the pixels the stage cannot hold follow in composite_batched_direct_kernel.
 #include <climits>
 
 #include "vdi_device.cuh"
@@ -1415,39 +1430,53 @@ __global__ void __launch_bounds__(128) composite_overflow_kernel(const __grid_co
 }
 
 // ---------------------------------------------------------------------------
-// Lane-staged path (short lists: K <= kLaneKMax, a pixel's records fit a warp's
-// slab).  Two launches.
+// Lane-staged path (short lists: K <= kLaneKMax).  Two launches of one
+// kernel, each warp staging the records of 32 pixels in its shared-memory
+// slab with asynchronous copies (cp.async: every copy of a round is in
+// flight before the warp waits once) and sweeping each pixel there, a lane
+// per pixel, so that no march touches global memory.
 //
-// composite_lane_kernel: a warp takes 32 consecutive pixels.  It reads their
-// counts and offsets (coalesced over the pixels), then copies the records of
-// as many of them as its shared-memory slab holds, PE by PE: the spans of
-// consecutive pixels of one PE are consecutive in the PE's record array (the
-// layout generation writes), so a warp's loads are coalesced 16- and 8-byte
-// runs; other layouts find each record's pixel by a binary search over the
-// lanes.  Each lane then sweeps its pixel's K lists in the slab into pieces
-// and counts the non-transparent ones: at most n_s means gamma = 0 (sec. 2.4:
-// the count at gamma = 0 is within the budget), and a second sweep emits the
-// pixel's records straight away.  Pixels that need the gamma search, or whose
-// records do not fit the slab, are appended to a list.
+// Batch pass (LIST = false): a warp takes 32 consecutive pixels and reads
+// their counts and offsets (coalesced over the pixels).  The records go to the
+// slab PE by PE: the spans of consecutive pixels of one PE are consecutive in
+// the PE's record array (the layout generation writes), so a warp's copies
+// are coalesced 16- and 8-byte runs; other layouts find each record's pixel
+// by a binary search over the lanes.  A lane sweeps its pixel's K lists into
+// pieces and counts the non-transparent ones: at most n_s means gamma = 0
+// (sec. 2.4: the count at gamma = 0 is within the budget), and a second sweep
+// emits the pixel's records straight away.  Pixels that need the gamma
+// search, or whose records do not fit a slab, are appended to a list.
 //
-// composite_list_kernel: a warp takes 32 listed pixels; each lane sweeps its
-// pixel's lists from global memory once, writing the pieces into its column of
-// the warp's piece buffer (a few KB per warp in use, so the buffer stays in L2
-// across the search's marches), then runs the search and the emission over the
-// column.  A pixel with more pieces than the column holds is searched over
-// its lists directly.  The pieces are those of every other schedule, bit for
-// bit, so is the result.
+// List pass (LIST = true): a warp takes 32 listed pixels, stages their records
+// in a larger slab and runs the search and the emission of each, a lane per
+// pixel, over the slab.  Every lane of a list warp searches, so none idles
+// behind a searching neighbour as in the direct schedules.  A listed pixel
+// whose records exceed the list slab is composited by the direct sweep.
+// The pieces are those of every other schedule, bit for bit, so is the result.
 // ---------------------------------------------------------------------------
-constexpr int kLaneKMax = 8;      // PEs the lane path handles (heads in registers)
-constexpr int kLaneWarps = 4;     // warps per CTA of composite_lane_kernel
-constexpr int kLaneRCap = 480;    // records per warp slab
+constexpr int kLaneKMax = 8;        // PEs the lane path handles (heads in registers)
+constexpr int kLaneWarps = 4;       // warps per CTA
+constexpr int kLaneRCap = 480;      // records per warp slab, batch pass
+constexpr int kLaneListRCap = 1024; // records per warp slab, list pass
 
-template <int PREC>
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// A warp's slab of CAP records: F32 as rgba[] then fb[], F16 as the raw
+// 16-byte records.
+template <int PREC, int CAP>
 struct LaneSlab;
-template <>
-struct LaneSlab<VDI_PREC_F32> {
-    float4 rgba[kLaneRCap];
-    float2 fb[kLaneRCap];
+template <int CAP>
+struct LaneSlab<VDI_PREC_F32, CAP> {
+    float4 rgba[CAP];
+    float2 fb[CAP];
     __device__ __forceinline__ float2 bounds(uint32_t i) const { return fb[i]; }
     __device__ __forceinline__ RecC rec(uint32_t i) const {
         RecC r;
@@ -1456,13 +1485,13 @@ struct LaneSlab<VDI_PREC_F32> {
         return r;
     }
     __device__ __forceinline__ void copy(const PeIn& pe, uint64_t src, uint32_t dst) {
-        rgba[dst] = __ldcs(reinterpret_cast<const float4*>(pe.rgba) + src);
-        fb[dst] = __ldcs(pe.fb + src);
+        cp_async16(rgba + dst, reinterpret_cast<const float4*>(pe.rgba) + src);
+        cp_async8(fb + dst, pe.fb + src);
     }
 };
-template <>
-struct LaneSlab<VDI_PREC_F16> {
-    uint4 raw[kLaneRCap];
+template <int CAP>
+struct LaneSlab<VDI_PREC_F16, CAP> {
+    uint4 raw[CAP];
     __device__ __forceinline__ float2 bounds(uint32_t i) const {
         return make_float2(__uint_as_float(raw[i].x), __uint_as_float(raw[i].y));
     }
@@ -1472,17 +1501,13 @@ struct LaneSlab<VDI_PREC_F16> {
         return r;
     }
     __device__ __forceinline__ void copy(const PeIn& pe, uint64_t src, uint32_t dst) {
-        raw[dst] = __ldcs(reinterpret_cast<const uint4*>(pe.rgba) + src);
+        cp_async16(raw + dst, reinterpret_cast<const uint4*>(pe.rgba) + src);
     }
 };
 
-// The pieces of one pixel from its K lists in the slab (list e: slab entries
-// [st[e], st[e] + cnt[e])), in depth order: the sweep of sweep_reg with the
-// records read from shared memory.
 // moves a head to its next record with b > f (records with b <= f are ignored)
-template <int PREC>
-__device__ __forceinline__ void slab_next_valid(const LaneSlab<PREC>& S, uint32_t& cur, uint32_t& rem, float& hf,
-                                                float& hb) {
+template <class SLAB>
+__device__ __forceinline__ void slab_next_valid(const SLAB& S, uint32_t& cur, uint32_t& rem, float& hf, float& hb) {
     while (rem > 0) {
         const float2 fb = S.bounds(cur);
         if (fb.y > fb.x) {
@@ -1495,8 +1520,11 @@ __device__ __forceinline__ void slab_next_valid(const LaneSlab<PREC>& S, uint32_
     }
 }
 
-template <int PREC, typename V>
-__device__ __forceinline__ int sweep_slab(const LaneSlab<PREC>& S, int k, const uint32_t st[kLaneKMax],
+// The pieces of one pixel from its K lists in the slab (list e: slab entries
+// [st[e], st[e] + cnt[e])), in depth order: the sweep of sweep_reg with the
+// records read from shared memory.
+template <class SLAB, typename V>
+__device__ __forceinline__ int sweep_slab(const SLAB& S, int k, const uint32_t st[kLaneKMax],
                                           const uint32_t cnt[kLaneKMax], V& visit) {
     uint32_t cur[kLaneKMax], rem[kLaneKMax];
     float hf[kLaneKMax], hb[kLaneKMax];
@@ -1509,7 +1537,7 @@ __device__ __forceinline__ int sweep_slab(const LaneSlab<PREC>& S, int k, const 
         if (e < k) {
             cur[e] = st[e];
             rem[e] = cnt[e];
-            slab_next_valid<PREC>(S, cur[e], rem[e], hf[e], hb[e]);
+            slab_next_valid(S, cur[e], rem[e], hf[e], hb[e]);
             if (rem[e] > 0) t = fminf(t, hf[e]);
         }
     }
@@ -1594,13 +1622,26 @@ __device__ __forceinline__ int sweep_slab(const LaneSlab<PREC>& S, int k, const 
             if (((act >> e) & 1u) && hb[e] <= t1) {
                 ++cur[e];
                 --rem[e];
-                slab_next_valid<PREC>(S, cur[e], rem[e], hf[e], hb[e]);
+                slab_next_valid(S, cur[e], rem[e], hf[e], hb[e]);
             }
         }
         t = t1;
     }
     return npieces;
 }
+
+// One pixel's sweeps over the slab, for composite_search_emit.
+template <class SLAB>
+struct SlabSweeper {
+    static constexpr bool kSelectSteps = false;  // counting steps with branches (see CountVisitorQ)
+    const SLAB* S;
+    int k;
+    uint32_t st[kLaneKMax], cnt[kLaneKMax];
+    template <typename V>
+    __device__ __forceinline__ int run(V& v) const {
+        return sweep_slab(*S, k, st, cnt, v);
+    }
+};
 
 struct NtVisitor {
     int nt;
@@ -1623,8 +1664,8 @@ __device__ __forceinline__ void finish_pixel(const OutDev& out, uint32_t p, int 
 }
 
 struct LaneArgs {
-    unsigned int* counter;  // batch counter
-    uint32_t* list;         // [0]: count, [2..]: pixels for composite_list_kernel
+    unsigned int* counter;  // [0]: batch counter of the batch pass, [1]: item counter of the list pass
+    uint32_t* list;         // [0]: count, [2..]: pixels for the list pass
 };
 
 // appends the lanes with `flag` set to the list (one atomic per warp)
@@ -1639,22 +1680,101 @@ __device__ __forceinline__ void list_push(uint32_t* list, bool flag, uint32_t p)
     if (flag) list[2 + base + __popc(m & ((1u << lane) - 1u))] = p;
 }
 
+// Copies the records of the lanes with `take` set into the slab, PE-major,
+// and sets st[e] to each lane's first slab entry of PE e.  The copies are
+// asynchronous; the caller waits once for all of them.
+template <class SLAB>
+__device__ __forceinline__ void slab_stage(const PeIn* pe, int k, SLAB& S, bool take, const uint32_t cnt[kLaneKMax],
+                                           const uint64_t off[kLaneKMax], uint32_t st[kLaneKMax]) {
+    const int lane = threadIdx.x & 31;
+    uint32_t base_e = 0;
+#pragma unroll
+    for (int e = 0; e < kLaneKMax; ++e) {
+        st[e] = 0;
+        if (e < k) {
+            const uint32_t ce = take ? cnt[e] : 0u;
+            const uint32_t ie = warp_incl_scan_u32(ce);
+            const uint32_t pre = ie - ce;
+            const uint32_t n_e = __shfl_sync(0xffffffffu, ie, 31);
+            st[e] = base_e + pre;
+            // PE e's spans of this round are one run of its record array iff every non-empty span starts
+            // where the previous ones leave off
+            const unsigned nz = __ballot_sync(0xffffffffu, ce > 0);
+            if (nz) {
+                const int f = __ffs(nz) - 1;
+                const uint64_t o0 = __shfl_sync(0xffffffffu, off[e], f);
+                const bool run = !__any_sync(0xffffffffu, ce > 0 && off[e] != o0 + pre);
+                for (uint32_t r0 = 0; r0 < n_e; r0 += 32) {
+                    const uint32_t r = r0 + (uint32_t)lane;
+                    uint64_t src = o0 + r;
+                    if (!run) {
+                        // the lane whose span holds record r: the last with pre <= r
+                        int lo = 0, hi = 31;
+#pragma unroll
+                        for (int it = 0; it < 5; ++it) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            const uint32_t pm = __shfl_sync(0xffffffffu, pre, mid);
+                            if (pm <= r) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        const uint64_t oq = __shfl_sync(0xffffffffu, off[e], lo);
+                        const uint32_t pq = __shfl_sync(0xffffffffu, pre, lo);
+                        src = oq + (r - pq);
+                    }
+                    if (r < n_e) S.copy(pe[e], src, base_e + r);
+                }
+            }
+            base_e += n_e;
+        }
+    }
+}
+
+// the listed pixels the list pass marked (records beyond its slab), by the direct sweep
 template <int PREC, bool CENSUS>
+__global__ void __launch_bounds__(128) composite_marked_kernel(const __grid_constant__ CompArgs a,
+                                                               const uint32_t* __restrict__ list) {
+    const uint32_t n = *list;
+    CompCensus cs;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t v = list[2 + i];
+        if (v & 0x80000000u)
+            composite_pixel<kLaneKMax, 16, 2, PREC, CENSUS>(a.pe, a.k, a.out, a.iters, a.status, v & 0x7FFFFFFFu,
+                                                            nullptr, &cs);
+    }
+    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
+}
+
+template <int PREC, int CAP>
+constexpr size_t lane_smem_bytes() {
+    return kLaneWarps * sizeof(LaneSlab<PREC, CAP>);
+}
+
+template <int PREC, bool CENSUS, bool LIST>
 __global__ void __launch_bounds__(kLaneWarps * 32) composite_lane_kernel(const __grid_constant__ CompArgs a,
                                                                         const __grid_constant__ LaneArgs la) {
-    __shared__ LaneSlab<PREC> slabs[kLaneWarps];
+    constexpr int CAP = LIST ? kLaneListRCap : kLaneRCap;
+    using Slab = LaneSlab<PREC, CAP>;
+    extern __shared__ __align__(16) unsigned char lane_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    LaneSlab<PREC>& S = slabs[warp];
-    const uint32_t nbatch = ((uint32_t)a.npix + 31u) / 32u;
+    Slab& S = reinterpret_cast<Slab*>(lane_smem)[warp];
     const int k = a.k;
+    const uint32_t nitems = LIST ? (*la.list + 31u) / 32u : ((uint32_t)a.npix + 31u) / 32u;
     CompCensus cs;
     while (true) {
-        uint32_t batch = 0;
-        if (lane == 0) batch = atomicAdd(la.counter, 1u);
-        batch = __shfl_sync(0xffffffffu, batch, 0);
-        if (batch >= nbatch) break;
-        const uint32_t p = batch * 32u + (uint32_t)lane;
-        const bool valid = p < (uint32_t)a.npix;
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(la.counter + (LIST ? 1 : 0), 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= nitems) break;
+        bool valid;
+        uint32_t p;
+        if constexpr (LIST) {
+            const uint32_t i = item * 32u + (uint32_t)lane;
+            valid = i < *la.list;
+            p = valid ? la.list[2 + i] : 0u;
+        } else {
+            p = item * 32u + (uint32_t)lane;
+            valid = p < (uint32_t)a.npix;
+        }
         uint32_t cnt[kLaneKMax];
         uint64_t off[kLaneKMax];
         uint32_t tot = 0;
@@ -1668,167 +1788,78 @@ __global__ void __launch_bounds__(kLaneWarps * 32) composite_lane_kernel(const _
                 tot += cnt[e];
             }
         }
-        const bool big = valid && tot > (uint32_t)kLaneRCap;
-        list_push(la.list, big, p);
+        const bool big = valid && tot > (uint32_t)CAP;
+        if constexpr (LIST) {
+            if (big) la.list[2 + item * 32u + (uint32_t)lane] = p | 0x80000000u;  // for composite_marked_kernel
+        } else {
+            list_push(la.list, big, p);
+        }
         bool pending = valid && !big;
         while (__any_sync(0xffffffffu, pending)) {
             // this round: the pending lanes, in order, whose records fit the slab together
             const uint32_t incl = warp_incl_scan_u32(pending ? tot : 0u);
-            const bool take = pending && incl <= (uint32_t)kLaneRCap;
+            const bool take = pending && incl <= (uint32_t)CAP;
             pending = pending && !take;
             uint32_t st[kLaneKMax];
-            uint32_t base_e = 0;
-#pragma unroll
-            for (int e = 0; e < kLaneKMax; ++e) {
-                st[e] = 0;
-                if (e < k) {
-                    const uint32_t ce = take ? cnt[e] : 0u;
-                    const uint32_t ie = warp_incl_scan_u32(ce);
-                    const uint32_t pre = ie - ce;
-                    const uint32_t n_e = __shfl_sync(0xffffffffu, ie, 31);
-                    st[e] = base_e + pre;
-                    // PE e's spans of this round are one run of its record array iff every
-                    // non-empty span starts where the previous ones leave off
-                    const unsigned nz = __ballot_sync(0xffffffffu, ce > 0);
-                    if (nz) {
-                        const int f = __ffs(nz) - 1;
-                        const uint64_t o0 = __shfl_sync(0xffffffffu, off[e], f);
-                        const bool run = !__any_sync(0xffffffffu, ce > 0 && off[e] != o0 + pre);
-                        for (uint32_t r0 = 0; r0 < n_e; r0 += 32) {
-                            const uint32_t r = r0 + (uint32_t)lane;
-                            uint64_t src = o0 + r;
-                            if (!run) {
-                                // the lane whose span holds record r: the last with pre <= r
-                                int lo = 0, hi = 31;
-#pragma unroll
-                                for (int it = 0; it < 5; ++it) {
-                                    const int mid = (lo + hi + 1) >> 1;
-                                    const uint32_t pm = __shfl_sync(0xffffffffu, pre, mid);
-                                    if (pm <= r) lo = mid;
-                                    else hi = mid - 1;
-                                }
-                                const uint64_t oq = __shfl_sync(0xffffffffu, off[e], lo);
-                                const uint32_t pq = __shfl_sync(0xffffffffu, pre, lo);
-                                src = oq + (r - pq);
-                            }
-                            if (r < n_e) S.copy(a.pe[e], src, base_e + r);
-                        }
-                    }
-                    base_e += n_e;
-                }
-            }
+            slab_stage(a.pe, k, S, take, cnt, off, st);
+            cp_async_wait_all();
             __syncwarp();
             bool search = false;
             if (take) {
-                NtVisitor nv{0};
-                const int np = sweep_slab<PREC>(S, k, st, cnt, nv);
-                if (CENSUS) {
-                    cs.sweeps += 1;
-                    cs.pieces += (unsigned long long)np;
+                SlabSweeper<Slab> sw;
+                sw.S = &S;
+                sw.k = k;
+#pragma unroll
+                for (int e = 0; e < kLaneKMax; ++e) {
+                    sw.st[e] = st[e];
+                    sw.cnt[e] = cnt[e];
                 }
-                if (nv.nt <= a.out.n_s) {
-                    // gamma = 0: every non-transparent piece is a supersegment
-                    EmitVisitor em;
-                    em.s.cnt = 0;
-                    em.s.open = false;
-                    em.g2 = 0.f;
-                    em.cap = a.out.n_s;
-                    em.bt = 0.f;
-                    em.written = 0;
-                    em.base = (size_t)p * a.out.n_s;
-                    em.out = &a.out;
-                    sweep_slab<PREC>(S, k, st, cnt, em);
-                    if (em.s.open && em.written < a.out.n_s) em.store(em.s.fS, em.bt, em.s.P, em.s.A, em.s.L2);
-                    if (em.written != nv.nt) atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CUDA);
-                    finish_pixel(a.out, p, em.written, 0.f);
+                if (CENSUS) {
+                    cs.pixels += 1;
+                    cs.records += tot;
+                }
+                if constexpr (LIST) {
+                    composite_search_emit<2, CENSUS>(sw, a.out, a.iters, a.status, p, &cs);
+                } else {
+                    NtVisitor nv{0};
+                    const int np = sw.run(nv);
                     if (CENSUS) {
-                        cs.pixels += 1;
                         cs.sweeps += 1;
                         cs.pieces += (unsigned long long)np;
-                        cs.records += tot;
                     }
-                } else {
-                    search = true;
+                    if (nv.nt <= a.out.n_s) {
+                        // gamma = 0: every non-transparent piece is a supersegment
+                        EmitVisitor em;
+                        em.s.cnt = 0;
+                        em.s.open = false;
+                        em.g2 = 0.f;
+                        em.cap = a.out.n_s;
+                        em.bt = 0.f;
+                        em.written = 0;
+                        em.base = (size_t)p * a.out.n_s;
+                        em.out = &a.out;
+                        sw.run(em);
+                        if (em.s.open && em.written < a.out.n_s)
+                            em.store(em.s.fS, em.bt, em.s.P, em.s.A, em.s.L2);
+                        if (em.written != nv.nt) atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CUDA);
+                        finish_pixel(a.out, p, em.written, 0.f);
+                        if (CENSUS) {
+                            cs.sweeps += 1;
+                            cs.pieces += (unsigned long long)np;
+                        }
+                    } else {
+                        // searched in the list pass, which counts it again
+                        search = true;
+                        if (CENSUS) {
+                            cs.pixels -= 1;
+                            cs.records -= tot;
+                        }
+                    }
                 }
             }
-            list_push(la.list, search, p);
+            if constexpr (!LIST) list_push(la.list, search, p);
             __syncwarp();
         }
-    }
-    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
-}
-
-// Pieces of a pixel into its column of the warp's piece buffer (rows are 32
-// elements apart), with the count of non-transparent pieces; pieces past the
-// column's rows are counted, not written.
-struct ColumnWriter {
-    float4* A;
-    float2* B;
-    int rows, n, nt;
-    float f0;
-    __device__ __forceinline__ void operator()(const Piece& x) {
-        if (n == 0) f0 = x.f;
-        if (n < rows) {
-            A[(size_t)n * 32] = make_float4(x.P[0], x.P[1], x.P[2], x.a);
-            B[(size_t)n * 32] = make_float2(x.b, x.lgT);
-        }
-        ++n;
-        nt += x.a > 0.f;
-    }
-};
-
-template <int PREC, bool CENSUS>
-__global__ void __launch_bounds__(kStageWarps * 32) composite_list_kernel(const __grid_constant__ CompArgs a,
-                                                                         const __grid_constant__ StageArgs sa,
-                                                                         uint32_t* list) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t gw = (size_t)blockIdx.x * kStageWarps + warp;
-    float4* wA = sa.bufA + gw * (size_t)sa.rows * 32 + lane;
-    float2* wB = sa.bufB + gw * (size_t)sa.rows * 32 + lane;
-    const uint32_t n = *list;
-    const uint32_t nitems = (n + 31u) / 32u;
-    CompCensus cs;
-    for (uint32_t item = (uint32_t)gw; item < nitems; item += gridDim.x * kStageWarps) {
-        const uint32_t i = item * 32u + (uint32_t)lane;
-        if (i < n) {
-            const uint32_t p = list[2 + i];
-            Sweeper<kLaneKMax, 16, PREC> sw;
-            sw.init(a.pe, a.k, p, nullptr);
-            ColumnWriter cw{wA, wB, sa.rows, 0, 0, 0.f};
-            sw.run(cw);
-            if (CENSUS) {
-                cs.pixels += 1;
-                cs.records += sw.records();
-                cs.sweeps += 1;
-                cs.pieces += (unsigned long long)cw.n;
-            }
-            if (cw.n <= sa.rows) {
-                BufSweeper bs;
-                bs.A = wA;
-                bs.B = wB;
-                bs.n = cw.n;
-                bs.f0 = cw.f0;
-                composite_search_emit<2, CENSUS>(bs, a.out, a.iters, a.status, p, &cs);
-            } else {
-                // more pieces than the column holds: marked for composite_marked_kernel
-                list[2 + i] = p | 0x80000000u;
-            }
-        }
-    }
-    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
-}
-
-// the listed pixels composite_list_kernel marked, swept from their lists on every march
-template <int PREC, bool CENSUS>
-__global__ void __launch_bounds__(128) composite_marked_kernel(const __grid_constant__ CompArgs a,
-                                                               const uint32_t* __restrict__ list) {
-    const uint32_t n = *list;
-    CompCensus cs;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < n; i += gridDim.x * blockDim.x) {
-        const uint32_t v = i < n ? list[2 + i] : 0u;
-        if (v & 0x80000000u)
-            composite_pixel<kLaneKMax, 16, 2, PREC, CENSUS>(a.pe, a.k, a.out, a.iters, a.status, v & 0x7FFFFFFFu,
-                                                            nullptr, &cs);
     }
     if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
 }
@@ -2053,37 +2084,46 @@ static cudaError_t launch_staged(bool census, const CompArgs& a, void* workspace
     return launch_overflow<64, PREC>(census, a, sa.overflow, st);
 }
 
+template <int PREC, bool LIST>
+static cudaError_t launch_lane_pass(bool census, const CompArgs& a, const LaneArgs& la, uint64_t items,
+                                   cudaStream_t st) {
+    constexpr int CAP = LIST ? kLaneListRCap : kLaneRCap;
+    const size_t sm = lane_smem_bytes<PREC, CAP>();
+    auto kern = census ? composite_lane_kernel<PREC, true, LIST> : composite_lane_kernel<PREC, false, LIST>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLaneWarps * 32, sm);
+    if (e != cudaSuccess) return e;
+    uint64_t blocks = (uint64_t)device_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    const uint64_t need = (items + kLaneWarps - 1) / kLaneWarps;
+    if (blocks > need) blocks = need > 0 ? need : 1;
+    kern<<<(unsigned)blocks, kLaneWarps * 32, sm, st>>>(a, la);
+    return cudaGetLastError();
+}
+
 template <int PREC>
 static cudaError_t launch_lane(bool census, const CompArgs& a, void* workspace, size_t ws_bytes, cudaStream_t st) {
+    // workspace: [header][counters][list: count, pad, npix entries]
     const uint64_t npix = (uint64_t)a.npix;
-    const size_t ctas = stage_ctas((npix + 31) / 32);
-    const StageArgs sa = stage_args(workspace, ws_bytes, npix, 4, ctas);
-    if (sa.rows == 0) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(sa.counter, 0, 256 + 8, st);
-    if (e != cudaSuccess) return e;
-    auto k1 = census ? composite_lane_kernel<PREC, true> : composite_lane_kernel<PREC, false>;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, kLaneWarps * 32, 0);
+    if (ws_bytes < kWsHeader + 256 + stage_list_bytes(npix, 4)) return cudaErrorInvalidValue;
+    char* base = static_cast<char*>(workspace);
+    LaneArgs la;
+    la.counter = reinterpret_cast<unsigned int*>(base + kWsHeader);
+    la.list = reinterpret_cast<uint32_t*>(base + kWsHeader + 256);
+    cudaError_t e = cudaMemsetAsync(la.counter, 0, 256 + 8, st);
     if (e != cudaSuccess) return e;
     const uint64_t batches = (npix + 31) / 32;
-    uint64_t blocks = (uint64_t)device_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
-    const uint64_t need = (batches + kLaneWarps - 1) / kLaneWarps;
-    if (blocks > need) blocks = need > 0 ? need : 1;
-    LaneArgs la;
-    la.counter = sa.counter;
-    la.list = sa.overflow;
-    k1<<<(unsigned)blocks, kLaneWarps * 32, 0, st>>>(a, la);
-    e = cudaGetLastError();
+    e = launch_lane_pass<PREC, false>(census, a, la, batches, st);
     if (e != cudaSuccess) return e;
-    auto k2 = census ? composite_list_kernel<PREC, true> : composite_list_kernel<PREC, false>;
-    k2<<<(unsigned)ctas, kStageWarps * 32, 0, st>>>(a, sa, sa.overflow);
-    e = cudaGetLastError();
+    // the list pass: its grid is sized for every pixel listed (the count is known only on the device)
+    e = launch_lane_pass<PREC, true>(census, a, la, batches, st);
     if (e != cudaSuccess) return e;
     auto k3 = census ? composite_marked_kernel<PREC, true> : composite_marked_kernel<PREC, false>;
     unsigned b3 = (unsigned)((npix + 127) / 128);
-    const unsigned cap3 = (unsigned)device_sms() * 4u;
+    const unsigned cap3 = (unsigned)device_sms() * 2u;
     if (b3 > cap3) b3 = cap3;
-    k3<<<b3, 128, 0, st>>>(a, sa.overflow);
+    k3<<<b3, 128, 0, st>>>(a, la.list);
     return cudaGetLastError();
 }
 

@@ -48,9 +48,8 @@
 
 namespace vdi {
 
-struct GenArgs {
-    BrickDev b[VDI_MAX_PE];
-    CompactDev out[VDI_MAX_PE];
+// One generation request's parameters, shared by its PEs.
+struct GenReq {
     CamDev cam;
     int dims[3];
     const float* lut;  // 256 x 4, straight colour + opacity per ref_len
@@ -60,11 +59,17 @@ struct GenArgs {
     float gamma;
     int prec;
     int tiles_x, tiles_y;
+    OwnerDev own;  // non-convex ownership (own.map != nullptr): b[e] is the bounding box of PE e's blocks
+};
+
+struct GenArgs {
+    GenReq r;
+    BrickDev b[VDI_MAX_PE];
+    CompactDev out[VDI_MAX_PE];
     unsigned int* status;
     unsigned int* counter;  // work-item counter (persistent kernel)
     float2* cache;          // sample cache: [cap][slots] (table coordinate x, transparent samples before it)
     int cache_cap, slots;
-    OwnerDev own;  // non-convex ownership (own.map != nullptr): b[e] is the bounding box of PE e's blocks
 };
 
 // gen_count_kernel: CTAs of two warps on 16 x 4 tiles, eight per SM (128 registers), so that a
@@ -80,7 +85,7 @@ struct Census {
 
 // 257 entries of (colour/opacity, difference to the next entry); opacity
 // corrected to the step length: a' = 1 - (1 - a)^(step / ref_len).
-__device__ __forceinline__ void load_lut(const GenArgs& a, float4* lut2) {
+__device__ __forceinline__ void load_lut(const GenReq& a, float4* lut2) {
     __shared__ float4 base[257];
     for (int i = threadIdx.x; i < 257; i += blockDim.x) {
         int s = min(i, 255);
@@ -107,7 +112,7 @@ __device__ __forceinline__ void tile_pixel(int tiles_x, int tile, int th, int& i
 }
 
 // PE owning the cell of fixed-point midpoint P (clamped to the volume's cells).
-__device__ __forceinline__ int owner_at(const GenArgs& a, const long long P[3]) {
+__device__ __forceinline__ int owner_at(const GenReq& a, const long long P[3]) {
     int bl[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -143,7 +148,7 @@ __device__ __forceinline__ int block_span(const long long P[3], const long long 
 // first owned sample after a stretch of samples the PE does not own.
 template <typename F, typename B>
 __device__ __forceinline__ void march_owned(const Ray& r, int k0, int k1, const BrickDev& b,
-                                            const float4* __restrict__ lut2, float scale255, const GenArgs& a, int e,
+                                            const float4* __restrict__ lut2, float scale255, const GenReq& a, int e,
                                             F&& f, B&& on_break) {
     long long P[3];
 #pragma unroll
@@ -283,7 +288,7 @@ struct CacheRef {
 template <int NC, bool OWNED = false>
 __device__ __forceinline__ int first_march(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
                                            float scale255, const float* g2, int cap, const CacheRef* c, int* cnt,
-                                           Census& cs, const GenArgs* ga = nullptr, int e = 0, int* runs = nullptr) {
+                                           Census& cs, const GenReq* ga = nullptr, int e = 0, int* runs = nullptr) {
     cs.evals += (unsigned long long)(k1 - k0);
     cs.steps += (unsigned long long)(k1 - k0) * NC;
     cs.passes += 1;
@@ -362,7 +367,7 @@ __device__ __forceinline__ void cached_march(const CacheRef& c, int nt, const fl
 template <bool OWNED = false>
 __device__ __forceinline__ void volume_march(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
                                              float scale255, const float g2[3], int cnt[3], Census& cs,
-                                             const GenArgs* ga, int e) {
+                                             const GenReq* ga, int e) {
     int runs = 0;
     first_march<3, OWNED>(r, k0, k1, b, lut2, scale255, g2, INT_MAX, nullptr, cnt, cs, ga, e, &runs);
 }
@@ -374,7 +379,7 @@ __device__ __forceinline__ void volume_march(const Ray& r, int k0, int k1, const
 template <bool OWNED = false>
 __device__ __forceinline__ float search(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
                                         float scale255, int n_s, int iters, int nt, const CacheRef* c, int& count,
-                                        Census& cs, const GenArgs* ga = nullptr, int e = 0, int runs = 1) {
+                                        Census& cs, const GenReq* ga = nullptr, int e = 0, int runs = 1) {
     float lo = 0.f, hi = 2.f;
     // the distance never reaches 2: one supersegment per domain run
     int cnt_hi = nt > 0 ? (OWNED ? runs : 1) : 0;
@@ -517,18 +522,91 @@ __device__ __forceinline__ bool bracket_refine(const CacheRef& c, int nt, const 
     return true;
 }
 
-// The learned-gamma refinement (mode 3) is compiled only into the LEARNED
+// gamma and count of one (PE, ray): the body of the count kernels.  The
+// learned-gamma refinement (mode 3) is compiled only into the LEARNED
 // instantiation so that the search kernel keeps its register budget.  Every
 // march is inlined: out-of-line calls in this persistent loop cost far more
 // than the spills inlining brings (the learned choice took 80.6 ms with the
 // refinement, its marches and the search fallback out of line, 65.6 ms inlined).
+template <bool LEARNED, bool OWNED>
+__device__ __forceinline__ void count_ray(const GenReq& a, const BrickDev& b, const CompactDev& o, int e, int i, int j,
+                                          const float4* __restrict__ lut2, const CacheRef& cref, Census& cs,
+                                          unsigned long long& rays) {
+    const int mode = LEARNED ? 3 : a.mode;
+    const size_t p = (size_t)j * a.cam.W + i;
+    Ray r;
+    int k0 = 0, k1 = 0;
+    const bool any = ray_setup(a.cam, i, j, a.dims, a.step, r) && owned_range(r, a.step, b, a.dims, k0, k1);
+    float gamma = mode == 0 ? a.gamma : (mode >= 2 ? fmaxf(o.gamma[p], 0.f) : 0.f);
+    int count = 0;
+    int runs = 1;
+    if (any) {
+        rays += 1;
+        if (mode == 0) {
+            const float g2[1] = {__fmul_rn(a.gamma, a.gamma)};
+            int c[1];
+            first_march<1, OWNED>(r, k0, k1, b, lut2, a.scale255, g2, a.n_s, nullptr, c, cs, &a, e, &runs);
+            count = c[0];
+        } else {
+            const bool use_cache = cref.e != nullptr;
+            int nt;
+            bool searched = true;
+            if (mode >= 2) {
+                // one march: count at the given gamma, non-transparent count, cache
+                const float g2[1] = {__fmul_rn(gamma, gamma)};
+                int c[1];
+                nt = first_march<1, OWNED>(r, k0, k1, b, lut2, a.scale255, g2, INT_MAX, use_cache ? &cref : nullptr,
+                                           c, cs, &a, e, &runs);
+                if (mode == 2) {
+                    if (c[0] <= a.n_s) {
+                        count = c[0];
+                        searched = false;
+                    }
+                } else if (LEARNED && nt > a.n_s && use_cache && nt <= cref.cap) {
+                    searched = !bracket_refine(cref, nt, lut2, gamma, c[0], a.n_s, gamma, count, cs);
+                }
+            } else {
+                int dummy[1];
+                nt = first_march<0, OWNED>(r, k0, k1, b, lut2, a.scale255, nullptr, INT_MAX,
+                                           use_cache ? &cref : nullptr, dummy, cs, &a, e, &runs);
+            }
+            if (searched) {
+                if (nt <= a.n_s) {
+                    gamma = 0.f;
+                    count = nt;
+                } else {
+                    const CacheRef* c = (use_cache && nt <= cref.cap) ? &cref : nullptr;
+                    cs.searched += 1;
+                    cs.overflow += c ? 0 : 1;
+                    gamma = search<OWNED>(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count, cs, &a, e,
+                                          runs);
+                }
+            }
+        }
+    }
+    o.counts[p] = (uint32_t)count;
+    if (o.gamma) o.gamma[p] = gamma;
+}
+
+__device__ __forceinline__ void census_flush_gen(const Census& cs, unsigned long long rays, unsigned int* status) {
+    unsigned long long* ctr = reinterpret_cast<WsHeader*>(status)->counters;
+    atomicAdd(ctr + 0, cs.evals);
+    atomicAdd(ctr + 1, cs.steps);
+    atomicAdd(ctr + 2, cs.passes);
+    atomicAdd(ctr + 3, rays);
+    atomicAdd(ctr + 4, cs.searched);
+    atomicAdd(ctr + 5, cs.overflow);
+    atomicAdd(ctr + 6, cs.cached);
+    atomicAdd(ctr + 7, cs.remarched);
+}
+
 template <bool CENSUS, bool LEARNED, bool OWNED = false>
 __global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     __shared__ unsigned int s_item;
-    load_lut(a, lut2);
-    const unsigned tiles = (unsigned)(a.tiles_x * a.tiles_y);
-    const unsigned total = tiles * (unsigned)a.k;
+    load_lut(a.r, lut2);
+    const unsigned tiles = (unsigned)(a.r.tiles_x * a.r.tiles_y);
+    const unsigned total = tiles * (unsigned)a.r.k;
     CacheRef cref;
     cref.e = a.cache;
     cref.slot = blockIdx.x * blockDim.x + threadIdx.x;
@@ -536,7 +614,6 @@ __global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __gri
     cref.cap = a.cache_cap;
     Census cs;
     unsigned long long rays = 0;
-    const int mode = LEARNED ? 3 : a.mode;
     while (true) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
         __syncthreads();
@@ -545,75 +622,11 @@ __global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __gri
         if (item >= total) break;
         const int e = (int)(item / tiles);
         int i, j;
-        tile_pixel(a.tiles_x, (int)(item % tiles), kCountTileH, i, j);
-        if (i >= a.cam.W || j >= a.cam.H) continue;
-        const BrickDev& b = a.b[e];
-        const CompactDev& o = a.out[e];
-        const size_t p = (size_t)j * a.cam.W + i;
-        Ray r;
-        int k0 = 0, k1 = 0;
-        const bool any = ray_setup(a.cam, i, j, a.dims, a.step, r) && owned_range(r, a.step, b, a.dims, k0, k1);
-        float gamma = mode == 0 ? a.gamma : (mode >= 2 ? fmaxf(o.gamma[p], 0.f) : 0.f);
-        int count = 0;
-        int runs = 1;
-        if (any) {
-            rays += 1;
-            if (mode == 0) {
-                const float g2[1] = {__fmul_rn(a.gamma, a.gamma)};
-                int c[1];
-                first_march<1, OWNED>(r, k0, k1, b, lut2, a.scale255, g2, a.n_s, nullptr, c, cs, &a, e, &runs);
-                count = c[0];
-            } else {
-                const bool use_cache = a.cache != nullptr;
-                int nt;
-                bool searched = true;
-                if (mode >= 2) {
-                    // one march: count at the given gamma, non-transparent count, cache
-                    const float g2[1] = {__fmul_rn(gamma, gamma)};
-                    int c[1];
-                    nt = first_march<1, OWNED>(r, k0, k1, b, lut2, a.scale255, g2, INT_MAX,
-                                               use_cache ? &cref : nullptr, c, cs, &a, e, &runs);
-                    if (mode == 2) {
-                        if (c[0] <= a.n_s) {
-                            count = c[0];
-                            searched = false;
-                        }
-                    } else if (LEARNED && nt > a.n_s && use_cache && nt <= a.cache_cap) {
-                        searched = !bracket_refine(cref, nt, lut2, gamma, c[0], a.n_s, gamma, count, cs);
-                    }
-                } else {
-                    int dummy[1];
-                    nt = first_march<0, OWNED>(r, k0, k1, b, lut2, a.scale255, nullptr, INT_MAX,
-                                               use_cache ? &cref : nullptr, dummy, cs, &a, e, &runs);
-                }
-                if (searched) {
-                    if (nt <= a.n_s) {
-                        gamma = 0.f;
-                        count = nt;
-                    } else {
-                        const CacheRef* c = (use_cache && nt <= a.cache_cap) ? &cref : nullptr;
-                        cs.searched += 1;
-                        cs.overflow += c ? 0 : 1;
-                        gamma = search<OWNED>(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count,
-                                                        cs, &a, e, runs);
-                    }
-                }
-            }
-        }
-        o.counts[p] = (uint32_t)count;
-        if (o.gamma) o.gamma[p] = gamma;
+        tile_pixel(a.r.tiles_x, (int)(item % tiles), kCountTileH, i, j);
+        if (i >= a.r.cam.W || j >= a.r.cam.H) continue;
+        count_ray<LEARNED, OWNED>(a.r, a.b[e], a.out[e], e, i, j, lut2, cref, cs, rays);
     }
-    if (CENSUS) {
-        unsigned long long* ctr = reinterpret_cast<WsHeader*>(a.status)->counters;
-        atomicAdd(ctr + 0, cs.evals);
-        atomicAdd(ctr + 1, cs.steps);
-        atomicAdd(ctr + 2, cs.passes);
-        atomicAdd(ctr + 3, rays);
-        atomicAdd(ctr + 4, cs.searched);
-        atomicAdd(ctr + 5, cs.overflow);
-        atomicAdd(ctr + 6, cs.cached);
-        atomicAdd(ctr + 7, cs.remarched);
-    }
+    if (CENSUS) census_flush_gen(cs, rays, a.status);
 }
 
 struct RecOut {
@@ -621,12 +634,13 @@ struct RecOut {
     float L2;  // log2(1 - A) of the record: its FP16 form stores -L2
 };
 
-__device__ __forceinline__ void store_record(const GenArgs& a, const CompactDev& o, uint64_t idx, const RecOut& r) {
+__device__ __forceinline__ void store_record(unsigned int* status, int prec, const CompactDev& o, uint64_t idx,
+                                             const RecOut& r) {
     if (idx >= o.capacity) {
-        atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CAPACITY);
+        atomicCAS(status, 0u, (unsigned)VDI_ERR_CAPACITY);
         return;
     }
-    if (a.prec == VDI_PREC_F32) {
+    if (prec == VDI_PREC_F32) {
         reinterpret_cast<float4*>(o.rgba)[idx] = make_float4(r.P[0], r.P[1], r.P[2], r.A);
         reinterpret_cast<float2*>(o.fb)[idx] = make_float2(r.f, r.b);
     } else {
@@ -634,18 +648,12 @@ __device__ __forceinline__ void store_record(const GenArgs& a, const CompactDev&
     }
 }
 
-// REGULAR: records at p * n_s with a zero tail.  Compile-time, so that the
-// compact path carries none of it (as a run-time flag it cost the compact
-// emission 70%).
+// Emission of pixel (i, j) of PE e (one CTA = one tile of kEmitThreads pixels of one PE; `inside`:
+// the pixel lies in the image).  REGULAR: records at p * n_s with a zero tail.  Compile-time, so that
+// the compact path carries none of it (as a run-time flag it cost the compact emission 70%).
 template <bool OWNED, bool REGULAR>
-__global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_constant__ GenArgs a) {
-    __shared__ float4 lut2[2 * 257];
-    int i, j;
-    tile_pixel(a.tiles_x, blockIdx.x, kEmitTileH, i, j);
-    const bool inside = i < a.cam.W && j < a.cam.H;
-    const int e = blockIdx.y;
-    const BrickDev& b = a.b[e];
-    const CompactDev& o = a.out[e];
+__device__ __forceinline__ void emit_ray(const GenReq& a, const BrickDev& b, const CompactDev& o, int e, int i, int j,
+                                         bool inside, float4* lut2, unsigned int* status) {
     const size_t p = inside ? (size_t)j * a.cam.W + i : 0;
     const uint32_t want = inside ? o.counts[p] : 0u;
     // most (PE, tile) pairs hold no record (rays that miss the PE's box): such a CTA of the compact
@@ -661,7 +669,7 @@ __global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_
         if constexpr (REGULAR) {
             const RecOut z{0.f, 0.f, {0.f, 0.f, 0.f}, 0.f, 0.f};
             for (uint32_t q = min(written, (uint32_t)a.n_s); q < (uint32_t)a.n_s; ++q)
-                store_record(a, o, (uint64_t)p * (uint64_t)a.n_s + q, z);
+                store_record(status, a.prec, o, (uint64_t)p * (uint64_t)a.n_s + q, z);
         }
     };
     if (want == 0) {
@@ -681,7 +689,7 @@ __global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_
         if (base + want > o.capacity) {
             room = base >= o.capacity ? 0u : (uint32_t)(o.capacity - base);
             o.counts[p] = room;
-            atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CAPACITY);
+            atomicCAS(status, 0u, (unsigned)VDI_ERR_CAPACITY);
         }
     }
     Ray r;
@@ -706,7 +714,7 @@ __global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_
         // S closed by this sample: either it was shut (m = 0) or a new one opened
         const bool closed = was_open && (st.m == 0.f || st.cnt != before);
         if (closed) {
-            if (written < room) store_record(a, o, base + written, cur);
+            if (written < room) store_record(status, a.prec, o, base + written, cur);
             ++written;
         }
         if (st.cnt != before) {
@@ -722,7 +730,7 @@ __global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_
             if (st.m == 0.f) return;
             const RecOut cur{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1),
                              {st.P[0], st.P[1], st.P[2]}, st.A, st.L2};
-            if (written < room) store_record(a, o, base + written, cur);
+            if (written < room) store_record(status, a.prec, o, base + written, cur);
             ++written;
             st.m = 0.f;
         });
@@ -733,12 +741,141 @@ __global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_
         if (written < room) {
             RecOut ro{sample_front(r, a.step, kopen), sample_front(r, a.step, klast + 1), {st.P[0], st.P[1], st.P[2]},
                       st.A, st.L2};
-            store_record(a, o, base + written, ro);
+            store_record(status, a.prec, o, base + written, ro);
         }
         ++written;
     }
-    if (written != want) atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CUDA);
+    if (written != want) atomicCAS(status, 0u, (unsigned)VDI_ERR_CUDA);
     zero_tail();
+}
+
+template <bool OWNED, bool REGULAR>
+__global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_constant__ GenArgs a) {
+    __shared__ float4 lut2[2 * 257];
+    int i, j;
+    tile_pixel(a.r.tiles_x, blockIdx.x, kEmitTileH, i, j);
+    const bool inside = i < a.r.cam.W && j < a.r.cam.H;
+    const int e = blockIdx.y;
+    emit_ray<OWNED, REGULAR>(a.r, a.b[e], a.out[e], e, i, j, inside, lut2, a.status);
+}
+
+// ---------------------------------------------------------------------------
+// Batched generation: uneven requests (their own volumes, cameras, image
+// sizes, K, N_S, gamma modes and precisions) in one persistent count launch
+// over (request, PE, 16 x 4 tile) items, one batched prefix sum and one emit
+// launch over (request, PE, 16 x 8 tile) items.  The table (host and device
+// copies, the same bytes): [header][GenBatchReq x n][GenBatchPe x sum k]
+// [ScanList x sum k].
+// ---------------------------------------------------------------------------
+struct GenBatchReq {
+    GenReq r;
+    uint32_t item_begin;   // first count item of the request
+    uint32_t eitem_begin;  // first emit item
+    uint32_t pe_begin;     // first PE descriptor
+    int etiles_y;          // emit tile rows
+};
+
+struct GenBatchPe {
+    BrickDev b;
+    CompactDev out;
+};
+
+struct GenBatchHeader {
+    uint32_t n, total_items, total_eitems, total_pes;
+    uint32_t total_chunks, pad;
+    uint64_t reqs_off, pes_off, lists_off;
+};
+
+struct GenBatchArgs {
+    const GenBatchReq* reqs;
+    const GenBatchPe* pes;
+    int n;
+    uint32_t total_items;
+    unsigned int* status;
+    unsigned int* counter;
+    float2* cache;
+    int cache_cap, slots;
+};
+
+// the request holding work item `item` (the last one beginning at or before it)
+template <bool EMIT>
+__device__ __forceinline__ int batch_request(const GenBatchReq* reqs, int n, uint32_t item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const uint32_t b = EMIT ? __ldg(&reqs[mid].eitem_begin) : __ldg(&reqs[mid].item_begin);
+        if (b <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kCountThreads, 8) gen_count_batched_kernel(const __grid_constant__ GenBatchArgs a) {
+    __shared__ float4 lut2[2 * 257];
+    __shared__ unsigned int s_item;
+    CacheRef cref;
+    cref.e = a.cache;
+    cref.slot = blockIdx.x * blockDim.x + threadIdx.x;
+    cref.slots = a.slots;
+    cref.cap = a.cache_cap;
+    Census cs;
+    unsigned long long rays = 0;
+    int cur = -1;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const unsigned item = s_item;
+        __syncthreads();
+        if (item >= a.total_items) break;
+        const int q = batch_request<false>(a.reqs, a.n, item);
+        const GenBatchReq& br = a.reqs[q];
+        if (q != cur) {  // the CTA's table follows its request (q is the same for the whole CTA)
+            load_lut(br.r, lut2);
+            cur = q;
+        }
+        const unsigned tiles = (unsigned)(br.r.tiles_x * br.r.tiles_y);
+        const unsigned local = item - br.item_begin;
+        const int e = (int)(local / tiles);
+        int i, j;
+        tile_pixel(br.r.tiles_x, (int)(local % tiles), kCountTileH, i, j);
+        if (i >= br.r.cam.W || j >= br.r.cam.H) continue;
+        const GenBatchPe& pe = a.pes[br.pe_begin + e];
+        count_ray<false, false>(br.r, pe.b, pe.out, e, i, j, lut2, cref, cs, rays);
+    }
+}
+
+__global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_batched_kernel(const __grid_constant__ GenBatchArgs a) {
+    __shared__ float4 lut2[2 * 257];
+    const uint32_t item = blockIdx.x;
+    const int q = batch_request<true>(a.reqs, a.n, item);
+    const GenBatchReq& br = a.reqs[q];
+    const unsigned etiles = (unsigned)(br.r.tiles_x * br.etiles_y);
+    const unsigned local = item - br.eitem_begin;
+    const int e = (int)(local / etiles);
+    int i, j;
+    tile_pixel(br.r.tiles_x, (int)(local % etiles), kEmitTileH, i, j);
+    const bool inside = i < br.r.cam.W && j < br.r.cam.H;
+    const GenBatchPe& pe = a.pes[br.pe_begin + e];
+    emit_ray<false, false>(br.r, pe.b, pe.out, e, i, j, inside, lut2, a.status);
+}
+
+static void fill_req(GenReq& r, int k, const float* lut, const CamDev& cam, const int dims[3], float scale255,
+                     float step, float ref_len, int n_s) {
+    r.cam = cam;
+    for (int q = 0; q < 3; ++q) r.dims[q] = dims[q];
+    r.lut = lut;
+    r.scale255 = scale255;
+    r.step = step;
+    r.ref_len = ref_len;
+    r.k = k;
+    r.n_s = n_s;
+    r.iters = 0;
+    r.mode = 0;
+    r.gamma = 0.f;
+    r.prec = 0;
+    r.tiles_x = (cam.W + kTileW - 1) / kTileW;
+    r.tiles_y = (cam.H + kCountTileH - 1) / kCountTileH;  // the count kernel's; the emit launch sets its own
+    r.own = OwnerDev{nullptr, 0, {0, 0, 0}};
 }
 
 static void fill_args(GenArgs& a, const BrickDev* bricks, int k, const float* lut, const CamDev& cam,
@@ -748,22 +885,17 @@ static void fill_args(GenArgs& a, const BrickDev* bricks, int k, const float* lu
         a.b[e] = bricks[e];
         a.out[e] = out[e];
     }
-    a.cam = cam;
-    for (int q = 0; q < 3; ++q) a.dims[q] = dims[q];
-    a.lut = lut;
-    a.scale255 = scale255;
-    a.step = step;
-    a.ref_len = ref_len;
-    a.k = k;
-    a.n_s = n_s;
+    fill_req(a.r, k, lut, cam, dims, scale255, step, ref_len, n_s);
     a.status = status;
-    a.tiles_x = (cam.W + kTileW - 1) / kTileW;
-    a.tiles_y = (cam.H + kCountTileH - 1) / kCountTileH;  // the count kernel's; the emit launch sets its own
     a.counter = nullptr;
     a.cache = nullptr;
     a.cache_cap = 0;
     a.slots = 0;
-    a.own = OwnerDev{nullptr, 0, {0, 0, 0}};
+}
+
+// count-kernel mode of a gamma argument
+static int gamma_mode(float gamma) {
+    return gamma >= 0.f ? 0 : (gamma == VDI_GAMMA_GIVEN ? 2 : (gamma == kGammaLearnedBracket ? 3 : 1));
 }
 
 // persistent grid of gen_count_kernel on the current device
@@ -782,6 +914,11 @@ vdi_status gen_count_grid(int& ctas) {
         if (s != VDI_OK) return s;
         if (per_sm_c > per_sm) per_sm = per_sm_c;
     }
+    s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, gen_count_batched_kernel, kCountThreads,
+                                                                 0),
+                   "occupancy");
+    if (s != VDI_OK) return s;
+    if (per_sm_c > per_sm) per_sm = per_sm_c;
     ctas = sms * (per_sm > 0 ? per_sm : 1);
     return VDI_OK;
 }
@@ -796,16 +933,15 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
                             void* cache, size_t cache_bytes, cudaStream_t st, const OwnerDev* own) {
     GenArgs a;  // copied into the launch's parameter space
     fill_args(a, bricks, k, lut, cam, dims, scale255, step, ref_len, n_s, out, status);
-    if (own) a.own = *own;
-    a.iters = iters;
-    a.gamma = gamma;
-    a.mode = gamma >= 0.f ? 0 : (gamma == VDI_GAMMA_GIVEN ? 2 : (gamma == kGammaLearnedBracket ? 3 : 1));
-    a.prec = 0;
+    if (own) a.r.own = *own;
+    a.r.iters = iters;
+    a.r.gamma = gamma;
+    a.r.mode = gamma_mode(gamma);
     a.counter = counter;
     int ctas = 0;
     vdi_status s = gen_count_grid(ctas);
     if (s != VDI_OK) return s;
-    const unsigned items = (unsigned)(a.tiles_x * a.tiles_y) * (unsigned)k;
+    const unsigned items = (unsigned)(a.r.tiles_x * a.r.tiles_y) * (unsigned)k;
     if (items == 0) return VDI_OK;
     if (cache && cache_bytes >= gen_cache_bytes(ctas)) {
         a.slots = ctas * kCountThreads;
@@ -813,10 +949,10 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
         a.cache = reinterpret_cast<float2*>(cache);
     }
     if ((unsigned)ctas > items) ctas = (int)items;
-    const bool learned = a.mode == 3;
-    if (a.own.map && learned) return set_error(VDI_ERR_UNSUPPORTED, "learned gamma with an ownership map");
-    if (a.own.map && census) gen_count_kernel<true, false, true><<<ctas, kCountThreads, 0, st>>>(a);
-    else if (a.own.map) gen_count_kernel<false, false, true><<<ctas, kCountThreads, 0, st>>>(a);
+    const bool learned = a.r.mode == 3;
+    if (a.r.own.map && learned) return set_error(VDI_ERR_UNSUPPORTED, "learned gamma with an ownership map");
+    if (a.r.own.map && census) gen_count_kernel<true, false, true><<<ctas, kCountThreads, 0, st>>>(a);
+    else if (a.r.own.map) gen_count_kernel<false, false, true><<<ctas, kCountThreads, 0, st>>>(a);
     else if (census && learned) gen_count_kernel<true, true><<<ctas, kCountThreads, 0, st>>>(a);
     else if (census) gen_count_kernel<true, false><<<ctas, kCountThreads, 0, st>>>(a);
     else if (learned) gen_count_kernel<false, true><<<ctas, kCountThreads, 0, st>>>(a);
@@ -829,18 +965,128 @@ vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, cons
                            unsigned int* status, cudaStream_t st, bool regular, const OwnerDev* own) {
     GenArgs a;
     fill_args(a, bricks, k, lut, cam, dims, scale255, step, ref_len, n_s, out, status);
-    if (own) a.own = *own;
-    a.iters = 0;
-    a.gamma = 0.f;
-    a.mode = 0;
-    a.prec = prec;
-    a.tiles_y = (cam.H + kEmitTileH - 1) / kEmitTileH;
-    dim3 grid((unsigned)(a.tiles_x * a.tiles_y), (unsigned)k);
+    if (own) a.r.own = *own;
+    a.r.prec = prec;
+    a.r.tiles_y = (cam.H + kEmitTileH - 1) / kEmitTileH;
+    dim3 grid((unsigned)(a.r.tiles_x * a.r.tiles_y), (unsigned)k);
     if (grid.x == 0) return VDI_OK;
-    if (a.own.map) gen_emit_kernel<true, false><<<grid, kEmitThreads, 0, st>>>(a);
+    if (a.r.own.map) gen_emit_kernel<true, false><<<grid, kEmitThreads, 0, st>>>(a);
     else if (regular) gen_emit_kernel<false, true><<<grid, kEmitThreads, 0, st>>>(a);
     else gen_emit_kernel<false, false><<<grid, kEmitThreads, 0, st>>>(a);
     return cuda_check(cudaGetLastError(), "gen_emit_kernel launch");
+}
+
+size_t gen_batch_table_bytes(const vdi_gen_request* reqs, int n) {
+    size_t pes = 0;
+    for (int q = 0; q < n; ++q) pes += (size_t)(reqs[q].k > 0 ? reqs[q].k : 0);
+    return align_up(sizeof(GenBatchHeader), 64) + align_up(sizeof(GenBatchReq) * (size_t)n, 64) +
+           align_up(sizeof(GenBatchPe) * pes, 64) + sizeof(ScanList) * pes;
+}
+
+// The caller has checked every request (vdi_gen_batch_table_pack in api.cu).
+vdi_status gen_batch_table_pack(const vdi_gen_request* reqs, int n, const vdi_params* params, void* host_table,
+                                size_t bytes) {
+    if (bytes < gen_batch_table_bytes(reqs, n))
+        return set_error(VDI_ERR_INVALID_ARG, "generation batch table: buffer too small");
+    char* base = static_cast<char*>(host_table);
+    GenBatchHeader* hd = reinterpret_cast<GenBatchHeader*>(base);
+    size_t pes = 0;
+    for (int q = 0; q < n; ++q) pes += (size_t)reqs[q].k;
+    hd->reqs_off = align_up(sizeof(GenBatchHeader), 64);
+    hd->pes_off = hd->reqs_off + align_up(sizeof(GenBatchReq) * (size_t)n, 64);
+    hd->lists_off = hd->pes_off + align_up(sizeof(GenBatchPe) * pes, 64);
+    GenBatchReq* rd = reinterpret_cast<GenBatchReq*>(base + hd->reqs_off);
+    GenBatchPe* pd = reinterpret_cast<GenBatchPe*>(base + hd->pes_off);
+    ScanList* ld = reinterpret_cast<ScanList*>(base + hd->lists_off);
+    uint64_t items = 0, eitems = 0, chunks = 0;
+    uint32_t pe = 0;
+    for (int q = 0; q < n; ++q) {
+        const vdi_gen_request& g = reqs[q];
+        GenBatchReq& r = rd[q];
+        const CamDev cam = make_cam(g.cam);
+        fill_req(r.r, g.k, g.tf_lut, cam, g.bricks[0].dims, (float)(255.0 * (double)g.bricks[0].value_scale),
+                 params->step, params->ref_len, g.n_s);
+        r.r.iters = params->bisect_iters;
+        r.r.gamma = g.gamma;
+        r.r.mode = gamma_mode(g.gamma);
+        r.r.prec = g.out[0].prec;
+        r.etiles_y = (cam.H + kEmitTileH - 1) / kEmitTileH;
+        r.item_begin = (uint32_t)items;
+        r.eitem_begin = (uint32_t)eitems;
+        r.pe_begin = pe;
+        items += (uint64_t)(r.r.tiles_x * r.r.tiles_y) * (uint64_t)g.k;
+        eitems += (uint64_t)(r.r.tiles_x * r.etiles_y) * (uint64_t)g.k;
+        const int npix = cam.W * cam.H;
+        for (int e = 0; e < g.k; ++e, ++pe) {
+            pd[pe].b = brick_dev(g.bricks[e]);
+            const vdi_compact& o = g.out[e];
+            pd[pe].out = CompactDev{o.counts, o.offsets, o.rgba, o.fb, o.gamma, o.capacity};
+            ld[pe].counts = o.counts;
+            ld[pe].offsets = o.offsets;
+            ld[pe].n = npix;
+            ld[pe].chunk_begin = (uint32_t)chunks;
+            chunks += scan_chunks(npix);
+        }
+    }
+    if (items > 0xFFFFFFFFull || eitems > 0x7FFFFFFFull || chunks > 0x7FFFFFFFull)
+        return set_error(VDI_ERR_INVALID_ARG, "generation batch table: too many work items");
+    hd->n = (uint32_t)n;
+    hd->total_items = (uint32_t)items;
+    hd->total_eitems = (uint32_t)eitems;
+    hd->total_pes = pe;
+    hd->total_chunks = (uint32_t)chunks;
+    hd->pad = 0;
+    return VDI_OK;
+}
+
+// [0, 256) status header, [256, 512) work counter, the prefix sum's partial
+// sums, then (optionally) the sample cache
+size_t gen_batched_workspace_bytes(const void* host_table) {
+    const GenBatchHeader* hd = static_cast<const GenBatchHeader*>(host_table);
+    int ctas = 0;
+    size_t cache = 0;
+    if (gen_count_grid(ctas) == VDI_OK) cache = gen_cache_bytes(ctas);
+    return kGenFixed + align_up((size_t)hd->total_chunks * sizeof(uint64_t), 256) + align_up(cache, 256);
+}
+
+vdi_status launch_gen_batched(const void* dev_table, const void* host_table, void* workspace, size_t ws_bytes,
+                              cudaStream_t st) {
+    const GenBatchHeader* hd = static_cast<const GenBatchHeader*>(host_table);
+    const size_t fixed = kGenFixed + align_up((size_t)hd->total_chunks * sizeof(uint64_t), 256);
+    if (ws_bytes < fixed)
+        return set_error(VDI_ERR_WORKSPACE, "vdi_generate_batched: workspace %zu < %zu bytes", ws_bytes, fixed);
+    char* ws = static_cast<char*>(workspace);
+    vdi_status s = cuda_check(cudaMemsetAsync(ws, 0, kGenFixed, st), "status clear");
+    if (s != VDI_OK || hd->n == 0 || hd->total_items == 0) return s;
+    const char* t = static_cast<const char*>(dev_table);
+    GenBatchArgs a;
+    a.reqs = reinterpret_cast<const GenBatchReq*>(t + hd->reqs_off);
+    a.pes = reinterpret_cast<const GenBatchPe*>(t + hd->pes_off);
+    a.n = (int)hd->n;
+    a.total_items = hd->total_items;
+    a.status = reinterpret_cast<unsigned int*>(ws);
+    a.counter = reinterpret_cast<unsigned int*>(ws + kWsHeader);
+    a.cache = nullptr;
+    a.cache_cap = 0;
+    a.slots = 0;
+    int ctas = 0;
+    s = gen_count_grid(ctas);
+    if (s != VDI_OK) return s;
+    if (ws_bytes >= fixed + gen_cache_bytes(ctas)) {
+        a.slots = ctas * kCountThreads;
+        a.cache_cap = kCacheCap;
+        a.cache = reinterpret_cast<float2*>(ws + fixed);
+    }
+    if ((unsigned)ctas > hd->total_items) ctas = (int)hd->total_items;
+    gen_count_batched_kernel<<<ctas, kCountThreads, 0, st>>>(a);
+    s = cuda_check(cudaGetLastError(), "gen_count_batched_kernel launch");
+    if (s != VDI_OK) return s;
+    s = launch_scan_batched(reinterpret_cast<const ScanList*>(t + hd->lists_off), (int)hd->total_pes,
+                            hd->total_chunks, reinterpret_cast<uint64_t*>(ws + kGenFixed), st);
+    if (s != VDI_OK) return s;
+    if (hd->total_eitems == 0) return VDI_OK;
+    gen_emit_batched_kernel<<<hd->total_eitems, kEmitThreads, 0, st>>>(a);
+    return cuda_check(cudaGetLastError(), "gen_emit_batched_kernel launch");
 }
 
 }  // namespace vdi

@@ -103,6 +103,8 @@ __global__ void scan_down_kernel(const __grid_constant__ ScanArgs a) {
     }
 }
 
+uint32_t scan_chunks(int n) { return (uint32_t)(((size_t)n + kScanChunk - 1) / kScanChunk); }
+
 size_t scan_workspace(int k, int n) {
     size_t chunks = ((size_t)n + kScanChunk - 1) / kScanChunk;
     return align_up((size_t)k * chunks * sizeof(uint64_t), 256);
@@ -123,6 +125,79 @@ vdi_status launch_scan(int k, int n, uint32_t* const* counts, uint64_t* const* o
     scan_partials_kernel<<<k, kScanThreads, 0, st>>>(a);
     scan_down_kernel<<<grid, kScanThreads, 0, st>>>(a);
     return cuda_check(cudaGetLastError(), "scan kernels launch");
+}
+
+// ---------------------------------------------------------------------------
+// Batched: the lists of many (request, PE) pairs, each of its own length, in
+// one set of three launches.  Chunk c belongs to the last list whose
+// chunk_begin is <= c; partial sums are indexed by global chunk.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int list_of_chunk(const ScanList* L, int nl, uint32_t chunk) {
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&L[mid].chunk_begin) <= chunk) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void scan_reduce_batched_kernel(const ScanList* __restrict__ L, int nl, uint64_t* __restrict__ partial) {
+    const uint32_t chunk = blockIdx.x;
+    const ScanList& l = L[list_of_chunk(L, nl, chunk)];
+    const size_t base = (size_t)(chunk - l.chunk_begin) * kScanChunk + (size_t)threadIdx.x * kScanItems;
+    uint32_t it[kScanItems];
+    load_items(l.counts, l.n, base, it);
+    uint64_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) s += it[q];
+    uint64_t total;
+    block_exclusive_scan(s, total);
+    if (threadIdx.x == 0) partial[chunk] = total;
+}
+
+__global__ void scan_partials_batched_kernel(const ScanList* __restrict__ L, uint64_t* __restrict__ partial) {
+    const ScanList& l = L[blockIdx.x];
+    const int chunks = (l.n + kScanChunk - 1) / kScanChunk;
+    uint64_t* p = partial + l.chunk_begin;
+    uint64_t carry = 0;
+    for (int start = 0; start < chunks; start += kScanThreads) {
+        const int i = start + threadIdx.x;
+        const uint64_t v = i < chunks ? p[i] : 0;
+        uint64_t total;
+        const uint64_t ex = block_exclusive_scan(v, total);
+        if (i < chunks) p[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) l.offsets[l.n] = carry;
+}
+
+__global__ void scan_down_batched_kernel(const ScanList* __restrict__ L, int nl, const uint64_t* __restrict__ partial) {
+    const uint32_t chunk = blockIdx.x;
+    const ScanList& l = L[list_of_chunk(L, nl, chunk)];
+    const size_t base = (size_t)(chunk - l.chunk_begin) * kScanChunk + (size_t)threadIdx.x * kScanItems;
+    uint32_t it[kScanItems];
+    load_items(l.counts, l.n, base, it);
+    uint64_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) s += it[q];
+    uint64_t total;
+    uint64_t ex = block_exclusive_scan(s, total) + partial[chunk];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        const size_t i = base + q;
+        if (i < (size_t)l.n) l.offsets[i] = ex;
+        ex += it[q];
+    }
+}
+
+vdi_status launch_scan_batched(const ScanList* dev_lists, int nlists, uint32_t total_chunks, uint64_t* partial,
+                               cudaStream_t st) {
+    if (nlists <= 0 || total_chunks == 0) return VDI_OK;
+    scan_reduce_batched_kernel<<<total_chunks, kScanThreads, 0, st>>>(dev_lists, nlists, partial);
+    scan_partials_batched_kernel<<<nlists, kScanThreads, 0, st>>>(dev_lists, partial);
+    scan_down_batched_kernel<<<total_chunks, kScanThreads, 0, st>>>(dev_lists, nlists, partial);
+    return cuda_check(cudaGetLastError(), "batched scan kernels launch");
 }
 
 }  // namespace vdi

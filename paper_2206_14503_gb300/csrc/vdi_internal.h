@@ -56,8 +56,18 @@ constexpr size_t kWsHeader = 256;
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// One list of a batched prefix sum: counts[0..n) -> offsets[0..n], its chunks
+// of the partial sums starting at chunk_begin.
+struct ScanList {
+    const uint32_t* counts;
+    uint64_t* offsets;
+    int n;
+    uint32_t chunk_begin;
+};
+
 // host helpers (api.cu)
 CamDev make_cam(const vdi_camera& c);
+BrickDev brick_dev(const vdi_brick& b);
 vdi_status set_error(vdi_status s, const char* fmt, ...);
 vdi_status cuda_check(cudaError_t e, const char* what);
 
@@ -82,6 +92,16 @@ vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, cons
                            const OwnerDev* own = nullptr);
 size_t scan_workspace(int k, int n);
 vdi_status launch_scan(int k, int n, uint32_t* const* counts, uint64_t* const* offsets, void* ws, cudaStream_t st);
+uint32_t scan_chunks(int n);
+vdi_status launch_scan_batched(const ScanList* dev_lists, int nlists, uint32_t total_chunks, uint64_t* partial,
+                               cudaStream_t st);
+// batched generation (generate.cu): host table of uneven requests, its workspace, the launches
+size_t gen_batch_table_bytes(const vdi_gen_request* reqs, int n);
+vdi_status gen_batch_table_pack(const vdi_gen_request* reqs, int n, const vdi_params* params, void* host_table,
+                                size_t bytes);
+size_t gen_batched_workspace_bytes(const void* host_table);
+vdi_status launch_gen_batched(const void* dev_table, const void* host_table, void* workspace, size_t ws_bytes,
+                              cudaStream_t st);
 
 vdi_status launch_composite(const vdi_compact* pe, int k, int w, int h, const vdi_regular* out, int iters,
                             int schedule, unsigned int* status, void* workspace, size_t ws_bytes, cudaStream_t st,

@@ -173,3 +173,23 @@ def requests(n, seed=SEED_REQUESTS, w_range=(256, 1920), h_range=(256, 1080), k_
             vals.append(lo + hash4(seed, 0x72657173, r, i) % (hi - lo + 1))
         out.append(tuple(int(v) for v in vals))
     return out
+
+
+# grids of K = 1, 2, 4, 8, 16 near-equal bricks
+_GEN_GRIDS = ((1, 1, 1), (1, 1, 2), (1, 2, 2), (2, 2, 2), (4, 2, 2))
+
+
+def gen_requests(n, seed=SEED_REQUESTS, sides=(128, 192, 256, 384), w_range=(256, 1920), h_range=(256, 1080),
+                 n_s_range=(8, 64)):
+    """Seeded table of uneven generation requests: list of (side, grid, w, h, n_s), the volume a side^3
+    uint16 blob volume, K = product of grid in {1, 2, 4, 8, 16}, each field uniform on its set or range."""
+    out = []
+    for r in range(n):
+        h = [hash4(seed, 0x67656E72, r, i) for i in range(5)]
+        side = sides[h[0] % len(sides)]
+        grid = _GEN_GRIDS[h[1] % len(_GEN_GRIDS)]
+        w = w_range[0] + h[2] % (w_range[1] - w_range[0] + 1)
+        hh = h_range[0] + h[3] % (h_range[1] - h_range[0] + 1)
+        n_s = n_s_range[0] + h[4] % (n_s_range[1] - n_s_range[0] + 1)
+        out.append((int(side), grid, int(w), int(hh), int(n_s)))
+    return out

@@ -228,7 +228,7 @@ def test_learned_generation_is_exact_and_saves_work():
     lut_d = to_dev(lut)
     census = vdi.make_params(flags=vdi.VDI_FLAG_CENSUS)
 
-    def run(vol, cam, learned, offset=0.0):
+    def run(vol, cam, learned, offset=0.0, flags=0):
         npix = cam.width * cam.height
         br = _bricks(vdi, vol, dims, boxes)
         c = vdi.make_camera(cam)
@@ -236,8 +236,9 @@ def test_learned_generation_is_exact_and_saves_work():
         gws = vdi.Workspace(vdi.vdi_generate_workspace(k, cam.width, cam.height))
         if learned:
             ws = vdi.Workspace(vdi.vdi_learned_workspace(k, cam.width, cam.height))
+            p = vdi.make_params(flags=vdi.VDI_FLAG_CENSUS | flags)
             vdi.check(vdi.vdi_choose_gamma_learned(br.bricks, lut_d.data_ptr(), c, n_s, model.data_ptr(), offset,
-                                                   [o.struct() for o in outs], census, ws.ptr, ws.nbytes), "learned")
+                                                   [o.struct() for o in outs], p, ws.ptr, ws.nbytes), "learned")
             extra = ws.nbytes - vdi.vdi_generate_workspace(k, cam.width, cam.height)
             ctr = vdi.vdi_workspace_counters(ws.ptr + extra)
         else:
@@ -281,9 +282,17 @@ def test_learned_generation_is_exact_and_saves_work():
     # the composited VDI still renders the volume exactly from the generating view (sec. 2.3)
     g = composite(ll, cam.width, cam.height, n_s)
     ref = oracle.dvr(vol, lut, cam, 0.5, 1.0)
-    assert np.abs(g["image"] - ref).max() <= 1e-4
-    # gain: fewer rays need the bisection search (the rest take the predicted gamma after one march)
+    assert np.abs(g["image"] - ref).max() <= 1e-5
+    # gain: fewer rays need the bisection search, and less work is done -- fewer marches over a ray's
+    # samples (volume or cached) and fewer state-machine steps than the search (census counters [2], [1])
     assert cl[4] < cs[4], (cl, cs)
+    assert cl[2] < cs[2] and cl[1] < cs[1], (cl, cs)
     fell = cl[4] / max(cl[3], 1)
-    print(f"learned: offset {offset}, count error {err:.4f}, fallback {fell:.3f}, steps {cl[1]} vs search {cs[1]}, "
-          f"volume samples {cl[0]} vs {cs[0]}")
+    print(f"learned: offset {offset}, count error {err:.4f}, fallback {fell:.3f}, marches {cl[2]} vs search {cs[2]}, "
+          f"steps {cl[1]} vs {cs[1]}, volume samples {cl[0]} vs {cs[0]}")
+    # the single-pass form (the prediction as it is, the search for rays over the budget): counts never
+    # exceed the budget, and where the prediction is within it no search runs at all
+    l1, c1 = run(vol, cam, True, offset, vdi.VDI_FLAG_LEARNED_SINGLE_PASS)
+    err1, cmax1 = count_error(ls, l1)
+    assert cmax1 <= n_s and c1[4] < cs[4], (c1, cs)
+    print(f"learned single pass: count error {err1:.4f}, searched rays {c1[4]} vs {cs[4]}, marches {c1[2]}")
