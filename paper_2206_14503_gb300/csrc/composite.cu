@@ -1429,35 +1429,46 @@ __global__ void __launch_bounds__(128) composite_overflow_kernel(const __grid_co
     if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
 }
 
+// storage of the pieces of the pixels the lane schedule searches
+struct PiecePool {
+    float4* A;  // (P.rgb, a)
+    float2* B;  // (b, log2(1 - a))
+    uint32_t cap;
+};
+
+// list entry of a pixel for the flat search: pixel (top bit: composite it by the direct sweep), first
+// piece in the pool, number of pieces, front of the first piece
+struct FlatEntry {
+    uint32_t p, base, n;
+    float f0;
+};
+
 // ---------------------------------------------------------------------------
-// Lane-staged path (short lists: K <= kLaneKMax).  Two launches of one
-// kernel, each warp staging the records of 32 pixels in its shared-memory
-// slab with asynchronous copies (cp.async: every copy of a round is in
-// flight before the warp waits once) and sweeping each pixel there, a lane
-// per pixel, so that no march touches global memory.
+// Lane-staged path (short lists: K <= kLaneKMax).  Two passes.
 //
-// Batch pass (LIST = false): a warp takes 32 consecutive pixels and reads
-// their counts and offsets (coalesced over the pixels).  The records go to the
-// slab PE by PE: the spans of consecutive pixels of one PE are consecutive in
-// the PE's record array (the layout generation writes), so a warp's copies
-// are coalesced 16- and 8-byte runs; other layouts find each record's pixel
-// by a binary search over the lanes.  A lane sweeps its pixel's K lists into
-// pieces and counts the non-transparent ones: at most n_s means gamma = 0
-// (sec. 2.4: the count at gamma = 0 is within the budget), and a second sweep
-// emits the pixel's records straight away.  Pixels that need the gamma
-// search, or whose records do not fit a slab, are appended to a list.
+// Batch pass (composite_lane_kernel): a warp takes 32 consecutive pixels,
+// reads their counts and offsets (coalesced over the pixels) and copies their
+// records into its shared-memory slab with asynchronous copies (cp.async:
+// every copy of a round is in flight before the warp waits once), PE by PE:
+// the spans of consecutive pixels of one PE are consecutive in the PE's record
+// array (the layout generation writes), so the copies are coalesced 16- and
+// 8-byte runs; other layouts find each record's pixel by a binary search over
+// the lanes.  A lane sweeps its pixel's K lists in the slab into pieces and
+// counts the non-transparent ones: at most n_s means gamma = 0 (sec. 2.4: the
+// count at gamma = 0 is within the budget), and a second sweep emits the
+// pixel's records straight away.  A pixel that needs the gamma search gets
+// its pieces written, once, to a pool in the workspace and is listed.
 //
-// List pass (LIST = true): a warp takes 32 listed pixels, stages their records
-// in a larger slab and runs the search and the emission of each, a lane per
-// pixel, over the slab.  Every lane of a list warp searches, so none idles
-// behind a searching neighbour as in the direct schedules.  A listed pixel
-// whose records exceed the list slab is composited by the direct sweep.
-// The pieces are those of every other schedule, bit for bit, so is the result.
+// Search pass (composite_flat_kernel, below): the listed pixels' searches and
+// emissions over their pooled pieces, a lane per pixel, lanes taking new
+// pixels as they finish.  Pixels whose records exceed the slab, or whose
+// pieces do not fit the pool, are listed for the direct sweep
+// (composite_marked_kernel).  The pieces are those of every other schedule,
+// bit for bit, so is the result.
 // ---------------------------------------------------------------------------
 constexpr int kLaneKMax = 8;        // PEs the lane path handles (heads in registers)
 constexpr int kLaneWarps = 4;       // warps per CTA
-constexpr int kLaneRCap = 480;      // records per warp slab, batch pass
-constexpr int kLaneListRCap = 1024; // records per warp slab, list pass
+constexpr int kLaneRCap = 480;      // records per warp slab
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
@@ -1630,16 +1641,125 @@ __device__ __forceinline__ int sweep_slab(const SLAB& S, int k, const uint32_t s
     return npieces;
 }
 
-// One pixel's sweeps over the slab, for composite_search_emit.
+// One pixel's sweeps over the slab.  When the pixel's K lists are disjoint
+// in depth -- each list sorted with
+// non-overlapping records, and the PEs' depth ranges not overlapping (every
+// convex decomposition gives such lists: a ray crosses each box in one
+// stretch) -- no interval is covered by two records, so the pieces are the
+// records themselves, in the order of the PEs' ranges, with a transparent gap
+// piece wherever one record ends before the next begins: exactly the pieces
+// the sweep would cut, without comparing K list heads per piece.  Other
+// pixels take the sweep.
 template <class SLAB>
 struct SlabSweeper {
     static constexpr bool kSelectSteps = false;  // counting steps with branches (see CountVisitorQ)
     const SLAB* S;
     int k;
     uint32_t st[kLaneKMax], cnt[kLaneKMax];
+    bool disjoint;
+    uint32_t order;  // PEs by the front of their first record, 4 bits each
+
+    __device__ __forceinline__ void prepare() {
+        float lo[kLaneKMax], hi[kLaneKMax];
+        bool ok = true;
+        int nz = 0;
+#pragma unroll
+        for (int e = 0; e < kLaneKMax; ++e) {
+            lo[e] = kNoEvent;
+            hi[e] = -kNoEvent;
+            if (e < k) {
+                float prev = -kNoEvent;
+                for (uint32_t r = st[e]; r < st[e] + cnt[e]; ++r) {
+                    const float2 fb = S->bounds(r);
+                    if (!(fb.y > fb.x)) continue;
+                    ok = ok && fb.x >= prev;
+                    prev = fb.y;
+                    lo[e] = fminf(lo[e], fb.x);
+                    hi[e] = fb.y;
+                }
+                nz += lo[e] < kNoEvent;
+            }
+        }
+        // insertion sort of the PEs by their first front (ties by index, as the sweep's heads)
+        uint32_t ord = 0;
+        int n = 0;
+#pragma unroll
+        for (int e = 0; e < kLaneKMax; ++e) {
+            if (e < k && lo[e] < kNoEvent) {
+                int pos = n;
+                while (pos > 0) {
+                    const int q = (int)((ord >> (4 * (pos - 1))) & 15u);
+                    float lq = lo[0];
+#pragma unroll
+                    for (int w = 1; w < kLaneKMax; ++w)
+                        if (w == q) lq = lo[w];
+                    if (!(lq > lo[e])) break;
+                    const uint32_t sh = 4u * (uint32_t)pos;
+                    ord = (ord & ~(15u << sh)) | ((uint32_t)q << sh);
+                    --pos;
+                }
+                const uint32_t sh = 4u * (uint32_t)pos;
+                ord = (ord & ~(15u << sh)) | ((uint32_t)e << sh);
+                ++n;
+            }
+        }
+        // consecutive ranges must not overlap
+        float end = -kNoEvent;
+        for (int i = 0; i < n; ++i) {
+            const int e = (int)((ord >> (4 * i)) & 15u);
+            float le = lo[0], he = hi[0];
+#pragma unroll
+            for (int w = 1; w < kLaneKMax; ++w)
+                if (w == e) {
+                    le = lo[w];
+                    he = hi[w];
+                }
+            ok = ok && le >= end;
+            end = he;
+        }
+        disjoint = ok;
+        order = ord | ((uint32_t)n << 28);
+    }
+
     template <typename V>
     __device__ __forceinline__ int run(V& v) const {
-        return sweep_slab(*S, k, st, cnt, v);
+        if (!disjoint) return sweep_slab(*S, k, st, cnt, v);
+        const int n = (int)(order >> 28);
+        int np = 0;
+        float t = 0.f;
+        bool first = true;
+        for (int i = 0; i < n; ++i) {
+            const int e = (int)((order >> (4 * i)) & 15u);
+            uint32_t s0 = st[0], c0 = cnt[0];
+#pragma unroll
+            for (int w = 1; w < kLaneKMax; ++w)
+                if (w == e) {
+                    s0 = st[w];
+                    c0 = cnt[w];
+                }
+            for (uint32_t r = s0; r < s0 + c0; ++r) {
+                const float2 fb = S->bounds(r);
+                if (!(fb.y > fb.x)) continue;
+                Piece x;
+                if (!first && fb.x > t) {
+                    x.f = t;
+                    x.b = fb.x;
+                    x.P[0] = x.P[1] = x.P[2] = 0.f;
+                    x.a = 0.f;
+                    x.lgT = 0.f;
+                    v(x);
+                    ++np;
+                }
+                MixSums m;
+                sums_reset(m);
+                piece_from(m, true, S->rec(r), fb.x, fb.y, x);
+                v(x);
+                ++np;
+                t = fb.y;
+                first = false;
+            }
+        }
+        return np;
     }
 };
 
@@ -1663,13 +1783,26 @@ __device__ __forceinline__ void finish_pixel(const OutDev& out, uint32_t p, int 
     if (out.gamma) out.gamma[p] = gamma;
 }
 
+// list: [0] entries, [1] next entry for the search pass, [2] pieces taken from the pool, [3] unused,
+// then FlatEntry entries from word 4
 struct LaneArgs {
-    unsigned int* counter;  // [0]: batch counter of the batch pass, [1]: item counter of the list pass
-    uint32_t* list;         // [0]: count, [2..]: pixels for the list pass
+    unsigned int* counter;  // batch counter of the batch pass
+    uint32_t* list;
+    PiecePool pool;
 };
 
-// appends the lanes with `flag` set to the list (one atomic per warp)
-__device__ __forceinline__ void list_push(uint32_t* list, bool flag, uint32_t p) {
+// Pieces of a pixel into its run of the pool.
+struct PoolWriter {
+    float4* A;
+    float2* B;
+    __device__ __forceinline__ void operator()(const Piece& x) {
+        *A++ = make_float4(x.P[0], x.P[1], x.P[2], x.a);
+        *B++ = make_float2(x.b, x.lgT);
+    }
+};
+
+// appends an entry for each lane with `flag` set (one atomic per warp)
+__device__ __forceinline__ void list_push(uint32_t* list, bool flag, const FlatEntry& en) {
     const unsigned m = __ballot_sync(0xffffffffu, flag);
     if (!m) return;
     const int lane = threadIdx.x & 31;
@@ -1677,7 +1810,7 @@ __device__ __forceinline__ void list_push(uint32_t* list, bool flag, uint32_t p)
     uint32_t base = 0;
     if (lane == leader) base = atomicAdd(list, (uint32_t)__popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (flag) list[2 + base + __popc(m & ((1u << lane) - 1u))] = p;
+    if (flag) reinterpret_cast<FlatEntry*>(list + 4)[base + __popc(m & ((1u << lane) - 1u))] = en;
 }
 
 // Copies the records of the lanes with `take` set into the slab, PE-major,
@@ -1729,14 +1862,15 @@ __device__ __forceinline__ void slab_stage(const PeIn* pe, int k, SLAB& S, bool 
     }
 }
 
-// the listed pixels the list pass marked (records beyond its slab), by the direct sweep
+// the listed pixels marked for the direct sweep (records beyond a slab, or pieces beyond the pool)
 template <int PREC, bool CENSUS>
 __global__ void __launch_bounds__(128) composite_marked_kernel(const __grid_constant__ CompArgs a,
                                                                const uint32_t* __restrict__ list) {
     const uint32_t n = *list;
+    const FlatEntry* entries = reinterpret_cast<const FlatEntry*>(list + 4);
     CompCensus cs;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t v = list[2 + i];
+        const uint32_t v = entries[i].p;
         if (v & 0x80000000u)
             composite_pixel<kLaneKMax, 16, 2, PREC, CENSUS>(a.pe, a.k, a.out, a.iters, a.status, v & 0x7FFFFFFFu,
                                                             nullptr, &cs);
@@ -1749,32 +1883,23 @@ constexpr size_t lane_smem_bytes() {
     return kLaneWarps * sizeof(LaneSlab<PREC, CAP>);
 }
 
-template <int PREC, bool CENSUS, bool LIST>
+template <int PREC, bool CENSUS>
 __global__ void __launch_bounds__(kLaneWarps * 32) composite_lane_kernel(const __grid_constant__ CompArgs a,
                                                                         const __grid_constant__ LaneArgs la) {
-    constexpr int CAP = LIST ? kLaneListRCap : kLaneRCap;
-    using Slab = LaneSlab<PREC, CAP>;
+    using Slab = LaneSlab<PREC, kLaneRCap>;
     extern __shared__ __align__(16) unsigned char lane_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Slab& S = reinterpret_cast<Slab*>(lane_smem)[warp];
     const int k = a.k;
-    const uint32_t nitems = LIST ? (*la.list + 31u) / 32u : ((uint32_t)a.npix + 31u) / 32u;
+    const uint32_t nitems = ((uint32_t)a.npix + 31u) / 32u;
     CompCensus cs;
     while (true) {
         uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(la.counter + (LIST ? 1 : 0), 1u);
+        if (lane == 0) item = atomicAdd(la.counter, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems) break;
-        bool valid;
-        uint32_t p;
-        if constexpr (LIST) {
-            const uint32_t i = item * 32u + (uint32_t)lane;
-            valid = i < *la.list;
-            p = valid ? la.list[2 + i] : 0u;
-        } else {
-            p = item * 32u + (uint32_t)lane;
-            valid = p < (uint32_t)a.npix;
-        }
+        const uint32_t p = item * 32u + (uint32_t)lane;
+        const bool valid = p < (uint32_t)a.npix;
         uint32_t cnt[kLaneKMax];
         uint64_t off[kLaneKMax];
         uint32_t tot = 0;
@@ -1788,78 +1913,344 @@ __global__ void __launch_bounds__(kLaneWarps * 32) composite_lane_kernel(const _
                 tot += cnt[e];
             }
         }
-        const bool big = valid && tot > (uint32_t)CAP;
-        if constexpr (LIST) {
-            if (big) la.list[2 + item * 32u + (uint32_t)lane] = p | 0x80000000u;  // for composite_marked_kernel
-        } else {
-            list_push(la.list, big, p);
-        }
+        // records beyond the slab: the direct sweep composites the pixel
+        const bool big = valid && tot > (uint32_t)kLaneRCap;
+        list_push(la.list, big, FlatEntry{p | 0x80000000u, 0u, 0u, 0.f});
         bool pending = valid && !big;
         while (__any_sync(0xffffffffu, pending)) {
             // this round: the pending lanes, in order, whose records fit the slab together
             const uint32_t incl = warp_incl_scan_u32(pending ? tot : 0u);
-            const bool take = pending && incl <= (uint32_t)CAP;
+            const bool take = pending && incl <= (uint32_t)kLaneRCap;
             pending = pending && !take;
             uint32_t st[kLaneKMax];
             slab_stage(a.pe, k, S, take, cnt, off, st);
             cp_async_wait_all();
             __syncwarp();
-            bool search = false;
-            if (take) {
-                SlabSweeper<Slab> sw;
-                sw.S = &S;
-                sw.k = k;
+            SlabSweeper<Slab> sw;
+            sw.S = &S;
+            sw.k = k;
 #pragma unroll
-                for (int e = 0; e < kLaneKMax; ++e) {
-                    sw.st[e] = st[e];
-                    sw.cnt[e] = cnt[e];
-                }
-                if (CENSUS) {
-                    cs.pixels += 1;
-                    cs.records += tot;
-                }
-                if constexpr (LIST) {
-                    composite_search_emit<2, CENSUS>(sw, a.out, a.iters, a.status, p, &cs);
-                } else {
-                    NtVisitor nv{0};
-                    const int np = sw.run(nv);
+            for (int e = 0; e < kLaneKMax; ++e) {
+                sw.st[e] = st[e];
+                sw.cnt[e] = take ? cnt[e] : 0u;
+            }
+            sw.prepare();
+            bool search = false;
+            uint32_t np = 0;
+            if (take) {
+                NtVisitor nv{0};
+                np = (uint32_t)sw.run(nv);
+                if (nv.nt <= a.out.n_s) {
+                    // gamma = 0: every non-transparent piece is a supersegment
+                    EmitVisitor em;
+                    em.s.cnt = 0;
+                    em.s.open = false;
+                    em.g2 = 0.f;
+                    em.cap = a.out.n_s;
+                    em.bt = 0.f;
+                    em.written = 0;
+                    em.base = (size_t)p * a.out.n_s;
+                    em.out = &a.out;
+                    sw.run(em);
+                    if (em.s.open && em.written < a.out.n_s) em.store(em.s.fS, em.bt, em.s.P, em.s.A, em.s.L2);
+                    if (em.written != nv.nt) atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CUDA);
+                    finish_pixel(a.out, p, em.written, 0.f);
                     if (CENSUS) {
-                        cs.sweeps += 1;
-                        cs.pieces += (unsigned long long)np;
+                        cs.pixels += 1;
+                        cs.records += tot;
+                        cs.sweeps += 2;
+                        cs.pieces += 2ull * np;
                     }
-                    if (nv.nt <= a.out.n_s) {
-                        // gamma = 0: every non-transparent piece is a supersegment
-                        EmitVisitor em;
-                        em.s.cnt = 0;
-                        em.s.open = false;
-                        em.g2 = 0.f;
-                        em.cap = a.out.n_s;
-                        em.bt = 0.f;
-                        em.written = 0;
-                        em.base = (size_t)p * a.out.n_s;
-                        em.out = &a.out;
-                        sw.run(em);
-                        if (em.s.open && em.written < a.out.n_s)
-                            em.store(em.s.fS, em.bt, em.s.P, em.s.A, em.s.L2);
-                        if (em.written != nv.nt) atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CUDA);
-                        finish_pixel(a.out, p, em.written, 0.f);
-                        if (CENSUS) {
-                            cs.sweeps += 1;
-                            cs.pieces += (unsigned long long)np;
-                        }
-                    } else {
-                        // searched in the list pass, which counts it again
-                        search = true;
-                        if (CENSUS) {
-                            cs.pixels -= 1;
-                            cs.records -= tot;
-                        }
-                    }
+                } else {
+                    search = true;  // counted by the search pass
                 }
             }
-            if constexpr (!LIST) list_push(la.list, search, p);
+            // the searching lanes' pieces go to the pool, one run per pixel (one atomic per warp)
+            if (__any_sync(0xffffffffu, search)) {
+                const uint32_t mine = search ? np : 0u;
+                const uint32_t inc = warp_incl_scan_u32(mine);
+                uint32_t base = 0;
+                if (lane == 31) base = atomicAdd(la.list + 2, inc);
+                base = __shfl_sync(0xffffffffu, base, 31) + inc - mine;
+                const bool fits = search && (uint64_t)base + mine <= (uint64_t)la.pool.cap;
+                float f0 = 0.f;
+                if (fits) {
+                    PoolWriter pw{la.pool.A + base, la.pool.B + base};
+                    struct First {
+                        PoolWriter* w;
+                        float* f0;
+                        bool seen;
+                        __device__ __forceinline__ void operator()(const Piece& x) {
+                            if (!seen) {
+                                *f0 = x.f;
+                                seen = true;
+                            }
+                            (*w)(x);
+                        }
+                    } fw{&pw, &f0, false};
+                    sw.run(fw);
+                }
+                list_push(la.list, search, FlatEntry{fits ? p : (p | 0x80000000u), base, mine, f0});
+            }
             __syncwarp();
         }
+    }
+    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
+}
+
+// ---------------------------------------------------------------------------
+// Flat search: composite_search_emit<2> for one pixel per lane, written as one
+// loop whose body handles one piece of the lane's current march.  Lanes at
+// different marches, or at different pixels, execute the same loop body, so
+// a warp's lanes stay busy however many marches their pixels need; a lane
+// that finishes its pixel takes the next one from the list.  The decisions,
+// the table of decision intervals and the replay of sequential bisection are
+// those of composite_search_emit, step for step, so the output is the same,
+// bit for bit.  The pieces come from a pool in the workspace (written by the
+// batch pass), one contiguous run per pixel.
+// ---------------------------------------------------------------------------
+enum : int { kFlatIdle = 0, kFlatFirst = 1, kFlatSearch = 2, kFlatEmit = 3 };
+
+struct FlatLane {
+    uint32_t p, base, n, j;
+    float f, f0;
+    int phase;
+    float g2[3];
+    CompCountQ st[3];  // a counting march's candidates; st[0] also holds the emission's supersegment
+    int nt;
+    float bt;  // emission: back of the last non-transparent piece of the open supersegment
+    int written;
+    float lo, hi, gamma;
+    int cnt_hi, it, count;
+};
+
+__device__ __forceinline__ void flat_start_count(FlatLane& L, float lo, float hi) {
+    float g[3];
+    tree_candidates<2>(lo, hi, g);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        L.g2[q] = __fmul_rn(g[q], g[q]);
+        L.st[q].cnt = 0;
+        L.st[q].open = false;
+        L.st[q].qlo = -1.f;
+        L.st[q].qhi = 3.0e38f;
+    }
+    L.nt = 0;
+    L.j = 0;
+    L.f = L.f0;
+}
+
+__device__ __forceinline__ void flat_start_emit(FlatLane& L) {
+    L.phase = kFlatEmit;
+    L.g2[0] = __fmul_rn(L.gamma, L.gamma);
+    L.st[0].cnt = 0;
+    L.st[0].open = false;
+    L.bt = 0.f;
+    L.written = 0;
+    L.j = 0;
+    L.f = L.f0;
+}
+
+__device__ __forceinline__ void flat_store(const OutDev& out, uint32_t p, int written, float f, float b,
+                                           const float P[3], float A, float L2) {
+    const size_t idx = (size_t)p * out.n_s + written;
+    if (out.prec == VDI_PREC_F32) {
+        reinterpret_cast<float4*>(out.rgba)[idx] = make_float4(P[0], P[1], P[2], A);
+        out.fb[idx] = make_float2(f, b);
+    } else {
+        reinterpret_cast<uint4*>(out.rgba)[idx] = f16_pack(f, b, P[0], P[1], P[2], L2);
+    }
+}
+
+// the emission step of EmitVisitor on the lane's supersegment st[0]
+__device__ __forceinline__ void flat_emit_step(FlatLane& L, const Piece& x, const OutDev& out) {
+    CompCountQ& s = L.st[0];
+    const int cap = out.n_s;
+    if (!s.open) {
+        if (x.a > 0.f) {
+            s.P[0] = x.P[0]; s.P[1] = x.P[1]; s.P[2] = x.P[2];
+            s.A = x.a; s.L2 = x.lgT; s.fS = x.f; s.bS = x.b; s.open = true;
+            L.bt = x.b;
+            ++s.cnt;
+        }
+        return;
+    }
+    const float lx = __fsub_rn(x.b, x.f), lS = __fsub_rn(s.bS, s.fS);
+    const float r = (lx > 0.f && lS > 0.f) ? __fmul_rn(lx, rcp_approx(lS)) : 1.f;
+    if (s.cnt < cap && criterion(s.P, s.A, s.L2, r, x.P, L.g2[0])) {
+        if (L.written < cap) {
+            flat_store(out, L.p, L.written, s.fS, L.bt, s.P, s.A, s.L2);
+            ++L.written;
+        }
+        if (x.a > 0.f) {
+            s.P[0] = x.P[0]; s.P[1] = x.P[1]; s.P[2] = x.P[2];
+            s.A = x.a; s.L2 = x.lgT; s.fS = x.f; s.bS = x.b;
+            L.bt = x.b;
+            ++s.cnt;
+        } else {
+            s.open = false;
+        }
+    } else {
+        absorb(s.P, s.A, s.L2, x.P, x.a, x.lgT);
+        s.bS = x.b;
+        if (x.a > 0.f) L.bt = x.b;
+    }
+}
+
+// Continues the bisection replay from level L.it: levels whose midpoint a recorded decision interval
+// answers need no march; returns with the next march started, or with the emission started.
+template <bool CENSUS>
+__device__ __forceinline__ void flat_advance(FlatLane& L, CountTable& t, int iters, int n_s, CompCensus& cs) {
+    while (L.it < iters) {
+        const float mid = 0.5f * (L.lo + L.hi);
+        const int c = t.lookup(__fmul_rn(mid, mid));
+        if (c < 0) {
+            L.phase = kFlatSearch;
+            flat_start_count(L, L.lo, L.hi);
+            return;
+        }
+        if (CENSUS) cs.table_hits += 1;
+        ++L.it;
+        if (c <= n_s) {
+            L.hi = mid;
+            L.cnt_hi = c;
+            if (c == n_s) break;
+        } else {
+            L.lo = mid;
+        }
+    }
+    L.gamma = L.hi;
+    L.count = L.cnt_hi;
+    flat_start_emit(L);
+}
+
+template <bool CENSUS>
+__device__ __forceinline__ void flat_end_march(FlatLane& L, CountTable& t, const OutDev& out, int iters,
+                                               unsigned int* status, CompCensus& cs) {
+    if (CENSUS) {
+        cs.sweeps += 1;
+        cs.pieces += L.n;
+        if (L.phase != kFlatEmit) cs.cand_steps += (unsigned long long)L.n * 3;
+    }
+    if (L.phase == kFlatFirst) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) t.add(L.g2[q], L.st[q].qlo, L.st[q].qhi, L.st[q].cnt);
+        if (L.nt <= out.n_s) {
+            L.gamma = 0.f;
+            L.count = L.nt;
+            flat_start_emit(L);
+        } else {
+            if (CENSUS) cs.searched += 1;
+            L.lo = 0.f;
+            L.hi = 2.f;
+            L.cnt_hi = 1;  // the distance never reaches 2: one supersegment
+            L.it = 0;
+            flat_advance<CENSUS>(L, t, iters, out.n_s, cs);
+        }
+    } else if (L.phase == kFlatSearch) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) t.add(L.g2[q], L.st[q].qlo, L.st[q].qhi, L.st[q].cnt);
+        const int c = L.st[0].cnt;
+        const float mid = 0.5f * (L.lo + L.hi);
+        ++L.it;
+        if (c <= out.n_s) {
+            L.hi = mid;
+            L.cnt_hi = c;
+            if (c == out.n_s) {
+                L.it = iters;  // done
+            }
+        } else {
+            L.lo = mid;
+        }
+        flat_advance<CENSUS>(L, t, iters, out.n_s, cs);
+    } else {
+        // the emission: the open supersegment, the zero tail, count and gamma
+        CompCountQ& s = L.st[0];
+        if (s.open && L.written < out.n_s) {
+            flat_store(out, L.p, L.written, s.fS, L.bt, s.P, s.A, s.L2);
+            ++L.written;
+        }
+        finish_pixel(out, L.p, L.written, L.gamma);
+        if (L.written != L.count) atomicCAS(status, 0u, (unsigned)VDI_ERR_CUDA);
+        L.phase = kFlatIdle;
+    }
+}
+
+// The flat search over the listed pixels (list: [count, next-entry counter, pad, pad] then FlatEntry
+// entries; entries whose pixel carries the top bit are left to composite_marked_kernel).
+template <bool CENSUS>
+__global__ void __launch_bounds__(128) composite_flat_kernel(const __grid_constant__ CompArgs a,
+                                                             const __grid_constant__ PiecePool pool,
+                                                             uint32_t* list) {
+    const FlatEntry* entries = reinterpret_cast<const FlatEntry*>(list + 4);
+    const uint32_t n_list = list[0];
+    const int lane = threadIdx.x & 31;
+    FlatLane L;
+    L.phase = kFlatIdle;
+    CountTable t;
+    t.n = 0;
+    CompCensus cs;
+    bool exhausted = false;
+    float4 cA = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 cB = make_float2(0.f, 0.f);
+    while (true) {
+        // idle lanes take the next entries, one atomic per warp
+        const unsigned need = __ballot_sync(0xffffffffu, L.phase == kFlatIdle && !exhausted);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            uint32_t first = 0;
+            if (lane == leader) first = atomicAdd(list + 1, (uint32_t)__popc(need));
+            first = __shfl_sync(0xffffffffu, first, leader);
+            if ((need >> lane) & 1u) {
+                bool started = false;
+                for (uint32_t i = first + __popc(need & ((1u << lane) - 1u)); i < n_list && !started;
+                     i = atomicAdd(list + 1, 1u)) {
+                    const FlatEntry en = entries[i];
+                    if (en.p & 0x80000000u) continue;  // the direct sweep's
+                    L.p = en.p;
+                    L.base = en.base;
+                    L.n = en.n;
+                    L.f0 = en.f0;
+                    L.phase = kFlatFirst;
+                    t.n = 0;
+                    flat_start_count(L, 0.f, 2.f);
+                    if (CENSUS) {
+                        cs.pixels += 1;
+                        for (int e = 0; e < a.k; ++e) cs.records += __ldg(a.pe[e].counts + L.p);
+                    }
+                    started = true;
+                }
+                if (!started) exhausted = true;
+            }
+        }
+        if (!__any_sync(0xffffffffu, L.phase != kFlatIdle)) break;
+        if (L.phase == kFlatIdle) continue;
+        // one piece of the lane's march
+        if (L.j == 0) {
+            cA = pool.A[L.base];
+            cB = pool.B[L.base];
+        }
+        Piece x;
+        x.f = L.f;
+        x.b = cB.x;
+        x.P[0] = cA.x;
+        x.P[1] = cA.y;
+        x.P[2] = cA.z;
+        x.a = cA.w;
+        x.lgT = cB.y;
+        if (L.j + 1 < L.n) {
+            cA = pool.A[L.base + L.j + 1];
+            cB = pool.B[L.base + L.j + 1];
+        }
+        if (L.phase == kFlatEmit) {
+            flat_emit_step(L, x, a.out);
+        } else {
+            L.nt += x.a > 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cq_step_select(L.st[q], x, L.g2[q]);
+        }
+        L.f = x.b;
+        if (++L.j == L.n) flat_end_march<CENSUS>(L, t, a.out, a.iters, a.status, cs);
     }
     if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
 }
@@ -2084,40 +2475,48 @@ static cudaError_t launch_staged(bool census, const CompArgs& a, void* workspace
     return launch_overflow<64, PREC>(census, a, sa.overflow, st);
 }
 
-template <int PREC, bool LIST>
-static cudaError_t launch_lane_pass(bool census, const CompArgs& a, const LaneArgs& la, uint64_t items,
-                                   cudaStream_t st) {
-    constexpr int CAP = LIST ? kLaneListRCap : kLaneRCap;
-    const size_t sm = lane_smem_bytes<PREC, CAP>();
-    auto kern = census ? composite_lane_kernel<PREC, true, LIST> : composite_lane_kernel<PREC, false, LIST>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLaneWarps * 32, sm);
-    if (e != cudaSuccess) return e;
-    uint64_t blocks = (uint64_t)device_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
-    const uint64_t need = (items + kLaneWarps - 1) / kLaneWarps;
-    if (blocks > need) blocks = need > 0 ? need : 1;
-    kern<<<(unsigned)blocks, kLaneWarps * 32, sm, st>>>(a, la);
-    return cudaGetLastError();
-}
-
 template <int PREC>
 static cudaError_t launch_lane(bool census, const CompArgs& a, void* workspace, size_t ws_bytes, cudaStream_t st) {
-    // workspace: [header][counters][list: count, pad, npix entries]
+    // workspace: [header][counters][list: 4 words, npix entries][pool: float4 x cap][pool: float2 x cap]
     const uint64_t npix = (uint64_t)a.npix;
-    if (ws_bytes < kWsHeader + 256 + stage_list_bytes(npix, 4)) return cudaErrorInvalidValue;
+    const size_t list_bytes = align_up(16 + npix * sizeof(FlatEntry), 256);
+    const size_t fixed = kWsHeader + 256 + list_bytes;
+    if (ws_bytes < fixed) return cudaErrorInvalidValue;
     char* base = static_cast<char*>(workspace);
     LaneArgs la;
     la.counter = reinterpret_cast<unsigned int*>(base + kWsHeader);
     la.list = reinterpret_cast<uint32_t*>(base + kWsHeader + 256);
-    cudaError_t e = cudaMemsetAsync(la.counter, 0, 256 + 8, st);
+    size_t cap = (ws_bytes - fixed) / (sizeof(float4) + sizeof(float2));
+    if (cap > 0x7FFFFFFFu) cap = 0x7FFFFFFFu;
+    la.pool.cap = (uint32_t)cap;
+    la.pool.A = reinterpret_cast<float4*>(base + fixed);
+    la.pool.B = reinterpret_cast<float2*>(base + fixed + cap * sizeof(float4));
+    cudaError_t e = cudaMemsetAsync(la.counter, 0, 256 + 16, st);
+    if (e != cudaSuccess) return e;
+    // batch pass
+    const size_t sm = lane_smem_bytes<PREC, kLaneRCap>();
+    auto k1 = census ? composite_lane_kernel<PREC, true> : composite_lane_kernel<PREC, false>;
+    e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, kLaneWarps * 32, sm);
     if (e != cudaSuccess) return e;
     const uint64_t batches = (npix + 31) / 32;
-    e = launch_lane_pass<PREC, false>(census, a, la, batches, st);
+    uint64_t blocks = (uint64_t)device_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    const uint64_t need = (batches + kLaneWarps - 1) / kLaneWarps;
+    if (blocks > need) blocks = need > 0 ? need : 1;
+    k1<<<(unsigned)blocks, kLaneWarps * 32, sm, st>>>(a, la);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // the list pass: its grid is sized for every pixel listed (the count is known only on the device)
-    e = launch_lane_pass<PREC, true>(census, a, la, batches, st);
+    // search pass: a persistent grid; the list's length is known only on the device
+    auto k2 = census ? composite_flat_kernel<true> : composite_flat_kernel<false>;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2, 128, 0);
+    if (e != cudaSuccess) return e;
+    uint64_t b2 = (uint64_t)device_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    const uint64_t need2 = (npix + 127) / 128;
+    if (b2 > need2) b2 = need2 > 0 ? need2 : 1;
+    k2<<<(unsigned)b2, 128, 0, st>>>(a, la.pool, la.list);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto k3 = census ? composite_marked_kernel<PREC, true> : composite_marked_kernel<PREC, false>;
     unsigned b3 = (unsigned)((npix + 127) / 128);

@@ -72,8 +72,12 @@ struct GenArgs {
     int cache_cap, slots;
 };
 
-// gen_count_kernel: CTAs of two warps on 16 x 4 tiles, eight per SM (128 registers), so that a
-// tile's barrier waits on one other warp's searches; gen_emit_kernel: four warps on 16 x 8 tiles
+// gen_count_kernel: CTAs of two warps on 16 x 4 tiles, VDI_COUNT_MIN_BLOCKS per SM (the register
+// bound follows), so that a tile's barrier waits on one other warp's searches; gen_emit_kernel: four
+// warps on 16 x 8 tiles
+#ifndef VDI_COUNT_MIN_BLOCKS
+#define VDI_COUNT_MIN_BLOCKS 12
+#endif
 constexpr int kTileW = 16, kCountTileH = 4, kCountThreads = 64, kEmitTileH = 8, kEmitThreads = 128;
 constexpr int kCacheCap = 1024;  // cached non-transparent samples per (PE, ray)
 
@@ -83,7 +87,7 @@ struct Census {
     unsigned long long evals = 0, steps = 0, passes = 0, searched = 0, overflow = 0, cached = 0, remarched = 0;
 };
 
-// 257 entries of (colour/opacity, difference to the next entry); opacity
+// 257 entries of colour/opacity, then their differences to the next entry; opacity
 // corrected to the step length: a' = 1 - (1 - a)^(step / ref_len).
 __device__ __forceinline__ void load_lut(const GenReq& a, float4* lut2) {
     __shared__ float4 base[257];
@@ -96,8 +100,8 @@ __device__ __forceinline__ void load_lut(const GenReq& a, float4* lut2) {
     __syncthreads();
     for (int i = threadIdx.x; i < 257; i += blockDim.x) {
         float4 v = base[i], w = base[min(i + 1, 256)];
-        lut2[2 * i] = v;
-        lut2[2 * i + 1] = make_float4(__fsub_rn(w.x, v.x), __fsub_rn(w.y, v.y), __fsub_rn(w.z, v.z),
+        lut2[i] = v;
+        lut2[257 + i] = make_float4(__fsub_rn(w.x, v.x), __fsub_rn(w.y, v.y), __fsub_rn(w.z, v.z),
                                       __fsub_rn(w.w, v.w));
     }
     __syncthreads();
@@ -600,8 +604,10 @@ __device__ __forceinline__ void census_flush_gen(const Census& cs, unsigned long
     atomicAdd(ctr + 7, cs.remarched);
 }
 
+// the learned instantiation keeps 8 blocks (128 registers): its inlined refinement spills under tighter bounds
 template <bool CENSUS, bool LEARNED, bool OWNED = false>
-__global__ void __launch_bounds__(kCountThreads, 8) gen_count_kernel(const __grid_constant__ GenArgs a) {
+__global__ void __launch_bounds__(kCountThreads, LEARNED ? 8 : VDI_COUNT_MIN_BLOCKS) gen_count_kernel(
+    const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     __shared__ unsigned int s_item;
     load_lut(a.r, lut2);
@@ -810,7 +816,7 @@ __device__ __forceinline__ int batch_request(const GenBatchReq* reqs, int n, uin
     return lo;
 }
 
-__global__ void __launch_bounds__(kCountThreads, 8) gen_count_batched_kernel(const __grid_constant__ GenBatchArgs a) {
+__global__ void __launch_bounds__(kCountThreads, VDI_COUNT_MIN_BLOCKS) gen_count_batched_kernel(const __grid_constant__ GenBatchArgs a) {
     __shared__ float4 lut2[2 * 257];
     __shared__ unsigned int s_item;
     CacheRef cref;

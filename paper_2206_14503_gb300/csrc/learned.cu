@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(64) tile_features_kernel(const __grid_constant
     __syncthreads();
     for (int i = threadIdx.x; i < 257; i += blockDim.x) {
         int n = min(i + 1, 256);
-        lut2[2 * i] = make_float4(base[i][0], base[i][1], base[i][2], base[i][3]);
-        lut2[2 * i + 1] = make_float4(__fsub_rn(base[n][0], base[i][0]), __fsub_rn(base[n][1], base[i][1]),
+        lut2[i] = make_float4(base[i][0], base[i][1], base[i][2], base[i][3]);
+        lut2[257 + i] = make_float4(__fsub_rn(base[n][0], base[i][0]), __fsub_rn(base[n][1], base[i][1]),
                                       __fsub_rn(base[n][2], base[i][2]), __fsub_rn(base[n][3], base[i][3]));
     }
     __syncthreads();

@@ -296,7 +296,9 @@ __device__ __forceinline__ void cell_load(const long long P[3], const BrickDev& 
 }
 
 // Classification of table coordinate x in [0, 255]: the step-corrected table
-// (257 entries of value and difference) interpolated at x, premultiplied
+// (257 entries, then their 257 differences to the next entry; two halves so
+// that a warp's 16-byte reads of different entries spread over all banks)
+// interpolated at x, premultiplied
 // colour, log-transmittance.  A function of x alone, so a cached x gives the
 // sample's colour and opacity bit for bit.
 __device__ __forceinline__ void classify_x(float x, const float4* __restrict__ lut2, Sample& s) {
@@ -304,7 +306,7 @@ __device__ __forceinline__ void classify_x(float x, const float4* __restrict__ l
     float fl;
     int i = floor_magic(x, fl);
     float wt = __fsub_rn(x, fl);
-    float4 base = lut2[2 * i], dl = lut2[2 * i + 1];
+    float4 base = lut2[i], dl = lut2[257 + i];
     float R = __fmaf_rn(wt, dl.x, base.x);
     float G = __fmaf_rn(wt, dl.y, base.y);
     float B = __fmaf_rn(wt, dl.z, base.z);
