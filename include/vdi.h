@@ -350,7 +350,7 @@ vdi_status vdi_generate_static_scratch(const vdi_brick* bricks, int32_t k, const
  * The pieces are re-segmented with Eq. 1 and a per-pixel gamma search, and
  * at most n_s supersegments are written front to back with a zero tail.
  * params->schedule (all give the same result, bit for bit):
- *   0 automatic (VDI_SCHED_STAGED);
+ *   0 automatic (VDI_SCHED_LANE for k <= 8, else VDI_SCHED_STAGED);
  *   VDI_SCHED_STAGED (4): a warp builds the pieces of 32 pixels, one pixel at
  *     a time with all its lanes (coalesced loads of the K lists, a stable
  *     merge of their bounds, an exact prefix scan of the records' terms) into

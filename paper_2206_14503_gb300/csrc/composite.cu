@@ -25,20 +25,26 @@
 // autotuner, vdi_composite_autotune; the default is the lane schedule for
 // K <= 8 and the staged one above):
 //   VDI_SCHED_LANE (5, K <= 8): composite_lane_kernel copies a warp's 32
-//     pixels' records into shared memory with coalesced loads, sweeps each
-//     pixel there (a lane each), and emits the pixels whose gamma = 0 count is
-//     within n_s; the rest are listed and composite_list_kernel searches them,
-//     a lane each, so that no lane idles behind a searching neighbour;
-//   VDI_SCHED_STAGED (4): composite_staged_kernel, a persistent grid of
-//     8-warp CTAs, builds the pieces of 32 pixels a warp at a time (whole warp
-//     per pixel: coalesced span loads, merge-path sort of the bounds, exact
-//     prefix scan of the mixture terms) into a per-warp piece buffer, then
-//     each lane searches and emits its pixel from its column; pixels with more
-//     than 1024 records or more pieces than the buffer's rows are listed for
-//     composite_overflow_kernel (the direct schedule 2);
+//     pixels' records into shared memory with asynchronous coalesced copies,
+//     sweeps each pixel there (a lane each; depth-disjoint lists, as every box
+//     decomposition gives, without the K-head merge), and emits the pixels
+//     whose gamma = 0 count is within n_s; the others' pieces go to a pool in
+//     the workspace and composite_flat_kernel searches and emits them;
+//   VDI_SCHED_STAGED (4): composite_build_kernel builds each pixel's pieces
+//     with the whole warp (coalesced span loads, merge-path sort of the bounds,
+//     exact prefix scan of the mixture terms) into the pool, and
+//     composite_flat_kernel searches and emits every pixel; the host runs the
+//     pixels in chunks whose pieces fit the pool;
+//   both list pixels they cannot stage (more than 480 / 1024 records, pieces
+//     beyond the pool, lists out of depth order) for composite_marked_kernel,
+//     the direct sweep;
 //   1, 2, 3 (direct, composite_kernel): one thread per pixel re-sweeps its K
 //     lists on every march, heads in registers (1, K <= 8) or in shared memory
 //     under a winner tree (2; 3 with three levels per march).
+// composite_flat_kernel runs the search and the emission as one loop whose
+// body handles one piece of a lane's current march, so lanes at different
+// marches or pixels execute the same instructions and a lane that finishes
+// takes the next pixel.
 //
 // composite_batched_kernel runs many requests (different sizes, K, N_S) in one
 // persistent launch: warps pull (request, 32-pixel batch) items from an atomic
@@ -1073,13 +1079,24 @@ __device__ __forceinline__ void stage_apply(const PeIn* pe, const StageSmem& S, 
     a.xr ^= c;
 }
 
+// Where phase G writes a pixel's pieces: a column of a warp's piece buffer
+// (rows 32 elements apart), or (POOL) a run of the pool allocated once the
+// pixel's piece count is known; base receives the run's first piece, and a
+// pixel whose run does not fit the pool gets npieces = -1 and no writes.
+struct PoolRun {
+    uint32_t* counter;
+    uint32_t cap;
+    uint32_t base;
+};
+
 // Phase G after the merge: exact prefix scan of the records' terms over the
 // sorted bounds (srt, E of them; nv valid records), in contiguous chunks per
-// lane, and the pieces written to the column.
-template <int PREC, bool OPQ>
+// lane, and the pieces written to the column (or the pool).
+template <int PREC, bool OPQ, bool POOL = false>
 __device__ __forceinline__ void stage_scan(const PeIn* pe, const StageSmem& S, const uint16_t* srt, uint32_t E,
                                            uint32_t nv, float4* colA, float2* colB, int& npieces, int& nt,
-                                           float& f0) {
+                                           float& f0, PoolRun* run = nullptr) {
+    constexpr size_t kStride = POOL ? 1 : 32;
     const int lane = threadIdx.x & 31;
     // exact prefix scan of the records' terms over the sorted bounds, in
     // contiguous chunks per lane
@@ -1106,6 +1123,20 @@ __device__ __forceinline__ void stage_scan(const PeIn* pe, const StageSmem& S, c
     ScanState st = shfl_up_state<OPQ>(inc, 1);
     if (lane == 0) scan_reset(st);
     const uint32_t total_pieces = __shfl_sync(0xffffffffu, inc.nb, 31);
+    if constexpr (POOL) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(run->counter, total_pieces);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        run->base = base;
+        if ((uint64_t)base + total_pieces > (uint64_t)run->cap) {
+            npieces = -1;
+            nt = 0;
+            f0 = 0.f;
+            return;
+        }
+        colA += base;
+        colB += base;
+    }
     // the pieces: after bound i the active set is that of [key_i, key_{i+1}]
     int my_nt = 0;
     uint32_t row = st.nb;
@@ -1128,8 +1159,8 @@ __device__ __forceinline__ void stage_scan(const PeIn* pe, const StageSmem& S, c
         }
         Piece x;
         piece_from(st.s, whole, wc, t, t1, x);
-        colA[(size_t)row * 32] = make_float4(x.P[0], x.P[1], x.P[2], x.a);
-        colB[(size_t)row * 32] = make_float2(x.b, x.lgT);
+        colA[(size_t)row * kStride] = make_float4(x.P[0], x.P[1], x.P[2], x.a);
+        colB[(size_t)row * kStride] = make_float2(x.b, x.lgT);
         my_nt += x.a > 0.f;
         ++row;
     }
@@ -1143,9 +1174,9 @@ __device__ __forceinline__ void stage_scan(const PeIn* pe, const StageSmem& S, c
 // Phase G for pixel p into one column of the piece buffer (colA/colB point at
 // row 0 of the column; rows are 32 elements apart).  Returns false when the
 // pixel has more than kStageRMax records.
-template <int PREC>
+template <int PREC, bool POOL = false>
 __device__ bool stage_pixel(const PeIn* pe, int k, uint32_t p, StageSmem& S, float4* colA, float2* colB, int rows,
-                            int& npieces, int& nt, float& f0) {
+                            int& npieces, int& nt, float& f0, PoolRun* run = nullptr) {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     // counts and list starts, prefix over PEs
@@ -1277,8 +1308,8 @@ __device__ bool stage_pixel(const PeIn* pe, int k, uint32_t p, StageSmem& S, flo
         __syncwarp();
     }
     const uint16_t* srt = S.pay[src];
-    if (opaque) stage_scan<PREC, true>(pe, S, srt, E, nv, colA, colB, npieces, nt, f0);
-    else stage_scan<PREC, false>(pe, S, srt, E, nv, colA, colB, npieces, nt, f0);
+    if (opaque) stage_scan<PREC, true, POOL>(pe, S, srt, E, nv, colA, colB, npieces, nt, f0, run);
+    else stage_scan<PREC, false, POOL>(pe, S, srt, E, nv, colA, colB, npieces, nt, f0, run);
     __syncwarp();
     return true;
 }
@@ -1371,65 +1402,7 @@ __device__ __forceinline__ void stage_batch(const PeIn* pe, int k, uint32_t base
     }
 }
 
-template <int PREC, bool CENSUS>
-__global__ void __launch_bounds__(kStageWarps * 32, 1) composite_staged_kernel(const __grid_constant__ CompArgs a,
-                                                                          const __grid_constant__ StageArgs sa) {
-    extern __shared__ __align__(16) unsigned char stage_smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    StageSmem& S = reinterpret_cast<StageSmem*>(stage_smem)[warp];
-    const size_t gw = (size_t)blockIdx.x * kStageWarps + warp;
-    float4* wA = sa.bufA + gw * (size_t)sa.rows * 32;
-    float2* wB = sa.bufB + gw * (size_t)sa.rows * 32;
-    const uint32_t nbatch = ((uint32_t)a.npix + 31u) / 32u;
-    CompCensus cs;
-    while (true) {
-        uint32_t batch = 0;
-        if (lane == 0) batch = atomicAdd(sa.counter, 1u);
-        batch = __shfl_sync(0xffffffffu, batch, 0);
-        if (batch >= nbatch) break;
-        const uint32_t base = batch * 32u;
-        bool ok;
-        int n, nt;
-        float f0;
-        stage_batch<PREC>(a.pe, a.k, base, (uint32_t)a.npix, S, wA, wB, sa.rows, ok, n, nt, f0);
-        const uint32_t p = base + (uint32_t)lane;
-        if (p < (uint32_t)a.npix) {
-            if (ok) {
-                BufSweeper sw;
-                sw.A = wA + lane;
-                sw.B = wB + lane;
-                sw.n = n;
-                sw.f0 = f0;
-                if (CENSUS) {
-                    cs.pixels += 1;
-                    for (int e = 0; e < a.k; ++e) cs.records += __ldg(a.pe[e].counts + p);
-                }
-                composite_search_emit<2, CENSUS>(sw, a.out, a.iters, a.status, p, &cs);
-            } else {
-                const uint32_t slot = atomicAdd(sa.overflow, 1u);
-                sa.overflow[1 + slot] = p;
-            }
-        }
-        __syncwarp();
-    }
-    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
-}
-
-// the pixels the stage could not hold, by the direct path (heads in shared memory)
-template <int P, int PREC, bool CENSUS>
-__global__ void __launch_bounds__(128) composite_overflow_kernel(const __grid_constant__ CompArgs a,
-                                                                 const uint32_t* overflow) {
-    extern __shared__ uint32_t smem[];
-    const uint32_t n = *overflow;
-    CompCensus cs;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < n; i += gridDim.x * blockDim.x) {
-        if (i < n) composite_pixel<0, P, 2, PREC, CENSUS>(a.pe, a.k, a.out, a.iters, a.status, overflow[1 + i], smem,
-                                                          &cs);
-    }
-    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
-}
-
-// storage of the pieces of the pixels the lane schedule searches
+// storage of the pieces of the pixels the lane and pooled staged paths search
 struct PiecePool {
     float4* A;  // (P.rgb, a)
     float2* B;  // (b, log2(1 - a))
@@ -1658,6 +1631,7 @@ struct SlabSweeper {
     uint32_t st[kLaneKMax], cnt[kLaneKMax];
     bool disjoint;
     uint32_t order;  // PEs by the front of their first record, 4 bits each
+    int nonempty;    // PEs with a record of positive length
 
     __device__ __forceinline__ void prepare() {
         float lo[kLaneKMax], hi[kLaneKMax];
@@ -1718,13 +1692,14 @@ struct SlabSweeper {
             end = he;
         }
         disjoint = ok;
-        order = ord | ((uint32_t)n << 28);
+        order = ord;
+        nonempty = n;
     }
 
     template <typename V>
     __device__ __forceinline__ int run(V& v) const {
         if (!disjoint) return sweep_slab(*S, k, st, cnt, v);
-        const int n = (int)(order >> 28);
+        const int n = nonempty;
         int np = 0;
         float t = 0.f;
         bool first = true;
@@ -1862,18 +1837,21 @@ __device__ __forceinline__ void slab_stage(const PeIn* pe, int k, SLAB& S, bool 
     }
 }
 
-// the listed pixels marked for the direct sweep (records beyond a slab, or pieces beyond the pool)
-template <int PREC, bool CENSUS>
+// the listed pixels marked for the direct sweep (records beyond a slab, pieces beyond the pool, lists
+// out of depth order), list heads in registers (KMAX > 0) or in shared memory under a winner tree of P
+// leaves (KMAX == 0)
+template <int KMAX, int P, int PREC, bool CENSUS>
 __global__ void __launch_bounds__(128) composite_marked_kernel(const __grid_constant__ CompArgs a,
                                                                const uint32_t* __restrict__ list) {
+    extern __shared__ uint32_t smem[];
     const uint32_t n = *list;
     const FlatEntry* entries = reinterpret_cast<const FlatEntry*>(list + 4);
     CompCensus cs;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t v = entries[i].p;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < n; i += gridDim.x * blockDim.x) {
+        const uint32_t v = i < n ? entries[i].p : 0u;
         if (v & 0x80000000u)
-            composite_pixel<kLaneKMax, 16, 2, PREC, CENSUS>(a.pe, a.k, a.out, a.iters, a.status, v & 0x7FFFFFFFu,
-                                                            nullptr, &cs);
+            composite_pixel<KMAX, P, 2, PREC, CENSUS>(a.pe, a.k, a.out, a.iters, a.status, v & 0x7FFFFFFFu, smem,
+                                                      &cs);
     }
     if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
 }
@@ -1994,6 +1972,63 @@ __global__ void __launch_bounds__(kLaneWarps * 32) composite_lane_kernel(const _
             }
             __syncwarp();
         }
+    }
+    if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
+}
+
+// ---------------------------------------------------------------------------
+// Pooled staged path (K > kLaneKMax): composite_build_kernel builds each
+// pixel's pieces as phase G of the staged schedule does -- the whole warp on
+// one pixel: coalesced span loads, a stable merge of the bounds, the exact
+// prefix scan of the mixture terms -- but writes them as one run of the pool
+// and lists the pixel; composite_flat_kernel then searches and emits every
+// listed pixel, a lane each.  The host runs the pixels in chunks whose pieces
+// fit the pool.
+// ---------------------------------------------------------------------------
+struct BuildArgs {
+    unsigned int* counter;  // batch counter
+    uint32_t* list;         // as LaneArgs::list
+    PiecePool pool;
+    uint32_t p0, p1;        // the chunk's pixels
+};
+
+template <int PREC, bool CENSUS>
+__global__ void __launch_bounds__(kStageWarps * 32, 1) composite_build_kernel(const __grid_constant__ CompArgs a,
+                                                                              const __grid_constant__ BuildArgs ba) {
+    extern __shared__ __align__(16) unsigned char stage_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    StageSmem& S = reinterpret_cast<StageSmem*>(stage_smem)[warp];
+    const uint32_t nbatch = (ba.p1 - ba.p0 + 31u) / 32u;
+    CompCensus cs;
+    while (true) {
+        uint32_t batch = 0;
+        if (lane == 0) batch = atomicAdd(ba.counter, 1u);
+        batch = __shfl_sync(0xffffffffu, batch, 0);
+        if (batch >= nbatch) break;
+        const uint32_t base = ba.p0 + batch * 32u;
+        FlatEntry mine{0u, 0u, 0u, 0.f};
+        bool have = false;
+        for (int col = 0; col < 32; ++col) {
+            const uint32_t p = base + (uint32_t)col;
+            if (p >= ba.p1) break;
+            PoolRun run{ba.list + 2, ba.pool.cap, 0u};
+            int n = 0, nt = 0;
+            float f0 = 0.f;
+            const bool ok = stage_pixel<PREC, true>(a.pe, a.k, p, S, ba.pool.A, ba.pool.B, 0x7FFFFFFF, n, nt, f0, &run);
+            if (lane == col) {
+                if (!ok || n < 0) {
+                    mine = FlatEntry{p | 0x80000000u, 0u, 0u, 0.f};
+                    have = true;
+                } else if (n == 0) {
+                    finish_pixel(a.out, p, 0, 0.f);  // no record: an empty list
+                    if (CENSUS) cs.pixels += 1;
+                } else {
+                    mine = FlatEntry{p, run.base, (uint32_t)n, f0};
+                    have = true;
+                }
+            }
+        }
+        list_push(ba.list, have, mine);
     }
     if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
 }
@@ -2203,22 +2238,25 @@ __global__ void __launch_bounds__(128) composite_flat_kernel(const __grid_consta
             first = __shfl_sync(0xffffffffu, first, leader);
             if ((need >> lane) & 1u) {
                 bool started = false;
-                for (uint32_t i = first + __popc(need & ((1u << lane) - 1u)); i < n_list && !started;
-                     i = atomicAdd(list + 1, 1u)) {
+                uint32_t i = first + __popc(need & ((1u << lane) - 1u));
+                while (i < n_list) {
                     const FlatEntry en = entries[i];
-                    if (en.p & 0x80000000u) continue;  // the direct sweep's
-                    L.p = en.p;
-                    L.base = en.base;
-                    L.n = en.n;
-                    L.f0 = en.f0;
-                    L.phase = kFlatFirst;
-                    t.n = 0;
-                    flat_start_count(L, 0.f, 2.f);
-                    if (CENSUS) {
-                        cs.pixels += 1;
-                        for (int e = 0; e < a.k; ++e) cs.records += __ldg(a.pe[e].counts + L.p);
+                    if (!(en.p & 0x80000000u)) {  // (entries with the top bit are the direct sweep's)
+                        L.p = en.p;
+                        L.base = en.base;
+                        L.n = en.n;
+                        L.f0 = en.f0;
+                        L.phase = kFlatFirst;
+                        t.n = 0;
+                        flat_start_count(L, 0.f, 2.f);
+                        if (CENSUS) {
+                            cs.pixels += 1;
+                            for (int e = 0; e < a.k; ++e) cs.records += __ldg(a.pe[e].counts + L.p);
+                        }
+                        started = true;
+                        break;
                     }
-                    started = true;
+                    i = atomicAdd(list + 1, 1u);
                 }
                 if (!started) exhausted = true;
             }
@@ -2347,7 +2385,7 @@ __global__ void __launch_bounds__(128) composite_batched_direct_kernel(const __g
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-int default_schedule(int k) { return k <= 8 ? 1 : VDI_SCHED_STAGED; }
+int default_schedule(int k) { return k <= kLaneKMax ? VDI_SCHED_LANE : VDI_SCHED_STAGED; }
 
 static OutDev out_dev(const vdi_regular* out) {
     OutDev o;
@@ -2392,10 +2430,18 @@ static size_t stage_buffer_bytes(size_t ctas, int rows) {
     return ctas * kStageWarps * (size_t)rows * 32 * (sizeof(float4) + sizeof(float2));
 }
 
+// pixels per chunk of the pooled staged path that the queried workspace holds at the stage's worst case
+constexpr uint64_t kPoolChunkPixels = 131072;
+
 size_t composite_workspace_bytes(int w, int h) {
     const uint64_t npix = (uint64_t)w * (uint64_t)h;
-    const uint64_t batches = (npix + 31) / 32;
-    return kWsHeader + 256 + stage_list_bytes(npix, 4) + stage_buffer_bytes(stage_ctas(batches), kStageCap);
+    const size_t piece = sizeof(float4) + sizeof(float2);
+    // pooled staged path: a chunk of up to kPoolChunkPixels pixels, each with room for the stage's pieces
+    const uint64_t chunk = npix < kPoolChunkPixels ? npix : kPoolChunkPixels;
+    const size_t pooled = kWsHeader + 512 + (size_t)chunk * (sizeof(FlatEntry) + 2 * kStageRMax * piece);
+    // lane path: the list of every pixel and a pool of 16 pieces per pixel
+    const size_t lane = kWsHeader + 256 + align_up(16 + npix * sizeof(FlatEntry), 256) + (size_t)npix * 16 * piece;
+    return pooled > lane ? pooled : lane;
 }
 
 // Staged-path layout in the workspace; rows = 0 when the workspace holds no
@@ -2441,38 +2487,83 @@ static cudaError_t launch_sched(int schedule, int k, bool census, unsigned block
     return launch_cs<0, 64, 2, PREC>(census, blocks, threads, st, a);
 }
 
-template <int P, int PREC>
-static cudaError_t launch_overflow(bool census, const CompArgs& a, const uint32_t* overflow, cudaStream_t st) {
-    const size_t sm = heads_smem_bytes<P>(128);
-    auto kern = census ? composite_overflow_kernel<P, PREC, true> : composite_overflow_kernel<P, PREC, false>;
+
+template <int KMAX, int P, int PREC>
+static cudaError_t launch_marked(bool census, const CompArgs& a, const uint32_t* list, uint64_t npix,
+                                 cudaStream_t st) {
+    const size_t sm = KMAX > 0 ? 0 : heads_smem_bytes<P>(128);
+    auto kern = census ? composite_marked_kernel<KMAX, P, PREC, true> : composite_marked_kernel<KMAX, P, PREC, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    unsigned blocks = (unsigned)(((uint64_t)a.npix + 127) / 128);
-    const unsigned cap = (unsigned)device_sms() * 8u;
-    if (blocks > cap) blocks = cap;
-    kern<<<blocks, 128, sm, st>>>(a, overflow);
+    unsigned b = (unsigned)((npix + 127) / 128);
+    const unsigned cap = (unsigned)device_sms() * 2u;
+    if (b > cap) b = cap;
+    kern<<<b, 128, sm, st>>>(a, list);
     return cudaGetLastError();
 }
 
 template <int PREC>
-static cudaError_t launch_staged(bool census, const CompArgs& a, void* workspace, size_t ws_bytes, cudaStream_t st) {
+static cudaError_t launch_flat(bool census, const CompArgs& a, const PiecePool& pool, uint32_t* list, uint64_t lanes,
+                               cudaStream_t st) {
+    auto k2 = census ? composite_flat_kernel<true> : composite_flat_kernel<false>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2, 128, 0);
+    if (e != cudaSuccess) return e;
+    uint64_t b = (uint64_t)device_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    const uint64_t need = (lanes + 127) / 128;
+    if (b > need) b = need > 0 ? need : 1;
+    k2<<<(unsigned)b, 128, 0, st>>>(a, pool, list);
+    return cudaGetLastError();
+}
+
+// pieces a pixel of the pooled staged path may need (the stage holds kStageRMax records)
+constexpr uint64_t kPoolPiecesPerPixel = 2 * kStageRMax;
+
+template <int PREC>
+static cudaError_t launch_staged_pool(bool census, const CompArgs& a, void* workspace, size_t ws_bytes,
+                                     cudaStream_t st) {
+    // workspace: [header][counters][list: 4 words, entries of a chunk][pool: float4 x cap][pool: float2 x cap]
     const uint64_t npix = (uint64_t)a.npix;
-    const size_t ctas = stage_ctas((npix + 31) / 32);
-    const StageArgs sa = stage_args(workspace, ws_bytes, npix, 4, ctas);
-    if (sa.rows == 0) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(sa.counter, 0, 256 + 8, st);
-    if (e != cudaSuccess) return e;
+    char* base = static_cast<char*>(workspace);
+    // the chunk: as many pixels as the pool holds at the stage's worst case, all of them if they fit
+    const size_t head = kWsHeader + 256;
+    if (ws_bytes < head + 256) return cudaErrorInvalidValue;
+    const size_t per_pixel = sizeof(FlatEntry) + kPoolPiecesPerPixel * (sizeof(float4) + sizeof(float2));
+    uint64_t chunk = (ws_bytes - head - 256) / per_pixel;
+    if (chunk > npix) chunk = npix;
+    if (chunk == 0) return cudaErrorInvalidValue;
+    const size_t list_bytes = align_up(16 + chunk * sizeof(FlatEntry), 256);
+    size_t cap = (ws_bytes - head - list_bytes) / (sizeof(float4) + sizeof(float2));
+    if (cap > 0x7FFFFFFFu) cap = 0x7FFFFFFFu;
+    BuildArgs ba;
+    ba.counter = reinterpret_cast<unsigned int*>(base + kWsHeader);
+    ba.list = reinterpret_cast<uint32_t*>(base + head);
+    ba.pool.cap = (uint32_t)cap;
+    ba.pool.A = reinterpret_cast<float4*>(base + head + list_bytes);
+    ba.pool.B = reinterpret_cast<float2*>(base + head + list_bytes + cap * sizeof(float4));
     const size_t sm = kStageWarps * sizeof(StageSmem);
-    auto kern = census ? composite_staged_kernel<PREC, true> : composite_staged_kernel<PREC, false>;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    kern<<<(unsigned)ctas, kStageWarps * 32, sm, st>>>(a, sa);
-    e = cudaGetLastError();
+    auto kb = census ? composite_build_kernel<PREC, true> : composite_build_kernel<PREC, false>;
+    cudaError_t e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int P = tree_leaves(a.k);
-    if (P == 16) return launch_overflow<16, PREC>(census, a, sa.overflow, st);
-    if (P == 32) return launch_overflow<32, PREC>(census, a, sa.overflow, st);
-    return launch_overflow<64, PREC>(census, a, sa.overflow, st);
+    for (uint64_t p0 = 0; p0 < npix; p0 += chunk) {
+        const uint64_t p1 = p0 + chunk < npix ? p0 + chunk : npix;
+        ba.p0 = (uint32_t)p0;
+        ba.p1 = (uint32_t)p1;
+        e = cudaMemsetAsync(ba.counter, 0, 256, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ba.list, 0, 16, st);
+        if (e != cudaSuccess) return e;
+        kb<<<(unsigned)stage_ctas((p1 - p0 + 31) / 32), kStageWarps * 32, sm, st>>>(a, ba);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_flat<PREC>(census, a, ba.pool, ba.list, p1 - p0, st);
+        if (e == cudaSuccess) {
+            if (P == 16) e = launch_marked<0, 16, PREC>(census, a, ba.list, p1 - p0, st);
+            else if (P == 32) e = launch_marked<0, 32, PREC>(census, a, ba.list, p1 - p0, st);
+            else e = launch_marked<0, 64, PREC>(census, a, ba.list, p1 - p0, st);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <int PREC>
@@ -2509,21 +2600,9 @@ static cudaError_t launch_lane(bool census, const CompArgs& a, void* workspace, 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // search pass: a persistent grid; the list's length is known only on the device
-    auto k2 = census ? composite_flat_kernel<true> : composite_flat_kernel<false>;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2, 128, 0);
+    e = launch_flat<PREC>(census, a, la.pool, la.list, npix, st);
     if (e != cudaSuccess) return e;
-    uint64_t b2 = (uint64_t)device_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
-    const uint64_t need2 = (npix + 127) / 128;
-    if (b2 > need2) b2 = need2 > 0 ? need2 : 1;
-    k2<<<(unsigned)b2, 128, 0, st>>>(a, la.pool, la.list);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    auto k3 = census ? composite_marked_kernel<PREC, true> : composite_marked_kernel<PREC, false>;
-    unsigned b3 = (unsigned)((npix + 127) / 128);
-    const unsigned cap3 = (unsigned)device_sms() * 2u;
-    if (b3 > cap3) b3 = cap3;
-    k3<<<b3, 128, 0, st>>>(a, la.list);
-    return cudaGetLastError();
+    return launch_marked<kLaneKMax, 16, PREC>(census, a, la.list, npix, st);
 }
 
 vdi_status launch_composite(const vdi_compact* pe, int k, int w, int h, const vdi_regular* out, int iters,
@@ -2542,14 +2621,20 @@ vdi_status launch_composite(const vdi_compact* pe, int k, int w, int h, const vd
     a.out = out_dev(out);
     a.status = status;
     const int prec_in = pe[0].prec;
+    const bool automatic = schedule == 0;
     if (schedule == 0 || (schedule == 1 && k > 8)) schedule = default_schedule(k);
+    // an automatic choice falls back to a direct schedule when the workspace holds no list or stage
+    if (automatic && schedule == VDI_SCHED_LANE &&
+        ws_bytes < kWsHeader + 256 + align_up(16 + (uint64_t)w * h * sizeof(FlatEntry), 256))
+        schedule = 1;
+    if (automatic && schedule == VDI_SCHED_STAGED && ws_bytes < composite_workspace_bytes(1, 1)) schedule = 2;
     if (a.npix == 0) return VDI_OK;
     const bool f32 = prec_in == VDI_PREC_F32;
     cudaError_t e;
     if (schedule == VDI_SCHED_LANE && k > kLaneKMax) schedule = VDI_SCHED_STAGED;
     if (schedule == VDI_SCHED_STAGED) {
-        e = f32 ? launch_staged<VDI_PREC_F32>(census, a, workspace, ws_bytes, st)
-                : launch_staged<VDI_PREC_F16>(census, a, workspace, ws_bytes, st);
+        e = f32 ? launch_staged_pool<VDI_PREC_F32>(census, a, workspace, ws_bytes, st)
+                : launch_staged_pool<VDI_PREC_F16>(census, a, workspace, ws_bytes, st);
     } else if (schedule == VDI_SCHED_LANE) {
         e = f32 ? launch_lane<VDI_PREC_F32>(census, a, workspace, ws_bytes, st)
                 : launch_lane<VDI_PREC_F16>(census, a, workspace, ws_bytes, st);

@@ -87,7 +87,7 @@ bool plan(const vdi_pipeline_desc* d, Layout& L) {
     }
     const vdi_params& p = d->params;
     if (!(p.step > 0.f) || !(p.ref_len > 0.f) || p.bisect_iters < 1 || p.bisect_iters > 24 || p.schedule < 0 ||
-        p.schedule > VDI_SCHED_STAGED) {
+        p.schedule > VDI_SCHED_LANE) {
         set_error(VDI_ERR_INVALID_ARG, "vdi_pipeline: params");
         return false;
     }

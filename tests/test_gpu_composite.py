@@ -96,6 +96,12 @@ def test_composite_of_generated_subvdis(tiny_workload):
     oc, _, orecs = oracle_composite(lists, w["n_s"], npix)
     compare_lists(g["counts"], np.concatenate([g["fb"], g["rgba"]], -1), oc, orecs,
                   1e-5 * chords(cam, w["dims"]), 1e-5)
+    # sub-VDIs of a box decomposition are disjoint in depth along every ray (the lane schedule's
+    # fast path): every schedule gives the same bits
+    for sched in _schedules(len(lists)):
+        gs = composite(lists, cam.width, cam.height, w["n_s"], schedule=sched)
+        for key in ("counts", "gamma", "fb", "rgba"):
+            assert np.array_equal(gs[key], g[key]), (sched, key)
     # and flattening gives the volume rendering (associativity of over)
     ref = oracle.dvr(w["vol"], w["lut"], cam, w["step"], w["ref_len"])
     assert np.abs(g["image"] - ref).max() <= 1e-5
@@ -160,3 +166,37 @@ def test_full_size_sampled_pixels_dense_k32():
     gr = np.concatenate([g["fb"], g["rgba"]], -1)[pix]
     compare_lists(g["counts"][pix], gr, cnt, recs, 1e-5, 1e-5)
     assert np.abs(g["image"][pix] - oracle.flatten(cnt, recs)).max() <= 1e-5
+
+
+@pytest.mark.parametrize("k,n_s", [(6, 12), (4, 30)])
+def test_schedules_agree_on_large_inputs(k, n_s):
+    # enough pixels that the search passes' persistent grids take work many times over (the lane schedule
+    # lists hundreds of thousands of pixels); every schedule writes a fresh output and must give the same
+    # bits
+    import torch
+
+    import paper_2206_14503_gb300 as vdi
+    from synth import gpu_lists
+
+    w, h = 640, 480
+    npix = w * h
+    pes = []
+    for e in range(k):
+        c, o, fb, rgba = gpu_lists.dense_set(0x1A4E + k, 0, e, npix, n_s)
+        # lengths U{0..n_s}: keep a pixel-dependent prefix of each dense list
+        cnt = (torch.arange(npix, device="cuda", dtype=torch.int64) * (2654435761 + 97 * e) >> 7) % (n_s + 1)
+        pes.append(vdi.Compact.from_tensors(cnt.to(torch.int32), o, rgba, fb, vdi.VDI_PREC_F32))
+    ws = vdi.Workspace(vdi.vdi_composite_workspace(k, w, h, n_s))
+    ref = None
+    for sched in _schedules(k):
+        out = vdi.Regular(npix, n_s)
+        vdi.check(vdi.vdi_composite([p.struct() for p in pes], w, h, out.struct(), vdi.make_params(schedule=sched),
+                                    ws.ptr, ws.nbytes), f"schedule {sched}")
+        vdi.check(ws.status(), "status")
+        got = (out.counts, out.gamma, out.rgba, out.fb)
+        if ref is None:
+            ref = got
+            assert int((out.counts > 0).sum()) > npix // 2
+        else:
+            for a, b in zip(ref, got):
+                assert torch.equal(a, b), sched
