@@ -408,7 +408,7 @@ def gen_batched_eval(vdi, torch, stream, n_req=16, warmup=1, steps=3):
             vol = gpu_volume.volume(dims, 32, 3, synth.SEED_VOLUME + 10 + r)
             br = vdi.Bricks(vol, dims, vdi.vdi_split_boxes(dims, grid), stream)
             cam = synth.orbit(dims, 16, w, h, synth.SEED_ORBIT)[r % 16]
-            outs = [vdi.Compact(w * h, w * h * n_s // 2) for _ in range(grid[0] * grid[1] * grid[2])]
+            outs = [vdi.Compact(w * h, w * h * n_s) for _ in range(grid[0] * grid[1] * grid[2])]
             keep.append((vol, br, outs))
             reqs.append((br.bricks, lut.data_ptr(), vdi.make_camera(cam), n_s, vdi.VDI_GAMMA_SEARCH,
                          [o.struct() for o in outs]))

@@ -46,10 +46,12 @@
 // marches or pixels execute the same instructions and a lane that finishes
 // takes the next pixel.
 //
-// composite_batched_kernel runs many requests (different sizes, K, N_S) in one
-// persistent launch: warps pull (request, 32-pixel batch) items from an atomic
-// counter and run the staged schedule; requests with a direct schedule and
-// the pixels the stage cannot hold follow in composite_batched_direct_kernel.
+// The batched path runs many requests (different sizes, K, N_S) as the pooled
+// staged schedule does: composite_batched_build_kernel pulls (request, 32-pixel
+// batch) items from an atomic counter and builds them into the pool,
+// composite_batched_flat_kernel searches and emits, and requests with a direct
+// schedule (and pixels the stage cannot hold) go to
+// composite_batched_marked_kernel.
 #include <climits>
 
 #include "vdi_device.cuh"
@@ -987,7 +989,6 @@ __global__ void __launch_bounds__(128, NLEV > 2 ? 2 : 3) composite_kernel(const 
 // stage holds are listed for the direct path (a second launch).
 
 constexpr int kStageRMax = 1024;           // records per pixel held by the stage
-constexpr int kStageCap = 2 * kStageRMax;  // piece rows per column (pieces <= 2 R - 1)
 constexpr int kStageWarps = 8;             // warps per CTA
 
 struct StageSmem {
@@ -1314,93 +1315,6 @@ __device__ bool stage_pixel(const PeIn* pe, int k, uint32_t p, StageSmem& S, flo
     return true;
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-// rows ahead of the current one whose lines are requested into L2
-constexpr int kPrefetchRows = 16;
-
-// Phase S: the pieces of one column, streamed with loads two pieces ahead
-// (and L2 prefetches further ahead).
-struct BufSweeper {
-    static constexpr bool kSelectSteps = true;  // branch-free counting steps (see CountVisitorQ)
-    const float4* A;
-    const float2* B;
-    int n;
-    float f0;
-    template <typename V>
-    __device__ __forceinline__ int run(V& visit) const {
-        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-        float2 b0 = make_float2(0.f, 0.f), b1 = b0;
-        if (n > 0) {
-            a0 = __ldcg(A);
-            b0 = __ldcg(B);
-        }
-        if (n > 1) {
-            a1 = __ldcg(A + 32);
-            b1 = __ldcg(B + 32);
-        }
-        float f = f0;
-        for (int j = 0; j < n; ++j) {
-            if ((j & 3) == 0 && j + kPrefetchRows < n) {
-                prefetch_l2(A + (size_t)(j + kPrefetchRows) * 32);
-                prefetch_l2(B + (size_t)(j + kPrefetchRows) * 32);
-            }
-            const float4 a = a0;
-            const float2 b = b0;
-            a0 = a1;
-            b0 = b1;
-            if (j + 2 < n) {
-                a1 = __ldcg(A + (size_t)(j + 2) * 32);
-                b1 = __ldcg(B + (size_t)(j + 2) * 32);
-            }
-            Piece x;
-            x.f = f;
-            x.b = b.x;
-            x.P[0] = a.x;
-            x.P[1] = a.y;
-            x.P[2] = a.z;
-            x.a = a.w;
-            x.lgT = b.y;
-            visit(x);
-            f = b.x;
-        }
-        return n;
-    }
-};
-
-struct StageArgs {
-    float4* bufA;  // per warp: rows x 32 columns
-    float2* bufB;
-    uint32_t* overflow;  // [0]: count, [2..]: entries
-    unsigned int* counter;
-    int rows;  // piece rows per column (at most kStageCap)
-};
-
-// Phase G for the batch's pixels, then Phase S for this lane's pixel.
-// `pixel_ok` etc. are per-lane results for pixel base + lane.
-template <int PREC>
-__device__ __forceinline__ void stage_batch(const PeIn* pe, int k, uint32_t base, uint32_t npix, StageSmem& S,
-                                            float4* wA, float2* wB, int rows, bool& ok, int& n, int& nt, float& f0) {
-    const int lane = threadIdx.x & 31;
-    ok = false;
-    n = nt = 0;
-    f0 = 0.f;
-    for (int col = 0; col < 32; ++col) {
-        const uint32_t p = base + (uint32_t)col;
-        if (p >= npix) break;
-        int pn, pnt;
-        float pf0;
-        const bool pok = stage_pixel<PREC>(pe, k, p, S, wA + col, wB + col, rows, pn, pnt, pf0);
-        if (lane == col) {
-            ok = pok;
-            n = pn;
-            nt = pnt;
-            f0 = pf0;
-        }
-    }
-}
 
 // storage of the pieces of the pixels the lane and pooled staged paths search
 struct PiecePool {
@@ -2047,6 +1961,7 @@ __global__ void __launch_bounds__(kStageWarps * 32, 1) composite_build_kernel(co
 enum : int { kFlatIdle = 0, kFlatFirst = 1, kFlatSearch = 2, kFlatEmit = 3 };
 
 struct FlatLane {
+    const OutDev* out;  // the pixel's output (its request's, in a batch)
     uint32_t p, base, n, j;
     float f, f0;
     int phase;
@@ -2094,41 +2009,6 @@ __device__ __forceinline__ void flat_store(const OutDev& out, uint32_t p, int wr
         out.fb[idx] = make_float2(f, b);
     } else {
         reinterpret_cast<uint4*>(out.rgba)[idx] = f16_pack(f, b, P[0], P[1], P[2], L2);
-    }
-}
-
-// the emission step of EmitVisitor on the lane's supersegment st[0]
-__device__ __forceinline__ void flat_emit_step(FlatLane& L, const Piece& x, const OutDev& out) {
-    CompCountQ& s = L.st[0];
-    const int cap = out.n_s;
-    if (!s.open) {
-        if (x.a > 0.f) {
-            s.P[0] = x.P[0]; s.P[1] = x.P[1]; s.P[2] = x.P[2];
-            s.A = x.a; s.L2 = x.lgT; s.fS = x.f; s.bS = x.b; s.open = true;
-            L.bt = x.b;
-            ++s.cnt;
-        }
-        return;
-    }
-    const float lx = __fsub_rn(x.b, x.f), lS = __fsub_rn(s.bS, s.fS);
-    const float r = (lx > 0.f && lS > 0.f) ? __fmul_rn(lx, rcp_approx(lS)) : 1.f;
-    if (s.cnt < cap && criterion(s.P, s.A, s.L2, r, x.P, L.g2[0])) {
-        if (L.written < cap) {
-            flat_store(out, L.p, L.written, s.fS, L.bt, s.P, s.A, s.L2);
-            ++L.written;
-        }
-        if (x.a > 0.f) {
-            s.P[0] = x.P[0]; s.P[1] = x.P[1]; s.P[2] = x.P[2];
-            s.A = x.a; s.L2 = x.lgT; s.fS = x.f; s.bS = x.b;
-            L.bt = x.b;
-            ++s.cnt;
-        } else {
-            s.open = false;
-        }
-    } else {
-        absorb(s.P, s.A, s.L2, x.P, x.a, x.lgT);
-        s.bS = x.b;
-        if (x.a > 0.f) L.bt = x.b;
     }
 }
 
@@ -2211,20 +2091,41 @@ __device__ __forceinline__ void flat_end_march(FlatLane& L, CountTable& t, const
     }
 }
 
-// The flat search over the listed pixels (list: [count, next-entry counter, pad, pad] then FlatEntry
-// entries; entries whose pixel carries the top bit are left to composite_marked_kernel).
-template <bool CENSUS>
-__global__ void __launch_bounds__(128) composite_flat_kernel(const __grid_constant__ CompArgs a,
-                                                             const __grid_constant__ PiecePool pool,
-                                                             uint32_t* list) {
-    const FlatEntry* entries = reinterpret_cast<const FlatEntry*>(list + 4);
+// Where the flat loop finds its pixels: the list's entries (one request) ...
+struct FlatSrcOne {
+    const FlatEntry* entries;
+    const OutDev* out;
+    const PeIn* pe;
+    int k;
+    __device__ __forceinline__ bool get(uint32_t i, FlatLane& L) const {
+        const FlatEntry en = entries[i];
+        if (en.p & 0x80000000u) return false;  // the direct sweep's
+        L.p = en.p;
+        L.base = en.base;
+        L.n = en.n;
+        L.f0 = en.f0;
+        L.out = out;
+        return true;
+    }
+    __device__ __forceinline__ unsigned long long records(uint32_t p) const {
+        unsigned long long r = 0;
+        for (int e = 0; e < k; ++e) r += __ldg(pe[e].counts + p);
+        return r;
+    }
+};
+
+// The search and emission of the listed pixels, a lane each (list: [count, next-entry counter, ...]
+// then the entries SRC reads).
+template <bool CENSUS, class SRC>
+__device__ __forceinline__ void flat_loop(const SRC& src, const PiecePool& pool, uint32_t* list, int iters,
+                                          unsigned int* status, CompCensus& cs) {
     const uint32_t n_list = list[0];
     const int lane = threadIdx.x & 31;
     FlatLane L;
     L.phase = kFlatIdle;
+    L.out = nullptr;
     CountTable t;
     t.n = 0;
-    CompCensus cs;
     bool exhausted = false;
     float4 cA = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 cB = make_float2(0.f, 0.f);
@@ -2240,18 +2141,13 @@ __global__ void __launch_bounds__(128) composite_flat_kernel(const __grid_consta
                 bool started = false;
                 uint32_t i = first + __popc(need & ((1u << lane) - 1u));
                 while (i < n_list) {
-                    const FlatEntry en = entries[i];
-                    if (!(en.p & 0x80000000u)) {  // (entries with the top bit are the direct sweep's)
-                        L.p = en.p;
-                        L.base = en.base;
-                        L.n = en.n;
-                        L.f0 = en.f0;
+                    if (src.get(i, L)) {
                         L.phase = kFlatFirst;
                         t.n = 0;
                         flat_start_count(L, 0.f, 2.f);
                         if (CENSUS) {
                             cs.pixels += 1;
-                            for (int e = 0; e < a.k; ++e) cs.records += __ldg(a.pe[e].counts + L.p);
+                            cs.records += src.records(L.p);
                         }
                         started = true;
                         break;
@@ -2280,16 +2176,43 @@ __global__ void __launch_bounds__(128) composite_flat_kernel(const __grid_consta
             cA = pool.A[L.base + L.j + 1];
             cB = pool.B[L.base + L.j + 1];
         }
-        if (L.phase == kFlatEmit) {
-            flat_emit_step(L, x, a.out);
-        } else {
-            L.nt += x.a > 0.f;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) cq_step_select(L.st[q], x, L.g2[q]);
+        // one instruction stream for counting and emitting lanes: candidate 0 carries the budget (none
+        // while counting) and, emitting, writes the supersegment a termination closes -- EmitVisitor's
+        // decisions, in select form; candidates 1 and 2 only count
+        {
+            const bool emitting = L.phase == kFlatEmit;
+            const int cap = emitting ? L.out->n_s : INT_MAX;
+            CompCountQ& s = L.st[0];
+            float q = 0.f;
+            const bool crit = s.open && s.cnt < cap &&
+                              criterion_q(s.P, s.A, s.L2, piece_ratio(s, x), x.P, L.g2[0], q);
+            if (emitting && crit && L.written < cap) {
+                flat_store(*L.out, L.p, L.written, s.fS, L.bt, s.P, s.A, s.L2);
+                ++L.written;
+            }
+            s.qhi = crit ? fminf(s.qhi, q) : s.qhi;
+            s.qlo = (s.open && !crit) ? fmaxf(s.qlo, q) : s.qlo;
+            const bool opaque = x.a > 0.f;
+            const bool fresh = opaque && (!s.open || crit);
+            const bool absorbing = s.open && !crit;
+            L.bt = (fresh || (absorbing && opaque)) ? x.b : L.bt;
+            apply_step(s, x, StepSel{fresh, crit && !opaque, absorbing});
+            L.nt += opaque;
+            cq_step_select(L.st[1], x, L.g2[1]);
+            cq_step_select(L.st[2], x, L.g2[2]);
         }
         L.f = x.b;
-        if (++L.j == L.n) flat_end_march<CENSUS>(L, t, a.out, a.iters, a.status, cs);
+        if (++L.j == L.n) flat_end_march<CENSUS>(L, t, *L.out, iters, status, cs);
     }
+}
+
+template <bool CENSUS>
+__global__ void __launch_bounds__(128) composite_flat_kernel(const __grid_constant__ CompArgs a,
+                                                             const __grid_constant__ PiecePool pool,
+                                                             uint32_t* list) {
+    CompCensus cs;
+    const FlatSrcOne src{reinterpret_cast<const FlatEntry*>(list + 4), &a.out, a.pe, a.k};
+    flat_loop<CENSUS>(src, pool, list, a.iters, a.status, cs);
     if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
 }
 
@@ -2323,61 +2246,122 @@ __device__ __forceinline__ int request_of(const BatchArgs& a, uint32_t item) {
     return lo;
 }
 
-// Items are (request, 32-pixel batch).  Requests with the staged schedule run
-// phases G and S; the others, and the pixels the stage cannot hold, are
-// listed (request << 32 | pixel) for the direct kernel that follows.
+// Pooled batched path: composite_batched_build_kernel takes (request,
+// 32-pixel batch) items of a chunk from an atomic counter and builds each
+// pixel's pieces into the pool as composite_build_kernel does (requests with
+// a direct schedule, and pixels the stage cannot hold, are listed for the
+// direct sweep); composite_batched_flat_kernel searches and emits the listed
+// pixels, a lane each, each into its request's output; composite_batched_
+// marked_kernel sweeps the pixels listed for the direct path.
+struct BatchEntry {
+    uint32_t p, base, n;
+    float f0;
+    uint32_t req, pad0, pad1, pad2;
+};
+
+struct BatchBuildArgs {
+    unsigned int* counter;  // item counter
+    uint32_t* list;         // [0] entries, [1] next entry of the flat pass, [2] pool pieces taken; entries from word 8
+    PiecePool pool;
+    uint32_t item0, item1;  // the chunk's items
+};
+
+__device__ __forceinline__ void batch_push(uint32_t* list, bool flag, const BatchEntry& en) {
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(list, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (flag) reinterpret_cast<BatchEntry*>(list + 8)[base + __popc(m & ((1u << lane) - 1u))] = en;
+}
+
 template <int PREC>
-__global__ void __launch_bounds__(kStageWarps * 32, 1) composite_batched_kernel(const __grid_constant__ BatchArgs a,
-                                                                            const __grid_constant__ StageArgs sa) {
+__global__ void __launch_bounds__(kStageWarps * 32, 1) composite_batched_build_kernel(
+    const __grid_constant__ BatchArgs a, const __grid_constant__ BatchBuildArgs bb) {
     extern __shared__ __align__(16) unsigned char stage_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     StageSmem& S = reinterpret_cast<StageSmem*>(stage_smem)[warp];
-    const size_t gw = (size_t)blockIdx.x * kStageWarps + warp;
-    float4* wA = sa.bufA + gw * (size_t)sa.rows * 32;
-    float2* wB = sa.bufB + gw * (size_t)sa.rows * 32;
-    unsigned long long* list = reinterpret_cast<unsigned long long*>(sa.overflow + 2);
     while (true) {
         uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(sa.counter, 1u);
+        if (lane == 0) item = bb.item0 + atomicAdd(bb.counter, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= a.total_items) break;
+        if (item >= bb.item1) break;
         const int rq = request_of(a, item);
         const ReqDev& r = a.reqs[rq];
         const uint32_t base = (item - r.item_begin) * 32u;
-        const uint32_t p = base + (uint32_t)lane;
-        bool ok = false;
-        int n = 0, nt = 0;
-        float f0 = 0.f;
-        if (r.schedule == VDI_SCHED_STAGED)
-            stage_batch<PREC>(a.pes + r.pe_begin, r.k, base, r.npix, S, wA, wB, sa.rows, ok, n, nt, f0);
-        if (p < r.npix) {
-            if (ok) {
-                BufSweeper sw;
-                sw.A = wA + lane;
-                sw.B = wB + lane;
-                sw.n = n;
-                sw.f0 = f0;
-                composite_search_emit<2, false>(sw, r.out, a.iters, a.status, p, nullptr);
-            } else {
-                const uint32_t slot = atomicAdd(sa.overflow, 1u);
-                list[slot] = ((unsigned long long)rq << 32) | p;
+        BatchEntry mine{0u, 0u, 0u, 0.f, (uint32_t)rq, 0u, 0u, 0u};
+        bool have = false;
+        if (r.schedule == VDI_SCHED_STAGED) {
+            for (int col = 0; col < 32; ++col) {
+                const uint32_t p = base + (uint32_t)col;
+                if (p >= r.npix) break;
+                PoolRun run{bb.list + 2, bb.pool.cap, 0u};
+                int n = 0, nt = 0;
+                float f0 = 0.f;
+                const bool ok = stage_pixel<PREC, true>(a.pes + r.pe_begin, r.k, p, S, bb.pool.A, bb.pool.B,
+                                                        0x7FFFFFFF, n, nt, f0, &run);
+                if (lane == col) {
+                    if (!ok || n < 0) {
+                        mine.p = p | 0x80000000u;
+                        have = true;
+                    } else if (n == 0) {
+                        finish_pixel(r.out, p, 0, 0.f);  // no record: an empty list
+                    } else {
+                        mine.p = p;
+                        mine.base = run.base;
+                        mine.n = (uint32_t)n;
+                        mine.f0 = f0;
+                        have = true;
+                    }
+                }
             }
+        } else {
+            const uint32_t p = base + (uint32_t)lane;
+            have = p < r.npix;
+            mine.p = p | 0x80000000u;
         }
-        __syncwarp();
+        batch_push(bb.list, have, mine);
     }
 }
 
+struct FlatSrcBatch {
+    const BatchEntry* entries;
+    const ReqDev* reqs;
+    __device__ __forceinline__ bool get(uint32_t i, FlatLane& L) const {
+        const BatchEntry en = entries[i];
+        if (en.p & 0x80000000u) return false;  // the direct sweep's
+        L.p = en.p;
+        L.base = en.base;
+        L.n = en.n;
+        L.f0 = en.f0;
+        L.out = &reqs[en.req].out;
+        return true;
+    }
+    __device__ __forceinline__ unsigned long long records(uint32_t) const { return 0; }
+};
+
+__global__ void __launch_bounds__(128) composite_batched_flat_kernel(const __grid_constant__ BatchArgs a,
+                                                                     const __grid_constant__ PiecePool pool,
+                                                                     uint32_t* list) {
+    CompCensus cs;
+    const FlatSrcBatch src{reinterpret_cast<const BatchEntry*>(list + 8), a.reqs};
+    flat_loop<false>(src, pool, list, a.iters, a.status, cs);
+}
+
 template <int P, int PREC>
-__global__ void __launch_bounds__(128) composite_batched_direct_kernel(const __grid_constant__ BatchArgs a,
-                                                                       const uint32_t* overflow) {
+__global__ void __launch_bounds__(128) composite_batched_marked_kernel(const __grid_constant__ BatchArgs a,
+                                                                       const uint32_t* __restrict__ list) {
     extern __shared__ uint32_t smem[];
-    const uint32_t n = *overflow;
-    const unsigned long long* list = reinterpret_cast<const unsigned long long*>(overflow + 2);
+    const uint32_t n = *list;
+    const BatchEntry* entries = reinterpret_cast<const BatchEntry*>(list + 8);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < n; i += gridDim.x * blockDim.x) {
-        if (i < n) {
-            const unsigned long long v = list[i];
-            const ReqDev& r = a.reqs[(int)(v >> 32)];
-            composite_pixel<0, P, 2, PREC>(a.pes + r.pe_begin, r.k, r.out, a.iters, a.status, (uint32_t)v, smem);
+        const BatchEntry en = i < n ? entries[i] : BatchEntry{0u, 0u, 0u, 0.f, 0u, 0u, 0u, 0u};
+        if (en.p & 0x80000000u) {
+            const ReqDev& r = a.reqs[en.req];
+            composite_pixel<0, P, 2, PREC>(a.pes + r.pe_begin, r.k, r.out, a.iters, a.status, en.p & 0x7FFFFFFFu,
+                                           smem);
         }
     }
 }
@@ -2422,14 +2406,6 @@ static size_t stage_ctas(uint64_t batches) {
     return (size_t)(need < sms ? (need > 0 ? need : 1) : sms);
 }
 
-static size_t stage_list_bytes(uint64_t entries, size_t entry_bytes) {
-    return align_up(8 + entries * entry_bytes, 256);
-}
-
-static size_t stage_buffer_bytes(size_t ctas, int rows) {
-    return ctas * kStageWarps * (size_t)rows * 32 * (sizeof(float4) + sizeof(float2));
-}
-
 // pixels per chunk of the pooled staged path that the queried workspace holds at the stage's worst case
 constexpr uint64_t kPoolChunkPixels = 131072;
 
@@ -2444,23 +2420,6 @@ size_t composite_workspace_bytes(int w, int h) {
     return pooled > lane ? pooled : lane;
 }
 
-// Staged-path layout in the workspace; rows = 0 when the workspace holds no
-// piece buffer of at least 2 rows.
-static StageArgs stage_args(void* workspace, size_t ws_bytes, uint64_t npix, size_t entry_bytes, size_t ctas) {
-    char* base = static_cast<char*>(workspace);
-    StageArgs sa;
-    sa.counter = reinterpret_cast<unsigned int*>(base + kWsHeader);
-    sa.overflow = reinterpret_cast<uint32_t*>(base + kWsHeader + 256);
-    const size_t fixed = kWsHeader + 256 + stage_list_bytes(npix, entry_bytes);
-    const size_t per_row = stage_buffer_bytes(ctas, 1);
-    size_t rows = ws_bytes > fixed ? (ws_bytes - fixed) / per_row : 0;
-    if (rows > (size_t)kStageCap) rows = kStageCap;
-    sa.rows = rows >= 2 ? (int)rows : 0;
-    char* buf = base + fixed;
-    sa.bufA = reinterpret_cast<float4*>(buf);
-    sa.bufB = reinterpret_cast<float2*>(buf + ctas * kStageWarps * (size_t)sa.rows * 32 * sizeof(float4));
-    return sa;
-}
 
 template <int KMAX, int P, int NLEV, int PREC>
 static cudaError_t launch_cs(bool census, unsigned blocks, int threads, cudaStream_t st, const CompArgs& a) {
@@ -2702,44 +2661,96 @@ vdi_status batch_table_pack(const vdi_request* reqs, int n, void* host_table, si
     return VDI_OK;
 }
 
-size_t batched_workspace_bytes(const void* host_table) {
-    const BatchHeader* hd = static_cast<const BatchHeader*>(host_table);
-    return kWsHeader + 256 + stage_list_bytes(hd->total_pixels, 8) +
-           stage_buffer_bytes(stage_ctas(hd->total_items), kStageCap);
+// Pooled batched path: pieces a request's pixel is expected to need (its K lists of at most N_S records
+// cut into at most 2 K N_S - 1 pieces, at most the stage's), and the workspace: [header][counter]
+// [list: 8 words, kBatchListCap entries at most][pool]
+constexpr uint64_t kBatchListCap = 1u << 22;
+constexpr uint64_t kBatchPoolCap = 1u << 28;
+
+static uint64_t batch_pixel_pieces(const ReqDev& r) {
+    const uint64_t est = 2ull * (uint64_t)r.k * (uint64_t)(r.out.n_s > 0 ? r.out.n_s : 1) + 1;
+    return est < kPoolPiecesPerPixel ? est : kPoolPiecesPerPixel;
 }
 
-template <int P, int PREC>
-static cudaError_t launch_batched_direct(const BatchArgs& a, const uint32_t* overflow, uint64_t pixels,
-                                         cudaStream_t st) {
-    const size_t sm = heads_smem_bytes<P>(128);
-    cudaError_t e = cudaFuncSetAttribute(composite_batched_direct_kernel<P, PREC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    uint64_t blocks = (pixels + 127) / 128;
-    const uint64_t cap = (uint64_t)device_sms() * 8u;
-    if (blocks > cap) blocks = cap;
-    composite_batched_direct_kernel<P, PREC><<<(unsigned)blocks, 128, sm, st>>>(a, overflow);
-    return cudaGetLastError();
+static size_t batch_list_bytes(const BatchHeader* hd) {
+    const uint64_t n = hd->total_pixels < kBatchListCap ? hd->total_pixels : kBatchListCap;
+    return align_up(32 + n * sizeof(BatchEntry), 256);
+}
+
+size_t batched_workspace_bytes(const void* host_table) {
+    const BatchHeader* hd = static_cast<const BatchHeader*>(host_table);
+    const ReqDev* rd = reinterpret_cast<const ReqDev*>(static_cast<const char*>(host_table) + hd->reqs_off);
+    uint64_t est = 0;
+    for (uint32_t q = 0; q < hd->n; ++q) est += (uint64_t)rd[q].npix * batch_pixel_pieces(rd[q]);
+    if (est > kBatchPoolCap) est = kBatchPoolCap;
+    if (est < kPoolPiecesPerPixel * 32) est = kPoolPiecesPerPixel * 32;
+    return kWsHeader + 256 + batch_list_bytes(hd) + (size_t)est * (sizeof(float4) + sizeof(float2));
 }
 
 template <int PREC>
-static cudaError_t launch_batched(const BatchArgs& a, const BatchHeader* hd, void* workspace, size_t ws_bytes,
-                                  cudaStream_t st) {
-    const size_t ctas = stage_ctas(hd->total_items);
-    const StageArgs sa = stage_args(workspace, ws_bytes, hd->total_pixels, 8, ctas);
-    if (sa.rows == 0) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(sa.counter, 0, 256 + 8, st);
-    if (e != cudaSuccess) return e;
+static cudaError_t launch_batched(const BatchArgs& a, const BatchHeader* hd, const ReqDev* rd, void* workspace,
+                                  size_t ws_bytes, cudaStream_t st) {
+    char* base = static_cast<char*>(workspace);
+    const size_t fixed = kWsHeader + 256 + batch_list_bytes(hd);
+    if (ws_bytes < fixed) return cudaErrorInvalidValue;
+    uint64_t cap = (ws_bytes - fixed) / (sizeof(float4) + sizeof(float2));
+    if (cap > 0x7FFFFFFFu) cap = 0x7FFFFFFFu;
+    if (cap < kPoolPiecesPerPixel * 32) return cudaErrorInvalidValue;  // one item's worst case
+    const uint64_t list_cap = hd->total_pixels < kBatchListCap ? hd->total_pixels : kBatchListCap;
+    BatchBuildArgs bb;
+    bb.counter = reinterpret_cast<unsigned int*>(base + kWsHeader);
+    bb.list = reinterpret_cast<uint32_t*>(base + kWsHeader + 256);
+    bb.pool.cap = (uint32_t)cap;
+    bb.pool.A = reinterpret_cast<float4*>(base + fixed);
+    bb.pool.B = reinterpret_cast<float2*>(base + fixed + cap * sizeof(float4));
     const size_t sm = kStageWarps * sizeof(StageSmem);
-    e = cudaFuncSetAttribute(composite_batched_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    composite_batched_kernel<PREC><<<(unsigned)ctas, kStageWarps * 32, sm, st>>>(a, sa);
-    e = cudaGetLastError();
+    cudaError_t e = cudaFuncSetAttribute(composite_batched_build_kernel<PREC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int P = tree_leaves((int)hd->max_k);
-    if (P == 16) return launch_batched_direct<16, PREC>(a, sa.overflow, hd->total_pixels, st);
-    if (P == 32) return launch_batched_direct<32, PREC>(a, sa.overflow, hd->total_pixels, st);
-    return launch_batched_direct<64, PREC>(a, sa.overflow, hd->total_pixels, st);
+    const size_t smd = P == 16 ? heads_smem_bytes<16>(128) : (P == 32 ? heads_smem_bytes<32>(128)
+                                                                        : heads_smem_bytes<64>(128));
+    auto km = P == 16 ? composite_batched_marked_kernel<16, PREC>
+                      : (P == 32 ? composite_batched_marked_kernel<32, PREC> : composite_batched_marked_kernel<64, PREC>);
+    e = cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, composite_batched_flat_kernel, 128, 0);
+    if (e != cudaSuccess) return e;
+    // chunks of whole items whose expected pieces fit the pool and whose pixels fit the list
+    uint32_t item = 0;
+    int q = 0;
+    while (item < hd->total_items) {
+        const uint32_t item0 = item;
+        uint64_t pieces = 0, pixels = 0;
+        while (item < hd->total_items) {
+            while (q + 1 < (int)hd->n && rd[q + 1].item_begin <= item) ++q;
+            const uint64_t px = 32;
+            const uint64_t pc = px * batch_pixel_pieces(rd[q]);
+            if (item > item0 && (pieces + pc > cap || pixels + px > list_cap)) break;
+            pieces += pc;
+            pixels += px;
+            ++item;
+        }
+        BatchBuildArgs c = bb;
+        c.item0 = item0;
+        c.item1 = item;
+        e = cudaMemsetAsync(bb.counter, 0, 256, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bb.list, 0, 32, st);
+        if (e != cudaSuccess) return e;
+        composite_batched_build_kernel<PREC><<<(unsigned)stage_ctas(item - item0), kStageWarps * 32, sm, st>>>(a, c);
+        uint64_t b = (uint64_t)device_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
+        const uint64_t need = (pixels + 127) / 128;
+        if (b > need) b = need > 0 ? need : 1;
+        composite_batched_flat_kernel<<<(unsigned)b, 128, 0, st>>>(a, bb.pool, bb.list);
+        unsigned b3 = (unsigned)((pixels + 127) / 128);
+        const unsigned cap3 = (unsigned)device_sms() * 2u;
+        if (b3 > cap3) b3 = cap3;
+        km<<<b3, 128, smd, st>>>(a, bb.list);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 vdi_status launch_composite_batched(const void* dev_table, const void* host_table, int iters, unsigned int* status,
@@ -2753,8 +2764,10 @@ vdi_status launch_composite_batched(const void* dev_table, const void* host_tabl
     a.total_items = hd->total_items;
     a.status = status;
     a.iters = iters;
-    const cudaError_t e = hd->prec_in == VDI_PREC_F32 ? launch_batched<VDI_PREC_F32>(a, hd, workspace, ws_bytes, st)
-                                                       : launch_batched<VDI_PREC_F16>(a, hd, workspace, ws_bytes, st);
+    const ReqDev* rd = reinterpret_cast<const ReqDev*>(static_cast<const char*>(host_table) + hd->reqs_off);
+    const cudaError_t e = hd->prec_in == VDI_PREC_F32
+                              ? launch_batched<VDI_PREC_F32>(a, hd, rd, workspace, ws_bytes, st)
+                              : launch_batched<VDI_PREC_F16>(a, hd, rd, workspace, ws_bytes, st);
     return cuda_check(e, "composite_batched launch");
 }
 

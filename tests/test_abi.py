@@ -195,7 +195,7 @@ def test_pipeline_arena_layout(vdi):
     b.boxes[1] = vdi.vdi_box((0, 0, 0), (33, 16, 8))  # past the last cell
     assert vdi.vdi_pipeline_arena_bytes(b) == 0
     b = _pipeline_desc(vdi)
-    b.params = vdi.make_params(schedule=5)
+    b.params = vdi.make_params(schedule=vdi.VDI_SCHED_LANE + 1)  # no such schedule
     assert vdi.vdi_pipeline_arena_bytes(b) == 0
 
 

@@ -296,3 +296,70 @@ def test_learned_generation_is_exact_and_saves_work():
     err1, cmax1 = count_error(ls, l1)
     assert cmax1 <= n_s and c1[4] < cs[4], (c1, cs)
     print(f"learned single pass: count error {err1:.4f}, searched rays {c1[4]} vs {cs[4]}, marches {c1[2]}")
+
+
+def test_learned_config_sampled_rays():
+    # the learned-gamma workload at full size: 1024^3 uint16 (128 blobs, 4 octaves), K = 16 bricks, 1920 x
+    # 1080, N_S = 32, gamma from the committed model; the composited VDI, flattened from the generating view,
+    # must equal the FP64 oracle's DVR (whatever the gammas, sec. 2.3) on sampled pixels within 1e-5, every
+    # list stays within the budget, and the count error against the search stays within 5%
+    import json
+
+    vdi, torch = _vdi()
+    from synth import gpu_volume
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    ckpt = os.path.join(here, "..", "paper_2206_14503_gb300", "models", "gamma_ns32_k16.ckpt")
+    offset = json.load(open(os.path.splitext(ckpt)[0] + ".json"))["offset"]
+    dims = (1024, 1024, 1024)
+    W, H, n_s = 1920, 1080, 32
+    npix = W * H
+    torch.cuda.empty_cache()
+    if torch.cuda.mem_get_info()[0] < 80e9:
+        pytest.skip("needs 80 GB of free device memory")
+    vol_d = gpu_volume.volume(dims, 128, 4, synth.SEED_VOLUME + 3)
+    boxes = vdi.vdi_split_boxes(dims, (4, 2, 2))
+    k = len(boxes)
+    br = vdi.Bricks(vol_d, dims, boxes)
+    lut = synth.transfer_function(synth.SEED_TF)
+    lut_d = to_dev(lut)
+    cam = synth.orbit(dims, 16, W, H, synth.SEED_ORBIT)[3]
+    c = vdi.make_camera(cam)
+    model = torch.zeros(vdi.vdi_model_bytes(), dtype=torch.uint8, device="cuda")
+    vdi.check(vdi.vdi_model_load(model.data_ptr(), ckpt), "model load")
+    cap = npix * n_s // 4
+    outs_l = [vdi.Compact(npix, cap) for _ in range(k)]
+    outs_s = [vdi.Compact(npix, 1) for _ in range(k)]
+    lws = vdi.Workspace(vdi.vdi_learned_workspace(k, W, H))
+    gws = vdi.Workspace(vdi.vdi_generate_workspace(k, W, H))
+    vdi.check(vdi.vdi_choose_gamma_learned(br.bricks, lut_d.data_ptr(), c, n_s, model.data_ptr(), offset,
+                                           [o.struct() for o in outs_l], vdi.make_params(), lws.ptr, lws.nbytes),
+              "learned")
+    vdi.check(vdi.vdi_generate(br.bricks, lut_d.data_ptr(), c, n_s, vdi.VDI_GAMMA_CHOSEN,
+                               [o.struct() for o in outs_l], vdi.make_params(), gws.ptr, gws.nbytes), "emit")
+    vdi.check(gws.status(), "emit status")
+    vdi.check(vdi.vdi_choose_gamma(br.bricks, lut_d.data_ptr(), c, n_s, vdi.VDI_GAMMA_SEARCH,
+                                   [o.struct() for o in outs_s], vdi.make_params(), gws.ptr, gws.nbytes), "search")
+    torch.cuda.synchronize()
+    cl = torch.stack([o.counts for o in outs_l]).long()
+    cs = torch.stack([o.counts for o in outs_s]).long()
+    nz = cs > 0
+    err = float((cl - cs).abs()[nz].sum()) / max(float(cs[nz].sum()), 1.0)
+    assert int(cl.max()) <= n_s and err <= 0.05, err
+    del br, outs_s
+    reg = vdi.Regular(npix, n_s)
+    wsc = vdi.Workspace(vdi.vdi_composite_workspace(k, W, H, n_s))
+    vdi.check(vdi.vdi_composite([o.struct() for o in outs_l], W, H, reg.struct(), vdi.make_params(), wsc.ptr,
+                                wsc.nbytes), "composite")
+    vdi.check(wsc.status(), "composite status")
+    img = torch.zeros((npix, 4), dtype=torch.float32, device="cuda")
+    vdi.check(vdi.vdi_render_view(reg.struct(), W, H, c, None, img.data_ptr()), "flatten")
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(44)
+    pix = np.sort(rng.choice(npix, 300, replace=False)).astype(np.int32)
+    vol = vol_d.cpu().numpy().view(np.uint16).reshape(dims[2], dims[1], dims[0])
+    ref = oracle.dvr(vol, lut, cam, 0.5, 1.0, pixels=pix)
+    got = img.cpu().numpy().astype(np.float64)[pix]
+    e_img = float(np.abs(got - ref).max())
+    print(f"learned 1024^3: count error {err:.4f}, flattened VDI vs FP64 DVR on 300 pixels {e_img:.2e}")
+    assert e_img <= 1e-5, e_img
