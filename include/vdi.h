@@ -197,7 +197,8 @@ vdi_status vdi_brick_build(const void* volume, vdi_voltype type, const int32_t d
 /* Workspace bytes for vdi_generate / vdi_choose_gamma with k PEs of w x h on
  * the current device: a status header, a work counter, the prefix sum's
  * partial sums (8 bytes per 4096 pixels per PE) and a sample cache (1024
- * entries of 8 bytes per resident thread: about 640 MB on a 152-SM GB300)
+ * entries of 8 bytes per resident thread: 152 SMs x 12 CTAs x 64 threads,
+ * about 0.96 GB, on a GB300)
  * that lets the gamma search run over each ray's
  * cached non-transparent samples instead of re-sampling the volume.  Any
  * workspace of at least 512 + 8 k ceil(w h / 4096) bytes is accepted; without

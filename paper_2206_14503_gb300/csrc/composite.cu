@@ -1960,6 +1960,10 @@ __global__ void __launch_bounds__(kStageWarps * 32, 1) composite_build_kernel(co
 // ---------------------------------------------------------------------------
 enum : int { kFlatIdle = 0, kFlatFirst = 1, kFlatSearch = 2, kFlatEmit = 3 };
 
+#ifndef VDI_FLAT_END_BATCH
+#define VDI_FLAT_END_BATCH 16
+#endif
+
 struct FlatLane {
     const OutDev* out;  // the pixel's output (its request's, in a batch)
     uint32_t p, base, n, j;
@@ -2157,8 +2161,19 @@ __device__ __forceinline__ void flat_loop(const SRC& src, const PiecePool& pool,
                 if (!started) exhausted = true;
             }
         }
-        if (!__any_sync(0xffffffffu, L.phase != kFlatIdle)) break;
-        if (L.phase == kFlatIdle) continue;
+        const bool active = L.phase != kFlatIdle;
+        const unsigned act = __ballot_sync(0xffffffffu, active);
+        if (!act) break;
+        // a lane at the end of its march waits until VDI_FLAT_END_BATCH lanes (or all active ones) are
+        // there: the end of a march (table updates, the replay of bisection levels, the next march's
+        // candidates) runs once for all of them instead of once per lane while the others idle
+        const bool at_end = active && L.j == L.n;
+        const unsigned pend = __ballot_sync(0xffffffffu, at_end);
+        if (pend != 0u && (pend == act || __popc(pend) >= VDI_FLAT_END_BATCH)) {
+            if (at_end) flat_end_march<CENSUS>(L, t, *L.out, iters, status, cs);
+            continue;
+        }
+        if (!active || at_end) continue;
         // one piece of the lane's march
         if (L.j == 0) {
             cA = pool.A[L.base];
@@ -2202,7 +2217,7 @@ __device__ __forceinline__ void flat_loop(const SRC& src, const PiecePool& pool,
             cq_step_select(L.st[2], x, L.g2[2]);
         }
         L.f = x.b;
-        if (++L.j == L.n) flat_end_march<CENSUS>(L, t, *L.out, iters, status, cs);
+        ++L.j;
     }
 }
 
