@@ -2134,7 +2134,8 @@ __device__ __forceinline__ void flat_loop(const SRC& src, const PiecePool& pool,
     float4 cA = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 cB = make_float2(0.f, 0.f);
     while (true) {
-        // idle lanes take the next entries, one atomic per warp
+        // idle lanes take the next entries, one atomic per warp (in a list sorted by piece count, the
+        // entries one fetch hands to a warp's lanes have nearly equal counts)
         const unsigned need = __ballot_sync(0xffffffffu, L.phase == kFlatIdle && !exhausted);
         if (need) {
             const int leader = __ffs(need) - 1;
@@ -2142,28 +2143,26 @@ __device__ __forceinline__ void flat_loop(const SRC& src, const PiecePool& pool,
             if (lane == leader) first = atomicAdd(list + 1, (uint32_t)__popc(need));
             first = __shfl_sync(0xffffffffu, first, leader);
             if ((need >> lane) & 1u) {
-                bool started = false;
-                uint32_t i = first + __popc(need & ((1u << lane) - 1u));
-                while (i < n_list) {
-                    if (src.get(i, L)) {
-                        L.phase = kFlatFirst;
-                        t.n = 0;
-                        flat_start_count(L, 0.f, 2.f);
-                        if (CENSUS) {
-                            cs.pixels += 1;
-                            cs.records += src.records(L.p);
-                        }
-                        started = true;
-                        break;
+                const uint32_t idx = first + (uint32_t)__popc(need & ((1u << lane) - 1u));
+                if (idx >= n_list) {
+                    exhausted = true;
+                } else if (src.get(idx, L)) {  // (a marked entry leaves the lane idle: it takes another)
+                    L.phase = kFlatFirst;
+                    t.n = 0;
+                    flat_start_count(L, 0.f, 2.f);
+                    if (CENSUS) {
+                        cs.pixels += 1;
+                        cs.records += src.records(L.p);
                     }
-                    i = atomicAdd(list + 1, 1u);
                 }
-                if (!started) exhausted = true;
             }
         }
         const bool active = L.phase != kFlatIdle;
         const unsigned act = __ballot_sync(0xffffffffu, active);
-        if (!act) break;
+        if (!act) {
+            if (__all_sync(0xffffffffu, exhausted)) break;
+            continue;  // lanes that drew a marked entry draw again
+        }
         // a lane at the end of its march waits until VDI_FLAT_END_BATCH lanes (or all active ones) are
         // there: the end of a march (table updates, the replay of bisection levels, the next march's
         // candidates) runs once for all of them instead of once per lane while the others idle
@@ -2229,6 +2228,120 @@ __global__ void __launch_bounds__(128) composite_flat_kernel(const __grid_consta
     const FlatSrcOne src{reinterpret_cast<const FlatEntry*>(list + 4), &a.out, a.pe, a.k};
     flat_loop<CENSUS>(src, pool, list, a.iters, a.status, cs);
     if (CENSUS) census_flush(cs, reinterpret_cast<WsHeader*>(a.status)->counters);
+}
+
+// ---------------------------------------------------------------------------
+// Order of the search pass: the listed pixels sorted by piece count, longest
+// first (a counting sort into a second list with the same header).  A warp's
+// lanes then take pixels of (nearly) equal piece counts, so their marches end
+// together and no lane waits for the others at the end of a march; the
+// longest pixels start first, so the last wave holds the shortest.  The order
+// of pixels with equal counts is that of the atomics, which is free to vary:
+// each pixel's result is independent of when it runs.  Marked pixels (the
+// direct sweep's) stay out of the sorted list.
+// ---------------------------------------------------------------------------
+constexpr int kSortBins = 2048;
+
+__device__ __forceinline__ uint32_t sort_bin(uint32_t n) {
+    return (uint32_t)(kSortBins - 1) - (n < (uint32_t)(kSortBins - 1) ? n : (uint32_t)(kSortBins - 1));
+}
+
+// hist[b] += entries of bin b (hist zeroed by the caller)
+template <class E, int HW>
+__global__ void __launch_bounds__(256) list_hist_kernel(const uint32_t* __restrict__ list, uint32_t* hist) {
+    __shared__ uint32_t h[kSortBins];
+    for (int i = threadIdx.x; i < kSortBins; i += blockDim.x) h[i] = 0u;
+    __syncthreads();
+    const uint32_t n = list[0];
+    const E* en = reinterpret_cast<const E*>(list + HW);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const E e = en[i];
+        if (!(e.p & 0x80000000u)) atomicAdd(&h[sort_bin(e.n)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSortBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// hist -> exclusive offsets (in place); the sorted list's header: [0] entries, [1] next entry = 0
+__global__ void __launch_bounds__(1024) list_offsets_kernel(uint32_t* hist, uint32_t* sorted) {
+    __shared__ uint32_t wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kPer = kSortBins / 1024;
+    uint32_t v[kPer], s = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        v[q] = hist[tid * kPer + q];
+        s += v[q];
+    }
+    const uint32_t incl = warp_incl_scan_u32(s);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = warp_incl_scan_u32(wsum[lane]);
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t ex = (warp > 0 ? wsum[warp - 1] : 0u) + incl - s;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        hist[tid * kPer + q] = ex;
+        ex += v[q];
+    }
+    if (tid == 0) {
+        sorted[0] = wsum[31];
+        sorted[1] = 0u;
+    }
+}
+
+// every unmarked entry to its bin's next slot (one atomic per bin and warp)
+template <class E, int HW>
+__global__ void __launch_bounds__(256) list_scatter_kernel(const uint32_t* __restrict__ list, uint32_t* pos,
+                                                           uint32_t* sorted) {
+    const uint32_t n = list[0];
+    const E* en = reinterpret_cast<const E*>(list + HW);
+    E* out = reinterpret_cast<E*>(sorted + HW);
+    const int lane = threadIdx.x & 31;
+    for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+        const uint32_t i = i0 + threadIdx.x;
+        E e{};
+        bool take = false;
+        if (i < n) {
+            e = en[i];
+            take = !(e.p & 0x80000000u);
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, take);
+        if (take) {
+            const uint32_t b = sort_bin(e.n);
+            const unsigned grp = __match_any_sync(act, b);
+            const int leader = __ffs(grp) - 1;
+            uint32_t slot = 0;
+            if (lane == leader) slot = atomicAdd(&pos[b], (uint32_t)__popc(grp));
+            slot = __shfl_sync(grp, slot, leader) + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+            out[slot] = e;
+        }
+    }
+}
+
+static int device_sms();
+
+// bytes of the sort's scratch: the histogram / offsets
+constexpr size_t kSortScratch = kSortBins * sizeof(uint32_t);
+
+// sorts list (HW header words, entries E) into sorted; hist: kSortScratch bytes
+template <class E, int HW>
+static cudaError_t launch_sort(const uint32_t* list, uint32_t* sorted, uint32_t* hist, uint64_t max_entries,
+                               cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(hist, 0, kSortScratch, st);
+    if (e != cudaSuccess) return e;
+    uint64_t b = (max_entries + 255) / 256;
+    const uint64_t cap = (uint64_t)device_sms() * 4u;
+    if (b > cap) b = cap;
+    if (b == 0) b = 1;
+    list_hist_kernel<E, HW><<<(unsigned)b, 256, 0, st>>>(list, hist);
+    list_offsets_kernel<<<1, 1024, 0, st>>>(hist, sorted);
+    list_scatter_kernel<E, HW><<<(unsigned)b, 256, 0, st>>>(list, hist, sorted);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -2430,8 +2543,9 @@ size_t composite_workspace_bytes(int w, int h) {
     // pooled staged path: a chunk of up to kPoolChunkPixels pixels, each with room for the stage's pieces
     const uint64_t chunk = npix < kPoolChunkPixels ? npix : kPoolChunkPixels;
     const size_t pooled = kWsHeader + 512 + (size_t)chunk * (sizeof(FlatEntry) + 2 * kStageRMax * piece);
-    // lane path: the list of every pixel and a pool of 16 pieces per pixel
-    const size_t lane = kWsHeader + 256 + align_up(16 + npix * sizeof(FlatEntry), 256) + (size_t)npix * 16 * piece;
+    // lane path: the list of every pixel, its sorted copy and a pool of 16 pieces per pixel
+    const size_t lane = kWsHeader + 256 + 2 * align_up(16 + npix * sizeof(FlatEntry), 256) + kSortScratch +
+                        (size_t)npix * 16 * piece;
     return pooled > lane ? pooled : lane;
 }
 
@@ -2497,6 +2611,8 @@ template <int PREC>
 static cudaError_t launch_staged_pool(bool census, const CompArgs& a, void* workspace, size_t ws_bytes,
                                      cudaStream_t st) {
     // workspace: [header][counters][list: 4 words, entries of a chunk][pool: float4 x cap][pool: float2 x cap]
+    // (the list stays in build order: dense pixels have equal piece counts, and a warp's lanes then read
+    // pool runs that one warp wrote next to each other)
     const uint64_t npix = (uint64_t)a.npix;
     char* base = static_cast<char*>(workspace);
     // the chunk: as many pixels as the pool holds at the stage's worst case, all of them if they fit
@@ -2542,15 +2658,18 @@ static cudaError_t launch_staged_pool(bool census, const CompArgs& a, void* work
 
 template <int PREC>
 static cudaError_t launch_lane(bool census, const CompArgs& a, void* workspace, size_t ws_bytes, cudaStream_t st) {
-    // workspace: [header][counters][list: 4 words, npix entries][pool: float4 x cap][pool: float2 x cap]
+    // workspace: [header][counters][list: 4 words, npix entries][the list sorted][sort scratch]
+    // [pool: float4 x cap][pool: float2 x cap]
     const uint64_t npix = (uint64_t)a.npix;
     const size_t list_bytes = align_up(16 + npix * sizeof(FlatEntry), 256);
-    const size_t fixed = kWsHeader + 256 + list_bytes;
+    const size_t fixed = kWsHeader + 256 + 2 * list_bytes + kSortScratch;
     if (ws_bytes < fixed) return cudaErrorInvalidValue;
     char* base = static_cast<char*>(workspace);
     LaneArgs la;
     la.counter = reinterpret_cast<unsigned int*>(base + kWsHeader);
     la.list = reinterpret_cast<uint32_t*>(base + kWsHeader + 256);
+    uint32_t* sorted = reinterpret_cast<uint32_t*>(base + kWsHeader + 256 + list_bytes);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(base + kWsHeader + 256 + 2 * list_bytes);
     size_t cap = (ws_bytes - fixed) / (sizeof(float4) + sizeof(float2));
     if (cap > 0x7FFFFFFFu) cap = 0x7FFFFFFFu;
     la.pool.cap = (uint32_t)cap;
@@ -2573,8 +2692,10 @@ static cudaError_t launch_lane(bool census, const CompArgs& a, void* workspace, 
     k1<<<(unsigned)blocks, kLaneWarps * 32, sm, st>>>(a, la);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // search pass: a persistent grid; the list's length is known only on the device
-    e = launch_flat<PREC>(census, a, la.pool, la.list, npix, st);
+    // search pass over the list sorted by piece count: a persistent grid; the list's length is known
+    // only on the device
+    e = launch_sort<FlatEntry, 4>(la.list, sorted, hist, npix, st);
+    if (e == cudaSuccess) e = launch_flat<PREC>(census, a, la.pool, sorted, npix, st);
     if (e != cudaSuccess) return e;
     return launch_marked<kLaneKMax, 16, PREC>(census, a, la.list, npix, st);
 }
@@ -2599,7 +2720,7 @@ vdi_status launch_composite(const vdi_compact* pe, int k, int w, int h, const vd
     if (schedule == 0 || (schedule == 1 && k > 8)) schedule = default_schedule(k);
     // an automatic choice falls back to a direct schedule when the workspace holds no list or stage
     if (automatic && schedule == VDI_SCHED_LANE &&
-        ws_bytes < kWsHeader + 256 + align_up(16 + (uint64_t)w * h * sizeof(FlatEntry), 256))
+        ws_bytes < kWsHeader + 256 + 2 * align_up(16 + (uint64_t)w * h * sizeof(FlatEntry), 256) + kSortScratch)
         schedule = 1;
     if (automatic && schedule == VDI_SCHED_STAGED && ws_bytes < composite_workspace_bytes(1, 1)) schedule = 2;
     if (a.npix == 0) return VDI_OK;
@@ -2705,6 +2826,8 @@ size_t batched_workspace_bytes(const void* host_table) {
 template <int PREC>
 static cudaError_t launch_batched(const BatchArgs& a, const BatchHeader* hd, const ReqDev* rd, void* workspace,
                                   size_t ws_bytes, cudaStream_t st) {
+    // workspace: [header][counter][list][pool: float4 x cap][pool: float2 x cap] (the list in build order, as
+    // the pooled path's)
     char* base = static_cast<char*>(workspace);
     const size_t fixed = kWsHeader + 256 + batch_list_bytes(hd);
     if (ws_bytes < fixed) return cudaErrorInvalidValue;

@@ -376,24 +376,77 @@ __device__ __forceinline__ void volume_march(const Ray& r, int k0, int k1, const
     first_march<3, OWNED>(r, k0, k1, b, lut2, scale255, g2, INT_MAX, nullptr, cnt, cs, ga, e, &runs);
 }
 
-// Per-ray bisection search (sec. 2.4), called when the count at gamma = 0
-// (nt) exceeds n_s: sequential bisection of [0, 2]; each march evaluates the
-// midpoint and its two children, so two levels are decided per march.
-// `runs`: the count at gamma = 2 (OWNED; otherwise 1).
-template <bool OWNED = false>
-__device__ __forceinline__ float search(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
-                                        float scale255, int n_s, int iters, int nt, const CacheRef* c, int& count,
-                                        Census& cs, const GenReq* ga = nullptr, int e = 0, int runs = 1) {
-    float lo = 0.f, hi = 2.f;
-    // the distance never reaches 2: one supersegment per domain run
-    int cnt_hi = nt > 0 ? (OWNED ? runs : 1) : 0;
-    int it = 0;
-    while (it < iters) {
-        const float mid = 0.5f * (lo + hi);
-        const float g[3] = {mid, 0.5f * (lo + mid), 0.5f * (mid + hi)};
-        float g2[3];
+// Per-ray bisection of gamma, two levels per march (each march evaluates the
+// midpoint and both of its children), in one of three phases that share the
+// march's call sites, so that the learned instantiation inlines one cached and
+// one volume march, as the search does:
+//   kBisSearch: the search of sec. 2.4, called when the count at gamma = 0
+//     (nt) exceeds n_s: sequential bisection of [0, 2] for `iters` levels;
+//     `runs` is the count at gamma = 2 (OWNED; otherwise 1).
+//   kBisBracket (learned): the prediction gp is feasible (count cp <= n_s):
+//     six levels of bisection of log2 gamma over [log2 gp - 4, log2 gp].
+//   kBisTop (learned): gp is infeasible: one march evaluates log2 gp + 4 (the
+//     bracket's top), its midpoint and left quarter; an infeasible top falls
+//     back to the search, otherwise the bisection continues in the bracket.
+// A midpoint whose count is within n_s becomes the upper end, and stops the
+// bisection if its count is exactly n_s.  Returns the upper end's gamma (the
+// smallest feasible gamma found; for the learned brackets within a factor
+// 2^(1/16) of the bracket's threshold) and its count.  The census counts a
+// fallback from kBisTop as a searched ray.
+enum : int { kBisTop = 0, kBisBracket = 1, kBisSearch = 2 };
+
+template <bool LEARNED, bool OWNED = false>
+__device__ __forceinline__ float bisect_gamma(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
+                                              float scale255, int n_s, int iters, int nt, const CacheRef* c,
+                                              int phase, float gp, int cp, int& count, Census& cs,
+                                              const GenReq* ga = nullptr, int e = 0, int runs = 1) {
+    constexpr float R = 4.f;     // learned bracket: 4 octaves of gamma
+    constexpr int kLevels = 6;   // learned bracket: levels of bisection in log2 gamma
+    float lo, hi, ghi;
+    int cnt_hi, it, levels;
+    if (LEARNED && phase != kBisSearch) {
+        const float lg = log2f(fmaxf(gp, 0x1p-30f));
+        it = 0;
+        levels = kLevels;
+        lo = lg;
+        hi = lg + R;
+        ghi = 0.f;
+        cnt_hi = 0;
+        if (phase == kBisBracket) {
+            hi = lg;
+            ghi = gp;
+            cnt_hi = cp;
+            lo = lg - R;
+            if (cp == n_s) it = levels;
+        }
+    } else {
+        phase = kBisSearch;
+        lo = 0.f;
+        hi = 2.f;
+        ghi = 2.f;
+        // the distance never reaches 2: one supersegment per domain run
+        cnt_hi = nt > 0 ? (OWNED ? runs : 1) : 0;
+        it = 0;
+        levels = iters;
+    }
+    while (it < levels) {
+        float x[3];
+        if (LEARNED && phase == kBisTop) {
+            x[0] = hi;
+            x[1] = lo + 0.5f * R;
+            x[2] = lo + 0.25f * R;
+        } else {
+            const float mid = 0.5f * (lo + hi);
+            x[0] = mid;
+            x[1] = 0.5f * (lo + mid);
+            x[2] = 0.5f * (mid + hi);
+        }
+        float g[3], g2[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) g2[q] = __fmul_rn(g[q], g[q]);
+        for (int q = 0; q < 3; ++q) {
+            g[q] = (LEARNED && phase != kBisSearch) ? exp2f(x[q]) : x[q];
+            g2[q] = __fmul_rn(g[q], g[q]);
+        }
         int cnt[3];
         if (c) {
             cached_march<OWNED>(*c, nt, lut2, g2, cnt, cs);
@@ -402,128 +455,73 @@ __device__ __forceinline__ float search(const Ray& r, int k0, int k1, const Bric
             volume_march<OWNED>(r, k0, k1, b, lut2, scale255, g2, cnt, cs, ga, e);
             cs.remarched += 1;
         }
+        if (LEARNED && phase == kBisTop) {
+            if (cnt[0] > n_s) {
+                // no feasible gamma in the bracket: the full search
+                cs.searched += 1;
+                cs.overflow += c ? 0 : 1;
+                phase = kBisSearch;
+                lo = 0.f;
+                hi = 2.f;
+                ghi = 2.f;
+                cnt_hi = nt > 0 ? (OWNED ? runs : 1) : 0;
+                it = 0;
+                levels = iters;
+                continue;
+            }
+            phase = kBisBracket;
+            hi = x[0];
+            ghi = g[0];
+            cnt_hi = cnt[0];
+            ++it;
+            if (cnt[1] <= n_s) {
+                hi = x[1];
+                ghi = g[1];
+                cnt_hi = cnt[1];
+                if (cnt[1] != n_s) {
+                    ++it;
+                    if (cnt[2] <= n_s) {
+                        hi = x[2];
+                        ghi = g[2];
+                        cnt_hi = cnt[2];
+                    } else {
+                        lo = x[2];
+                    }
+                }
+            } else {
+                lo = x[1];
+            }
+            if (cnt_hi == n_s) break;
+            continue;
+        }
         // level 1: the midpoint
         ++it;
         int child;
         if (cnt[0] <= n_s) {
-            hi = mid;
+            hi = x[0];
+            ghi = g[0];
             cnt_hi = cnt[0];
             if (cnt[0] == n_s) break;
             child = 1;
         } else {
-            lo = mid;
+            lo = x[0];
             child = 2;
         }
-        if (it >= iters) break;
+        if (it >= levels) break;
         // level 2: the child inside the new bracket
         ++it;
         const int cc = cnt[child];
         if (cc <= n_s) {
-            hi = g[child];
-            cnt_hi = cc;
-            if (cc == n_s) break;
-        } else {
-            lo = g[child];
-        }
-    }
-    count = cnt_hi;
-    return hi;
-}
-
-// Learned-gamma refinement over the cached samples.  The prediction gp (count
-// cp there) brackets the search: if gp is feasible (cp <= n_s) the bracket is
-// log2 gamma in [log2 gp - 4, log2 gp], else [log2 gp, log2 gp + 4] once its
-// top is found feasible; six levels of bisection in log2 gamma follow, two
-// per cached march.  Returns false when the bracket holds no feasible gamma
-// (the caller then runs the full search).  The result is the smallest
-// feasible gamma found, within a factor 2^(1/16) of the bracket's threshold.
-__device__ __forceinline__ bool bracket_refine(const CacheRef& c, int nt, const float4* __restrict__ lut2, float gp,
-                                               int cp, int n_s, float& gamma, int& count, Census& cs) {
-    constexpr float R = 4.f;
-    constexpr int kLevels = 6;
-    const float lg = log2f(fmaxf(gp, 0x1p-30f));
-    float lo, hi, ghi;
-    int cnt_hi, it = 0;
-    if (cp <= n_s) {
-        hi = lg;
-        ghi = gp;
-        cnt_hi = cp;
-        lo = lg - R;
-    } else {
-        // the bracket's top, its midpoint and left quarter in one march
-        const float x[3] = {lg + R, lg + 0.5f * R, lg + 0.25f * R};
-        float g[3], g2[3];
-        int cc[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            g[q] = exp2f(x[q]);
-            g2[q] = __fmul_rn(g[q], g[q]);
-        }
-        cached_march<false>(c, nt, lut2, g2, cc, cs);
-        cs.cached += 1;
-        if (cc[0] > n_s) return false;
-        lo = lg;
-        hi = x[0];
-        ghi = g[0];
-        cnt_hi = cc[0];
-        ++it;
-        if (cc[1] <= n_s) {
-            hi = x[1];
-            ghi = g[1];
-            cnt_hi = cc[1];
-            if (cc[1] != n_s) {
-                ++it;
-                if (cc[2] <= n_s) {
-                    hi = x[2];
-                    ghi = g[2];
-                    cnt_hi = cc[2];
-                } else {
-                    lo = x[2];
-                }
-            } else {
-                it = kLevels;
-            }
-        } else {
-            lo = x[1];
-        }
-    }
-    while (it < kLevels && cnt_hi != n_s) {
-        const float mid = 0.5f * (lo + hi);
-        const float x[3] = {mid, 0.5f * (lo + mid), 0.5f * (mid + hi)};
-        float g[3], g2[3];
-        int cc[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            g[q] = exp2f(x[q]);
-            g2[q] = __fmul_rn(g[q], g[q]);
-        }
-        cached_march<false>(c, nt, lut2, g2, cc, cs);
-        cs.cached += 1;
-        ++it;
-        int child;
-        if (cc[0] <= n_s) {
-            hi = mid;
-            ghi = g[0];
-            cnt_hi = cc[0];
-            if (cc[0] == n_s) break;
-            child = 1;
-        } else {
-            lo = mid;
-            child = 2;
-        }
-        if (it >= kLevels) break;
-        ++it;
-        if (cc[child] <= n_s) {
             hi = x[child];
             ghi = g[child];
-            cnt_hi = cc[child];
+            cnt_hi = cc;
+            if (cc == n_s) break;
         } else {
             lo = x[child];
         }
     }
-    gamma = ghi;
     count = cnt_hi;
-    return true;
+    return ghi;
 }
 
 // gamma and count of one (PE, ray): the body of the count kernels.  The
@@ -555,19 +553,21 @@ __device__ __forceinline__ void count_ray(const GenReq& a, const BrickDev& b, co
             const bool use_cache = cref.e != nullptr;
             int nt;
             bool searched = true;
+            int phase = kBisSearch, cp = 0;
             if (mode >= 2) {
                 // one march: count at the given gamma, non-transparent count, cache
                 const float g2[1] = {__fmul_rn(gamma, gamma)};
                 int c[1];
                 nt = first_march<1, OWNED>(r, k0, k1, b, lut2, a.scale255, g2, INT_MAX, use_cache ? &cref : nullptr,
                                            c, cs, &a, e, &runs);
+                cp = c[0];
                 if (mode == 2) {
                     if (c[0] <= a.n_s) {
                         count = c[0];
                         searched = false;
                     }
                 } else if (LEARNED && nt > a.n_s && use_cache && nt <= cref.cap) {
-                    searched = !bracket_refine(cref, nt, lut2, gamma, c[0], a.n_s, gamma, count, cs);
+                    phase = c[0] <= a.n_s ? kBisBracket : kBisTop;
                 }
             } else {
                 int dummy[1];
@@ -580,10 +580,12 @@ __device__ __forceinline__ void count_ray(const GenReq& a, const BrickDev& b, co
                     count = nt;
                 } else {
                     const CacheRef* c = (use_cache && nt <= cref.cap) ? &cref : nullptr;
-                    cs.searched += 1;
-                    cs.overflow += c ? 0 : 1;
-                    gamma = search<OWNED>(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, count, cs, &a, e,
-                                          runs);
+                    if (phase == kBisSearch) {
+                        cs.searched += 1;
+                        cs.overflow += c ? 0 : 1;
+                    }
+                    gamma = bisect_gamma<LEARNED, OWNED>(r, k0, k1, b, lut2, a.scale255, a.n_s, a.iters, nt, c, phase,
+                                                         gamma, cp, count, cs, &a, e, runs);
                 }
             }
         }
@@ -604,9 +606,13 @@ __device__ __forceinline__ void census_flush_gen(const Census& cs, unsigned long
     atomicAdd(ctr + 7, cs.remarched);
 }
 
-// the learned instantiation keeps 8 blocks (128 registers): its inlined refinement spills under tighter bounds
+// the learned instantiation's block bound (its first march at the prediction adds live state)
+#ifndef VDI_LEARNED_MIN_BLOCKS
+#define VDI_LEARNED_MIN_BLOCKS 10
+#endif
 template <bool CENSUS, bool LEARNED, bool OWNED = false>
-__global__ void __launch_bounds__(kCountThreads, LEARNED ? 8 : VDI_COUNT_MIN_BLOCKS) gen_count_kernel(
+__global__ void __launch_bounds__(kCountThreads, LEARNED ? VDI_LEARNED_MIN_BLOCKS : VDI_COUNT_MIN_BLOCKS)
+    gen_count_kernel(
     const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     __shared__ unsigned int s_item;

@@ -2,7 +2,7 @@
 
 Inputs are seeded synthetic lists (sorted, non-overlapping within a PE,
 overlapping across PEs: premultiplied colour, opacity ~ U[0,1)) and sub-VDIs
-generated by the oracle.  Tolerances (the benchmark spec's): RGBA 1e-5 absolute
+generated by the oracle.  Tolerances (the project's parity bar): RGBA 1e-5 absolute
 with FP32 records, 2e-3 with FP16 storage against the FP64 composite of the
 unrounded inputs; depth bounds within 1e-5 of the ray length (synthetic
 depths lie in [0, 1]); per-pixel counts, and counts plus depth bounds,
@@ -58,7 +58,7 @@ def test_composite_matches_oracle_synthetic(k, n_s, w, h):
     n = g["counts"]
     tail = np.arange(n_s)[None, :] >= n[:, None]
     assert np.all(g["rgba"][tail] == 0) and np.all(g["fb"][tail] == 0)
-    # gamma agrees where the counts agree (gamma is not one of the benchmark spec's quantities: the count is
+    # gamma agrees where the counts agree (gamma is not one of the quantities the tolerances bind: the count is
     # not monotone in gamma, so a decision that rounding flips at one midpoint can send the bisection into
     # another bracket that ends at the same count; measured 99.8% at K = 64)
     same = g["counts"] == cnt
@@ -110,7 +110,7 @@ def test_composite_of_generated_subvdis(tiny_workload):
 def test_dense_fp16_storage_error():
     # precision configuration in small: dense lists (n = N_S for every PE and pixel), K = 32, N_S = 32.
     # FP16 storage (colour and optical depth in binary16) on input and output against the FP64
-    # composite of the unrounded inputs: the benchmark spec's 2e-3
+    # composite of the unrounded inputs: the FP16 storage bound of 2e-3
     w, h, k, n_s = 24, 16, 32, 32
     npix = w * h
     lists = synth_lists(0xF16, 0, k, npix, n_s, dense=True)

@@ -5,7 +5,7 @@ setup, 20.44 fixed-point positions); what differs from the FP64 oracle is the
 FP32 arithmetic of sampling, classification and the state machine, a few
 units of 1e-7 in a sample's colour and opacity.  A decision of Eq. 1 (or of
 the gamma search) whose margin is below that can flip, which changes a list's
-count or a record's bounds.  Tolerances (the benchmark spec's): per-(PE, ray)
+count or a record's bounds.  Tolerances (the project's parity bar): per-(PE, ray)
 counts identical, and counts plus depth bounds within 1e-5 of the ray's chord
 identical, on at least 99.9% of lists; RGBA within 1e-5 on the records of
 those lists; the flattened composite within 1e-5 of the oracle's DVR on every

@@ -6,7 +6,7 @@ lists, regenerated on the host).
   holds N_S records per pixel): first with FP32 records (103 GB of input),
   then with FP16 storage of colour and optical depth (69 GB).  The FP16 path
   is held to 2e-3 against the FP64 composite of the unrounded inputs (the
-  the benchmark spec's bound for FP16 storage), and to the FP16 output's rounding
+  project's bound for FP16 storage), and to the FP16 output's rounding
   against the oracle run on the stored FP16 inputs (the same bytes the GPU
   read).
 - Batched: 64 requests of the seeded request table (W ~ U{256..1920},
@@ -106,7 +106,7 @@ def test_precision_scale_full_size():
                                 ws.nbytes), "composite f16")
     vdi.check(ws.status(), "composite f16 status")
     cnt_g, rec_g = _gpu_records(out16, pix)
-    # against the FP64 composite of the unrounded inputs: the storage error the benchmark spec bounds
+    # against the FP64 composite of the unrounded inputs: the storage error the 2e-3 bound is for
     st16_vs_64 = compare_lists(cnt_g, rec_g, cnt_o, rec_o, 1e-5, 2e-3, check=False)
     img16 = oracle.flatten(cnt_g, rec_g)
     img64 = oracle.flatten(cnt_o, rec_o)

@@ -80,8 +80,9 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
 
 def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
-    # the bench reports a committed DRAM-traffic capture only for the workload it describes and only
-    # while the kernel's sources hash to the captured ones
+    # the bench reports a committed DRAM-traffic capture of a smaller frame, scaled by the frames' sample
+    # evaluations, only for the workload it names and only while the kernel's sources hash to the
+    # captured ones
     import hashlib
     import json
     import types
@@ -93,13 +94,15 @@ def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
     (fake / "src").mkdir()
     (fake / "src" / "k.cu").write_text("kernel source\n")
     h = hashlib.sha256((fake / "src" / "k.cu").read_bytes()).hexdigest()
-    rec = {"kernel": "gen_count_kernel", "workload": "a workload", "dram_bytes_read": 3.0e9,
-           "dram_bytes_write": 1.0e9, "sources": ["src/k.cu"], "sources_sha256": h}
+    rec = {"kernel": "gen_count_kernel", "workload": "a small workload", "scales_to": "a workload",
+           "sample_evals": 1000, "dram_bytes_read": 3.0e9, "dram_bytes_write": 1.0e9, "sources": ["src/k.cu"],
+           "sources_sha256": h}
     (fake / "profiles" / "gen_count_traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(fake))
     wl = types.SimpleNamespace(name="a workload")
-    assert bench.gen_traffic(wl) == 4.0e9
-    assert bench.gen_traffic(types.SimpleNamespace(name="another workload")) is None
+    assert bench.gen_traffic(wl, 1000) == 4.0e9
+    assert bench.gen_traffic(wl, 8000) == 32.0e9
+    assert bench.gen_traffic(types.SimpleNamespace(name="another workload"), 1000) is None
     # the kernel source differs by one byte
     (fake / "src" / "k.cu").write_text("kernel source\n\n")
-    assert bench.gen_traffic(wl) is None
+    assert bench.gen_traffic(wl, 1000) is None
