@@ -819,7 +819,8 @@ def main():
     ostructs = [o.struct() for o in outs]
     rstruct = reg.struct()
     stages = ["brick", "choose_gamma", "scan+emit", "composite", "flatten"]
-    launches_per_step = 1 + 1 + 4 + 1 + 1  # brick, count, 3 scan + emit, composite, flatten
+    # brick, count, 3 scan + emit, flatten; the compositing launches are added once its schedule is known
+    launches_per_step = 1 + 1 + 4 + 1
 
     def frame(view, ev=None):
         cam = cams[view]
@@ -853,6 +854,9 @@ def main():
     tuned_schedule = int(req.arr[0].schedule)
     comp_schedule = vdi.VDI_SCHED_LANE if k <= 8 else vdi.VDI_SCHED_STAGED
     params_c = vdi.make_params(step=wl.step, ref_len=wl.ref_len, schedule=comp_schedule)
+    # lane schedule: batch pass, the three kernels of the list's sort, flat search pass, direct sweep of
+    # marked pixels; pooled: build, flat search and direct sweep per chunk of 131072 pixels
+    launches_per_step += 6 if comp_schedule == vdi.VDI_SCHED_LANE else 3 * -(-npix // 131072)
     sched_ms = {}
     for sched in (1, 2, 3, vdi.VDI_SCHED_STAGED, vdi.VDI_SCHED_LANE):
         p_s = vdi.make_params(step=wl.step, ref_len=wl.ref_len, schedule=sched)

@@ -1356,7 +1356,6 @@ struct FlatEntry {
 constexpr int kLaneKMax = 8;        // PEs the lane path handles (heads in registers)
 constexpr int kLaneWarps = 4;       // warps per CTA
 constexpr int kLaneRCap = 480;      // records per warp slab
-constexpr int kLaneCopyMaxNs = 32;  // largest N_S of the warp-copied gamma = 0 emission
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
@@ -1547,13 +1546,11 @@ struct SlabSweeper {
     bool disjoint;
     uint32_t order;  // PEs by the front of their first record, 4 bits each
     int nonempty;    // PEs with a record of positive length
-    int nto;         // records of positive length and opacity (the non-transparent pieces, if disjoint)
 
     __device__ __forceinline__ void prepare() {
         float lo[kLaneKMax], hi[kLaneKMax];
         bool ok = true;
         int nz = 0;
-        nto = 0;
 #pragma unroll
         for (int e = 0; e < kLaneKMax; ++e) {
             lo[e] = kNoEvent;
@@ -1563,7 +1560,6 @@ struct SlabSweeper {
                 for (uint32_t r = st[e]; r < st[e] + cnt[e]; ++r) {
                     const float2 fb = S->bounds(r);
                     if (!(fb.y > fb.x)) continue;
-                    nto += S->rec(r).c.w > 0.f;
                     ok = ok && fb.x >= prev;
                     prev = fb.y;
                     lo[e] = fminf(lo[e], fb.x);
@@ -1653,28 +1649,6 @@ struct SlabSweeper {
             }
         }
         return np;
-    }
-
-    // Disjoint lists: the slab entries of the records of positive length and opacity, in depth order,
-    // to map[0..nto).  With gamma = 0 (sec. 2.4) each of them is one output record, itself: every
-    // non-transparent piece terminates the open supersegment (Eq. 1 with gamma = 0, reading G2) and
-    // every gap closes it, so the emission copies these records.
-    __device__ __forceinline__ void collect(uint16_t* map) const {
-        int w = 0;
-        for (int i = 0; i < nonempty; ++i) {
-            const int e = (int)((order >> (4 * i)) & 15u);
-            uint32_t s0 = st[0], c0 = cnt[0];
-#pragma unroll
-            for (int q = 1; q < kLaneKMax; ++q)
-                if (q == e) {
-                    s0 = st[q];
-                    c0 = cnt[q];
-                }
-            for (uint32_t r = s0; r < s0 + c0; ++r) {
-                const float2 fb = S->bounds(r);
-                if (fb.y > fb.x && S->rec(r).c.w > 0.f) map[w++] = (uint16_t)r;
-            }
-        }
     }
 };
 
@@ -1798,21 +1772,16 @@ __global__ void __launch_bounds__(128) composite_marked_kernel(const __grid_cons
 
 template <int PREC, int CAP>
 constexpr size_t lane_smem_bytes() {
-    return kLaneWarps * (sizeof(LaneSlab<PREC, CAP>) + 32 * kLaneCopyMaxNs * sizeof(uint16_t));
+    return kLaneWarps * sizeof(LaneSlab<PREC, CAP>);
 }
 
-#ifndef VDI_LANE_MIN_BLOCKS
-#define VDI_LANE_MIN_BLOCKS 1
-#endif
 template <int PREC, bool CENSUS>
-__global__ void __launch_bounds__(kLaneWarps * 32, VDI_LANE_MIN_BLOCKS) composite_lane_kernel(const __grid_constant__ CompArgs a,
+__global__ void __launch_bounds__(kLaneWarps * 32) composite_lane_kernel(const __grid_constant__ CompArgs a,
                                                                         const __grid_constant__ LaneArgs la) {
     using Slab = LaneSlab<PREC, kLaneRCap>;
     extern __shared__ __align__(16) unsigned char lane_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Slab& S = reinterpret_cast<Slab*>(lane_smem)[warp];
-    // the warp's copy map: per lane the slab entries of its pixel's output records
-    uint16_t* M = reinterpret_cast<uint16_t*>(lane_smem + kLaneWarps * sizeof(Slab)) + warp * 32 * kLaneCopyMaxNs;
     const int k = a.k;
     const uint32_t nitems = ((uint32_t)a.npix + 31u) / 32u;
     CompCensus cs;
@@ -1858,23 +1827,12 @@ __global__ void __launch_bounds__(kLaneWarps * 32, VDI_LANE_MIN_BLOCKS) composit
                 sw.cnt[e] = take ? cnt[e] : 0u;
             }
             sw.prepare();
-            bool search = false, copy = false;
+            bool search = false;
             uint32_t np = 0;
             if (take) {
                 NtVisitor nv{0};
-                if (sw.disjoint) nv.nt = sw.nto;
-                else np = (uint32_t)sw.run(nv);
-                if (nv.nt <= a.out.n_s && sw.disjoint && a.out.n_s <= kLaneCopyMaxNs) {
-                    // gamma = 0 on disjoint lists: the warp copies the records below
-                    copy = true;
-                    sw.collect(M + lane * kLaneCopyMaxNs);
-                    if (CENSUS) {
-                        cs.pixels += 1;
-                        cs.records += tot;
-                        cs.sweeps += 1;
-                        cs.pieces += (unsigned long long)nv.nt;
-                    }
-                } else if (nv.nt <= a.out.n_s) {
+                np = (uint32_t)sw.run(nv);
+                if (nv.nt <= a.out.n_s) {
                     // gamma = 0: every non-transparent piece is a supersegment
                     EmitVisitor em;
                     em.s.cnt = 0;
@@ -1885,8 +1843,7 @@ __global__ void __launch_bounds__(kLaneWarps * 32, VDI_LANE_MIN_BLOCKS) composit
                     em.written = 0;
                     em.base = (size_t)p * a.out.n_s;
                     em.out = &a.out;
-                    const uint32_t ne = (uint32_t)sw.run(em);
-                    if (sw.disjoint) np = ne;
+                    sw.run(em);
                     if (em.s.open && em.written < a.out.n_s) em.store(em.s.fS, em.bt, em.s.P, em.s.A, em.s.L2);
                     if (em.written != nv.nt) atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CUDA);
                     finish_pixel(a.out, p, em.written, 0.f);
@@ -1898,47 +1855,6 @@ __global__ void __launch_bounds__(kLaneWarps * 32, VDI_LANE_MIN_BLOCKS) composit
                     }
                 } else {
                     search = true;  // counted by the search pass
-                    if (sw.disjoint) {
-                        NtVisitor pieces{0};
-                        np = (uint32_t)sw.run(pieces);
-                    }
-                }
-            }
-            // the copying lanes' records, written by the whole warp: each pixel's N_S slots are
-            // consecutive, so the lanes' stores of one pixel are one coalesced run
-            const unsigned cm = __ballot_sync(0xffffffffu, copy);
-            if (cm) {
-                __syncwarp();
-                const int n_s = a.out.n_s;
-                for (unsigned m = cm; m; m &= m - 1u) {
-                    const int q = __ffs(m) - 1;
-                    const int nq = __shfl_sync(0xffffffffu, sw.nto, q);
-                    const uint16_t* mq = M + q * kLaneCopyMaxNs;
-                    const size_t base = (size_t)(item * 32u + (uint32_t)q) * (size_t)n_s;
-                    for (int j = lane; j < n_s; j += 32) {
-                        const size_t idx = base + (size_t)j;
-                        if (j < nq) {
-                            const uint32_t r = mq[j];
-                            const RecC c = S.rec(r);
-                            const float2 fb = S.bounds(r);
-                            if (a.out.prec == VDI_PREC_F32) {
-                                reinterpret_cast<float4*>(a.out.rgba)[idx] = c.c;
-                                a.out.fb[idx] = fb;
-                            } else {
-                                reinterpret_cast<uint4*>(a.out.rgba)[idx] =
-                                    f16_pack(fb.x, fb.y, c.c.x, c.c.y, c.c.z, -c.tau);
-                            }
-                        } else if (a.out.prec == VDI_PREC_F32) {
-                            reinterpret_cast<float4*>(a.out.rgba)[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-                            a.out.fb[idx] = make_float2(0.f, 0.f);
-                        } else {
-                            reinterpret_cast<uint4*>(a.out.rgba)[idx] = make_uint4(0u, 0u, 0u, 0u);
-                        }
-                    }
-                }
-                if (copy) {
-                    a.out.counts[p] = (uint32_t)sw.nto;
-                    if (a.out.gamma) a.out.gamma[p] = 0.f;
                 }
             }
             // the searching lanes' pieces go to the pool, one run per pixel (one atomic per warp)
