@@ -106,3 +106,18 @@ def test_static_scratch_returns_device_status():
     s = vdi.vdi_generate_static_scratch(br.bricks, lut_d.data_ptr(), c, n_s, vdi.VDI_GAMMA_SEARCH,
                                         [o.struct() for o in got], vdi.make_params())
     assert s == vdi.VDI_OK
+
+
+def test_static_scratch_in_a_second_context():
+    # the array's address is looked up in the context current at each call: a call in a second context
+    # on the same device (created with the driver API, as an in-situ host may keep its own), and one in
+    # the primary context after that context is destroyed, give the first call's results (a child
+    # process, so that this process's torch context is not involved)
+    import os
+    import subprocess
+    import sys
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    r = subprocess.run([sys.executable, os.path.join(here, "static_scratch_contexts.py")], capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), (r.stdout[-2000:], r.stderr[-2000:])
