@@ -232,14 +232,34 @@ __global__ void __launch_bounds__(128) novel_view_kernel(const __grid_constant__
                 const bool rising = s >= ss;
                 const float ua = fabsf(df_sub(df_f(s), s_star).hi), ub = isinf(sn) ? INFINITY : fabsf(df_sub(df_f(sn), s_star).hi);
                 const float ulo = fminf(ua, ub), uhi = fmaxf(ua, ub);
-                for (int t = 0; t < n; ++t) {
-                    const int k = rising ? t : n - 1 - t;
+                // The column's records are sorted and disjoint in depth, and shell_offset is
+                // non-decreasing in depth, so the records this piece overlaps are one run: rising, from
+                // the first whose back lies beyond ulo to the first whose front reaches uhi; falling
+                // (records in reverse), from the last whose front lies below uhi down to the first whose
+                // back reaches down to ulo.  The run's start is found by bisection; the records skipped
+                // have no overlap (l <= 0), so the sum is that of the full loop.
+                int k0;
+                {
+                    int lo_k = 0, hi_k = n;
+                    while (lo_k < hi_k) {
+                        const int mid = (lo_k + hi_k) >> 1;
+                        float f, b;
+                        load_rec(a, p * a.n_s + mid, f, b);
+                        const bool before = rising ? !(shell_offset(b, rho) > ulo) : shell_offset(f, rho) < uhi;
+                        if (before) lo_k = mid + 1;
+                        else hi_k = mid;
+                    }
+                    k0 = rising ? lo_k : lo_k - 1;
+                }
+                for (int k = k0; rising ? k < n : k >= 0; k += rising ? 1 : -1) {
                     const size_t idx = p * a.n_s + k;
                     float f, b;
                     load_rec(a, idx, f, b);
                     if (!(b > f)) continue;
-                    const float lo = fmaxf(shell_offset(f, rho), ulo);
-                    const float hi = fminf(shell_offset(b, rho), uhi);
+                    const float so_f = shell_offset(f, rho), so_b = shell_offset(b, rho);
+                    if (rising ? so_f >= uhi : so_b <= ulo) break;
+                    const float lo = fmaxf(so_f, ulo);
+                    const float hi = fminf(so_b, uhi);
                     const float l = hi - lo;
                     if (!(l > 0.f)) continue;
                     float tau;
