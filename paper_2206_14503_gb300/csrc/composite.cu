@@ -662,19 +662,21 @@ __device__ __forceinline__ void cq_step(CompCountQ& s, const Piece& x, float g2)
 // are bit for bit those of the branchy steps, and a visitor's candidates form
 // straight-line code whose dependency chains interleave.
 struct StepSel {
-    bool fresh, close, absorbing;
+    bool fresh, close;
 };
 
+// A step that neither opens S (fresh) nor absorbs into it leaves S closed, and the colour, opacity,
+// optical depth and bounds of a closed S are never read again (the next fresh piece overwrites all of
+// them), so those steps may take the absorbing form as well: one select per value instead of two.
 template <typename S>
 __device__ __forceinline__ void apply_step(S& s, const Piece& x, StepSel d) {
     const float T = __fsub_rn(1.f, s.A);
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-        s.P[c] = d.fresh ? x.P[c] : (d.absorbing ? __fmaf_rn(T, x.P[c], s.P[c]) : s.P[c]);
-    s.A = d.fresh ? x.a : (d.absorbing ? __fmaf_rn(T, x.a, s.A) : s.A);
-    s.L2 = d.fresh ? x.lgT : (d.absorbing ? __fadd_rn(s.L2, x.lgT) : s.L2);
+    for (int c = 0; c < 3; ++c) s.P[c] = d.fresh ? x.P[c] : __fmaf_rn(T, x.P[c], s.P[c]);
+    s.A = d.fresh ? x.a : __fmaf_rn(T, x.a, s.A);
+    s.L2 = d.fresh ? x.lgT : __fadd_rn(s.L2, x.lgT);
     s.fS = d.fresh ? x.f : s.fS;
-    s.bS = (d.fresh || d.absorbing) ? x.b : s.bS;
+    s.bS = x.b;
     s.open = d.fresh || (s.open && !d.close);
     s.cnt += d.fresh ? 1 : 0;
 }
@@ -691,7 +693,7 @@ __device__ __forceinline__ void cq_step_select(CompCountQ& s, const Piece& x, fl
     s.qhi = crit ? fminf(s.qhi, q) : s.qhi;               // crit implies an open S
     s.qlo = (s.open && !crit) ? fmaxf(s.qlo, q) : s.qlo;
     const bool opaque = x.a > 0.f;
-    apply_step(s, x, StepSel{opaque && (!s.open || crit), crit && !opaque, s.open && !crit});
+    apply_step(s, x, StepSel{opaque && (!s.open || crit), crit && !opaque});
 }
 
 // SELECT: the branch-free steps (faster where the pieces come from the staged
@@ -1546,11 +1548,15 @@ struct SlabSweeper {
     bool disjoint;
     uint32_t order;  // PEs by the front of their first record, 4 bits each
     int nonempty;    // PEs with a record of positive length
+    int nvalid;      // records of positive length
+    int nto;         // of them, those of positive opacity (the non-transparent pieces, if disjoint)
 
     __device__ __forceinline__ void prepare() {
         float lo[kLaneKMax], hi[kLaneKMax];
         bool ok = true;
         int nz = 0;
+        nvalid = 0;
+        nto = 0;
 #pragma unroll
         for (int e = 0; e < kLaneKMax; ++e) {
             lo[e] = kNoEvent;
@@ -1560,6 +1566,8 @@ struct SlabSweeper {
                 for (uint32_t r = st[e]; r < st[e] + cnt[e]; ++r) {
                     const float2 fb = S->bounds(r);
                     if (!(fb.y > fb.x)) continue;
+                    ++nvalid;
+                    nto += S->rec(r).c.w > 0.f;
                     ok = ok && fb.x >= prev;
                     prev = fb.y;
                     lo[e] = fminf(lo[e], fb.x);
@@ -1657,6 +1665,42 @@ struct NtVisitor {
     __device__ __forceinline__ void operator()(const Piece& x) { nt += x.a > 0.f; }
 };
 
+// One sweep of the batch pass for every lane, whichever way its pixel goes.  A pixel whose
+// non-transparent pieces number at most N_S takes gamma = 0 (sec. 2.4), and then every
+// non-transparent piece is one output record, itself: each one terminates the open supersegment
+// (Eq. 1 with gamma = 0: the distance is >= 0, reading G2) and each transparent piece closes it,
+// so EmitVisitor with gamma = 0 stores exactly these pieces' values.  A pixel that needs the search
+// writes all its pieces to its pool run.
+struct LaneSink {
+    const OutDev* out;
+    size_t base;  // first output slot of the pixel
+    int written;
+    bool emit;
+    float4* A;  // the pixel's pool run
+    float2* B;
+    bool pool;
+    float f0;  // front of the first piece
+    uint32_t np;
+    __device__ __forceinline__ void operator()(const Piece& x) {
+        if (np == 0) f0 = x.f;
+        if (pool) {
+            A[np] = make_float4(x.P[0], x.P[1], x.P[2], x.a);
+            B[np] = make_float2(x.b, x.lgT);
+        }
+        if (emit && x.a > 0.f) {
+            const size_t idx = base + written;
+            if (out->prec == VDI_PREC_F32) {
+                reinterpret_cast<float4*>(out->rgba)[idx] = make_float4(x.P[0], x.P[1], x.P[2], x.a);
+                out->fb[idx] = make_float2(x.f, x.b);
+            } else {
+                reinterpret_cast<uint4*>(out->rgba)[idx] = f16_pack(x.f, x.b, x.P[0], x.P[1], x.P[2], x.lgT);
+            }
+            ++written;
+        }
+        ++np;
+    }
+};
+
 // writes the zero tail, count and gamma of pixel p after an emission of `written` records
 __device__ __forceinline__ void finish_pixel(const OutDev& out, uint32_t p, int written, float gamma) {
     for (int j = written; j < out.n_s; ++j) {
@@ -1680,15 +1724,6 @@ struct LaneArgs {
     PiecePool pool;
 };
 
-// Pieces of a pixel into its run of the pool.
-struct PoolWriter {
-    float4* A;
-    float2* B;
-    __device__ __forceinline__ void operator()(const Piece& x) {
-        *A++ = make_float4(x.P[0], x.P[1], x.P[2], x.a);
-        *B++ = make_float2(x.b, x.lgT);
-    }
-};
 
 // appends an entry for each lane with `flag` set (one atomic per warp)
 __device__ __forceinline__ void list_push(uint32_t* list, bool flag, const FlatEntry& en) {
@@ -1827,63 +1862,48 @@ __global__ void __launch_bounds__(kLaneWarps * 32) composite_lane_kernel(const _
                 sw.cnt[e] = take ? cnt[e] : 0u;
             }
             sw.prepare();
-            bool search = false;
-            uint32_t np = 0;
+            bool emit = false, search = false;
+            uint32_t bound = 0;  // pieces the pixel's pool run must hold
+            int nt = 0;
             if (take) {
-                NtVisitor nv{0};
-                np = (uint32_t)sw.run(nv);
-                if (nv.nt <= a.out.n_s) {
-                    // gamma = 0: every non-transparent piece is a supersegment
-                    EmitVisitor em;
-                    em.s.cnt = 0;
-                    em.s.open = false;
-                    em.g2 = 0.f;
-                    em.cap = a.out.n_s;
-                    em.bt = 0.f;
-                    em.written = 0;
-                    em.base = (size_t)p * a.out.n_s;
-                    em.out = &a.out;
-                    sw.run(em);
-                    if (em.s.open && em.written < a.out.n_s) em.store(em.s.fS, em.bt, em.s.P, em.s.A, em.s.L2);
-                    if (em.written != nv.nt) atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CUDA);
-                    finish_pixel(a.out, p, em.written, 0.f);
-                    if (CENSUS) {
-                        cs.pixels += 1;
-                        cs.records += tot;
-                        cs.sweeps += 2;
-                        cs.pieces += 2ull * np;
-                    }
+                if (sw.disjoint) {
+                    // the pieces are the valid records with a gap between some of them
+                    nt = sw.nto;
+                    bound = sw.nvalid > 0 ? 2u * (uint32_t)sw.nvalid - 1u : 0u;
                 } else {
-                    search = true;  // counted by the search pass
+                    NtVisitor nv{0};
+                    bound = (uint32_t)sw.run(nv);
+                    nt = nv.nt;
                 }
+                emit = nt <= a.out.n_s;
+                search = !emit;
             }
-            // the searching lanes' pieces go to the pool, one run per pixel (one atomic per warp)
+            // the searching lanes' pool runs (one atomic per warp)
+            uint32_t base = 0;
+            bool fits = false;
             if (__any_sync(0xffffffffu, search)) {
-                const uint32_t mine = search ? np : 0u;
+                const uint32_t mine = search ? bound : 0u;
                 const uint32_t inc = warp_incl_scan_u32(mine);
-                uint32_t base = 0;
                 if (lane == 31) base = atomicAdd(la.list + 2, inc);
                 base = __shfl_sync(0xffffffffu, base, 31) + inc - mine;
-                const bool fits = search && (uint64_t)base + mine <= (uint64_t)la.pool.cap;
-                float f0 = 0.f;
-                if (fits) {
-                    PoolWriter pw{la.pool.A + base, la.pool.B + base};
-                    struct First {
-                        PoolWriter* w;
-                        float* f0;
-                        bool seen;
-                        __device__ __forceinline__ void operator()(const Piece& x) {
-                            if (!seen) {
-                                *f0 = x.f;
-                                seen = true;
-                            }
-                            (*w)(x);
-                        }
-                    } fw{&pw, &f0, false};
-                    sw.run(fw);
-                }
-                list_push(la.list, search, FlatEntry{fits ? p : (p | 0x80000000u), base, mine, f0});
+                fits = search && (uint64_t)base + mine <= (uint64_t)la.pool.cap;
             }
+            // one sweep: the gamma = 0 pixels' records, the searched pixels' pieces
+            LaneSink snk{&a.out, (size_t)p * a.out.n_s, 0, emit, la.pool.A + base, la.pool.B + base, fits, 0.f, 0u};
+            if (emit || fits) sw.run(snk);
+            if (emit) {
+                if (snk.written != nt) atomicCAS(a.status, 0u, (unsigned)VDI_ERR_CUDA);
+                finish_pixel(a.out, p, snk.written, 0.f);
+                if (CENSUS) {
+                    const unsigned sweeps = sw.disjoint ? 1u : 2u;
+                    cs.pixels += 1;
+                    cs.records += tot;
+                    cs.sweeps += sweeps;
+                    cs.pieces += (unsigned long long)sweeps * snk.np;
+                }
+            }
+            if (__any_sync(0xffffffffu, search))
+                list_push(la.list, search, FlatEntry{fits ? p : (p | 0x80000000u), base, snk.np, snk.f0});
             __syncwarp();
         }
     }
@@ -1962,6 +1982,13 @@ enum : int { kFlatIdle = 0, kFlatFirst = 1, kFlatSearch = 2, kFlatEmit = 3 };
 
 #ifndef VDI_FLAT_END_BATCH
 #define VDI_FLAT_END_BATCH 16
+#endif
+// resident CTAs of the flat pass per SM over the dense pieces of the pooled and batched paths (the lane
+// path takes as many as the registers allow): with 2047-piece runs, more lanes per SM evict each
+// other's pool lines and decision tables from L1 (dense 512^2, K = 32: 137.7 ms at 5 CTAs, 150.8 at 6;
+// the plain frame: 3.20 ms at 6, 3.36 at 5)
+#ifndef VDI_FLAT_CTAS_PER_SM
+#define VDI_FLAT_CTAS_PER_SM 5
 #endif
 
 struct FlatLane {
@@ -2210,7 +2237,7 @@ __device__ __forceinline__ void flat_loop(const SRC& src, const PiecePool& pool,
             const bool fresh = opaque && (!s.open || crit);
             const bool absorbing = s.open && !crit;
             L.bt = (fresh || (absorbing && opaque)) ? x.b : L.bt;
-            apply_step(s, x, StepSel{fresh, crit && !opaque, absorbing});
+            apply_step(s, x, StepSel{fresh, crit && !opaque});
             L.nt += opaque;
             cq_step_select(L.st[1], x, L.g2[1]);
             cq_step_select(L.st[2], x, L.g2[2]);
@@ -2592,11 +2619,12 @@ static cudaError_t launch_marked(bool census, const CompArgs& a, const uint32_t*
 
 template <int PREC>
 static cudaError_t launch_flat(bool census, const CompArgs& a, const PiecePool& pool, uint32_t* list, uint64_t lanes,
-                               cudaStream_t st) {
+                               cudaStream_t st, int max_per_sm = 0) {
     auto k2 = census ? composite_flat_kernel<true> : composite_flat_kernel<false>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2, 128, 0);
     if (e != cudaSuccess) return e;
+    if (max_per_sm > 0 && per_sm > max_per_sm) per_sm = max_per_sm;
     uint64_t b = (uint64_t)device_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
     const uint64_t need = (lanes + 127) / 128;
     if (b > need) b = need > 0 ? need : 1;
@@ -2645,7 +2673,7 @@ static cudaError_t launch_staged_pool(bool census, const CompArgs& a, void* work
         if (e != cudaSuccess) return e;
         kb<<<(unsigned)stage_ctas((p1 - p0 + 31) / 32), kStageWarps * 32, sm, st>>>(a, ba);
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = launch_flat<PREC>(census, a, ba.pool, ba.list, p1 - p0, st);
+        if (e == cudaSuccess) e = launch_flat<PREC>(census, a, ba.pool, ba.list, p1 - p0, st, VDI_FLAT_CTAS_PER_SM);
         if (e == cudaSuccess) {
             if (P == 16) e = launch_marked<0, 16, PREC>(census, a, ba.list, p1 - p0, st);
             else if (P == 32) e = launch_marked<0, 32, PREC>(census, a, ba.list, p1 - p0, st);
@@ -2855,6 +2883,7 @@ static cudaError_t launch_batched(const BatchArgs& a, const BatchHeader* hd, con
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, composite_batched_flat_kernel, 128, 0);
     if (e != cudaSuccess) return e;
+    if (VDI_FLAT_CTAS_PER_SM > 0 && per_sm > VDI_FLAT_CTAS_PER_SM) per_sm = VDI_FLAT_CTAS_PER_SM;
     // chunks of whole items whose expected pieces fit the pool and whose pixels fit the list
     uint32_t item = 0;
     int q = 0;

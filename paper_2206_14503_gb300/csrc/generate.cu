@@ -762,7 +762,10 @@ __device__ __forceinline__ void emit_ray(const GenReq& a, const BrickDev& b, con
 }
 
 template <bool OWNED, bool REGULAR>
-__global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_kernel(const __grid_constant__ GenArgs a) {
+#ifndef VDI_EMIT_MIN_BLOCKS
+#define VDI_EMIT_MIN_BLOCKS 8
+#endif
+__global__ void __launch_bounds__(kEmitThreads, VDI_EMIT_MIN_BLOCKS) gen_emit_kernel(const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     int i, j;
     tile_pixel(a.r.tiles_x, blockIdx.x, kEmitTileH, i, j);
@@ -856,7 +859,7 @@ __global__ void __launch_bounds__(kCountThreads, VDI_COUNT_MIN_BLOCKS) gen_count
     }
 }
 
-__global__ void __launch_bounds__(kEmitThreads, 8) gen_emit_batched_kernel(const __grid_constant__ GenBatchArgs a) {
+__global__ void __launch_bounds__(kEmitThreads, VDI_EMIT_MIN_BLOCKS) gen_emit_batched_kernel(const __grid_constant__ GenBatchArgs a) {
     __shared__ float4 lut2[2 * 257];
     const uint32_t item = blockIdx.x;
     const int q = batch_request<true>(a.reqs, a.n, item);
