@@ -549,7 +549,8 @@ typedef struct {
 
 /* Device bytes of the arena a pipeline with this description needs (two
  * volumes, the k bricks, the k compact sub-VDIs, two regular VDIs, the
- * generation and compositing workspaces).  0 for an invalid description. */
+ * generation and compositing workspaces, two 8-byte status snapshots).  0 for
+ * an invalid description. */
 size_t vdi_pipeline_arena_bytes(const vdi_pipeline_desc* desc);
 /* Creates a pipeline on the current device.  arena: caller-allocated device
  * memory of vdi_pipeline_arena_bytes(desc) bytes, 256-byte aligned, owned by

@@ -5,12 +5,13 @@
 // regular VDI, so the overlap is between the copy engines and the SMs.
 //
 // Three streams per pipeline: copy-in (volume uploads), compute (brick build,
-// generation, compositing, status read-back), copy-out (regular-VDI
-// downloads), ordered by events.  The volume and the regular VDI are
-// double-buffered; the bricks, the sub-VDIs and the workspaces are used by
-// the compute stream alone, so one copy of each suffices.  A submission first
-// waits on the host for the frame two back, which frees its buffers: at most
-// two frames are in flight and no device-side wait spans more than one frame.
+// generation, compositing, a snapshot of the status words), copy-out
+// (regular-VDI downloads and the status read-back), ordered by events.  The
+// volume and the regular VDI are double-buffered; the bricks, the sub-VDIs
+// and the workspaces are used by the compute stream alone, so one copy of
+// each suffices.  A submission first waits on the host for the frame two
+// back, which frees its buffers: at most two frames are in flight and no
+// device-side wait spans more than one frame.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -37,6 +38,7 @@ struct Layout {
     size_t sub_rgba[VDI_MAX_PE], sub_fb[VDI_MAX_PE];
     size_t reg_counts[kDepth], reg_gamma[kDepth], reg_rgba[kDepth], reg_fb[kDepth];
     size_t wsg, wsg_bytes, wsc, wsc_bytes;
+    size_t status[kDepth];  // a frame's two status words, copied there by the compute stream
     size_t vol_bytes;
     uint64_t capacity;
     size_t total;
@@ -121,8 +123,19 @@ bool plan(const vdi_pipeline_desc* d, Layout& L) {
     L.wsg = take(L.wsg_bytes);
     L.wsc_bytes = vdi_composite_workspace(d->k, d->width, d->height, d->n_s);
     L.wsc = take(L.wsc_bytes);
+    for (int s = 0; s < kDepth; ++s) L.status[s] = take(2 * sizeof(unsigned int));
     L.total = at;
     return true;
+}
+
+// The status words of a frame's generation and compositing workspaces into the slot's snapshot.  A
+// kernel, not a copy: a device-to-host copy on the compute stream would queue on the copy engine behind
+// the previous frame's download and hold the compute stream until it ends.
+__global__ void status_snapshot_kernel(const unsigned int* gen, const unsigned int* comp, unsigned int* dst) {
+    if (threadIdx.x == 0) {
+        dst[0] = *gen;
+        dst[1] = *comp;
+    }
 }
 
 }  // namespace
@@ -314,11 +327,14 @@ vdi_status vdi_pipeline_submit(vdi_pipeline* pl, const void* volume, const vdi_c
     if (r == VDI_OK)
         r = vdi_composite(pl->sub, d.k, d.width, d.height, &pl->reg[s], &pl->params, a + L.wsc, L.wsc_bytes,
                           (vdi_stream)comp);
-    // the status words this frame's kernels left, read back before the next frame clears them
-    for (int w = 0; w < 2 && r == VDI_OK; ++w)
-        r = cuda_check(cudaMemcpyAsync(pl->mirror + 2 * s + w, a + (w ? L.wsc : L.wsg), sizeof(unsigned int),
-                                       cudaMemcpyDeviceToHost, comp),
-                       "status read");
+    // the status words this frame's kernels left, kept in the slot before the next frame clears them;
+    // the copy-out stream reads them back after the download
+    unsigned int* snap = reinterpret_cast<unsigned int*>(a + L.status[s]);
+    if (r == VDI_OK) {
+        status_snapshot_kernel<<<1, 32, 0, comp>>>(reinterpret_cast<const unsigned int*>(a + L.wsg),
+                                                   reinterpret_cast<const unsigned int*>(a + L.wsc), snap);
+        r = cuda_check(cudaGetLastError(), "status snapshot");
+    }
     // the completion events are recorded even after an error, so that waiting for the frame
     // waits for whatever part of it was enqueued
     vdi_status r2 = cuda_check(cudaEventRecord(pl->reg_ready[s], comp), "event record");
@@ -332,6 +348,10 @@ vdi_status vdi_pipeline_submit(vdi_pipeline* pl, const void* volume, const vdi_c
             r = cuda_check(cudaMemcpyAsync(dst->fb, g.fb, slots * 8, cudaMemcpyDeviceToHost, cout), "download");
         if (r == VDI_OK && dst->gamma)
             r = cuda_check(cudaMemcpyAsync(dst->gamma, g.gamma, npix * 4, cudaMemcpyDeviceToHost, cout), "download");
+        if (r == VDI_OK)
+            r = cuda_check(cudaMemcpyAsync(pl->mirror + 2 * s, snap, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                                           cout),
+                           "status read");
     }
     vdi_status r3 = cuda_check(cudaEventRecord(pl->done[s], cout), "event record");
     if (r == VDI_OK) r = r2;
