@@ -401,27 +401,31 @@ __device__ __forceinline__ void absorb(float P[3], float& A, float& L2, const fl
 }
 
 // Known counts: exact candidates and their decision intervals.
+#ifndef VDI_TABLE_N
+#define VDI_TABLE_N 27
+#endif
 struct CountTable {
-    static constexpr int N = 27;  // 9 marches of 3 candidates cover 16 levels
-    float g2[N], lo[N], hi[N];
+    static constexpr int N = VDI_TABLE_N;  // 27: 9 marches of 3 candidates cover 16 levels
+    float g2[N], lo[N], hi[N];  // lo, hi: the interval narrowed by the margin below
     int c[N];
     int n;
+    // The interval is narrowed by a relative margin of 2^-16, far above the ratio's approximation
+    // error; the narrowed bounds are kept.
     __device__ __forceinline__ void add(float g2v, float qlo, float qhi, int cnt) {
         if (n >= N) n = 0;  // full (more than 16 levels): start over, dropping the oldest
         {
             g2[n] = g2v;
-            lo[n] = qlo;
-            hi[n] = qhi;
+            lo[n] = qlo * (1.f + 1.0f / 65536.f);
+            hi[n] = qhi * (1.f - 1.0f / 65536.f);
             c[n] = cnt;
             ++n;
         }
     }
-    // count at gamma^2 = x if known, else -1.  The interval is narrowed by a
-    // relative margin of 2^-16, far above the ratio's approximation error.
+    // count at gamma^2 = x if known, else -1
     __device__ __forceinline__ int lookup(float x) const {
         for (int i = 0; i < n; ++i) {
             if (x == g2[i]) return c[i];
-            if (x > lo[i] * (1.f + 1.0f / 65536.f) && x <= hi[i] * (1.f - 1.0f / 65536.f)) return c[i];
+            if (x > lo[i] && x <= hi[i]) return c[i];
         }
         return -1;
     }
