@@ -132,6 +132,25 @@ def test_dense_fp16_storage_error():
     compare_lists(g32["counts"], np.concatenate([g32["fb"], g32["rgba"]], -1), cnt32, recs32, 1e-5, 1e-5)
 
 
+@pytest.mark.parametrize("k,n_s,w,h", [(5, 6, 53, 41), (8, 20, 50, 43)])
+def test_fp16_lane_schedule(k, n_s, w, h):
+    # FP16 records in and out through the default schedule for K <= 8 (the lane schedule: the gamma = 0
+    # records written by the batch pass, the searched pixels by the flat pass), against the oracle on the
+    # stored FP16 inputs (decoded exactly): 1e-5 on the colour plus the FP16 output's rounding (half an
+    # ulp of colour, 1.8e-4 of opacity); and the same bits from every schedule
+    npix = w * h
+    lists = synth_lists(0xF17 + k, 0, k, npix, n_s)
+    f16 = [(c, o, None, pack_f16_records(fb, rgba), 2) for c, o, fb, rgba, _ in lists]
+    g = composite(f16, w, h, n_s, prec_out=1)
+    cnt16, _, recs16 = oracle_composite(f16, n_s, npix)
+    compare_lists(g["counts"], np.concatenate([g["fb"], g["rgba"]], -1), cnt16, recs16, 1e-5, 5e-4)
+    assert (g["counts"] > 0).mean() > 0.5
+    for sched in _schedules(k):
+        gs = composite(f16, w, h, n_s, prec_out=1, schedule=sched)
+        for key in ("counts", "gamma", "fb", "rgba"):
+            assert np.array_equal(gs[key], g[key]), (sched, key)
+
+
 def test_empty_and_degenerate_inputs():
     w, h, n_s = 9, 7, 4
     npix = w * h
