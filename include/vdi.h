@@ -352,30 +352,35 @@ vdi_status vdi_generate_static_scratch(const vdi_brick* bricks, int32_t k, const
  * at most n_s supersegments are written front to back with a zero tail.
  * params->schedule (all give the same result, bit for bit):
  *   0 automatic (VDI_SCHED_LANE for k <= 8, else VDI_SCHED_STAGED);
- *   VDI_SCHED_STAGED (4): a warp builds the pieces of 32 pixels, one pixel at
- *     a time with all its lanes (coalesced loads of the K lists, a stable
- *     merge of their bounds, an exact prefix scan of the records' terms) into
- *     a piece buffer in the workspace; then each lane runs the search and the
- *     emission of one pixel over its buffered pieces.  Pixels with more than
- *     1024 records, or more pieces than the buffer's rows, take schedule 2 in
- *     a second launch;
+ *   VDI_SCHED_STAGED (4, the pooled schedule): a warp builds the pieces of
+ *     32 pixels, one pixel at a time with all its lanes (coalesced loads of
+ *     the K lists, a stable merge of their bounds, an exact prefix scan of
+ *     the records' terms), writes each pixel's pieces as one run of a pool in
+ *     the workspace and lists the pixel; a second launch runs the search and
+ *     the emission of every listed pixel, one lane each, lanes taking new
+ *     pixels as they finish; pixels with more than 1024 records or lists out
+ *     of depth order are composited by a direct sweep in a third launch.  The
+ *     image is processed in chunks of pixels whose pieces fit the pool;
  *   VDI_SCHED_LANE (5, k <= 8; larger k take VDI_SCHED_STAGED): a warp copies
  *     the records of 32 consecutive pixels into shared memory with coalesced
- *     loads, each lane sweeps its pixel's lists there, and a pixel whose
- *     count at gamma = 0 is within n_s is emitted at once; the pixels that
- *     need the search (or whose records exceed the warp's 480-record slab)
- *     are listed and follow in a second launch, one lane each, as schedule 1,
- *     so that every lane of a warp searches;
+ *     loads and each lane sweeps its pixel's lists there once: a pixel whose
+ *     count at gamma = 0 is within n_s is emitted at once, a pixel that needs
+ *     the search writes its pieces to the pool and is listed; the list is
+ *     sorted by piece count (three small launches) and searched as in the
+ *     pooled schedule; pixels whose records exceed the warp's 480-record slab,
+ *     or whose pieces do not fit the pool, take a direct sweep;
  *   1, 2, 3 (direct): each thread sweeps its pixel's K lists on every march;
  *     1: list heads in registers (k <= 8), two bisection levels per march;
  *     2: heads in shared memory under a winner tree, two levels per march;
  *     3: as 2 with three levels per march.
- * Workspace: vdi_composite_workspace bytes give the staged path its full
- * piece buffer (2048 rows per column); a smaller workspace gives fewer rows
- * (at least 256 bytes plus one row are needed for the staged path; the direct
- * schedules need 256 bytes).  Colours must be non-negative (premultiplied,
- * at most A); a record's extinction -log2(1 - A) / (b - f) is clamped at
- * 2^56 per unit depth. */
+ * Workspace: vdi_composite_workspace bytes hold the larger of the lane
+ * schedule's needs (two lists of 16 bytes per pixel, 8 KB of sort scratch and
+ * a pool of 16 pieces of 24 bytes per pixel) and the pooled schedule's (a
+ * chunk of up to 131072 pixels with room for 2048 pieces each).  An automatic
+ * schedule falls back to a direct one when the workspace is smaller; the
+ * direct schedules need 256 bytes.  Colours must be non-negative
+ * (premultiplied, at most A); a record's extinction -log2(1 - A) / (b - f) is
+ * clamped at 2^56 per unit depth. */
 #define VDI_SCHED_STAGED 4
 #define VDI_SCHED_LANE 5
 size_t vdi_composite_workspace(int32_t k, int32_t w, int32_t h, int32_t n_s);
@@ -383,9 +388,9 @@ vdi_status vdi_composite(const vdi_compact* pe, int32_t k, int32_t w, int32_t h,
                          const vdi_params* params, void* workspace, size_t ws_bytes, vdi_stream stream);
 
 /* ------------------------------------------------------------------------ */
-/* Batched compositing: many requests (image sizes, K, N_S) in one           */
-/* persistent launch.  No counterpart in the paper (which composites one VDI */
-/* per MPI rank); the per-pixel work is that of vdi_composite.              */
+/* Batched compositing: many requests (image sizes, K, N_S) in the same     */
+/* persistent launches.  No counterpart in the paper (which composites one  */
+/* VDI per MPI rank); the per-pixel work is that of vdi_composite.          */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     const vdi_compact* pe; /* host array of k sub-VDI descriptors (device pointers inside) */
@@ -403,14 +408,17 @@ size_t vdi_batch_table_bytes(const vdi_request* reqs, int32_t n);
 vdi_status vdi_batch_table_pack(const vdi_request* reqs, int32_t n, void* host_table, size_t bytes);
 /* Workspace bytes for a packed table (host_table from vdi_batch_table_pack). */
 size_t vdi_composite_batched_workspace(const void* host_table);
-/* Composites every request of the table in one persistent kernel: warps take
- * (request, 32-pixel batch) items from an atomic counter in the workspace
- * (reset by this call with a stream-ordered memset) until none is left and
- * run the staged schedule on them; requests with a direct schedule (1-3, run
- * as 2) and the pixels the stage cannot hold follow in a second launch over
- * the list the first one left in the workspace.  The memset and the launches
- * may be captured into a CUDA graph and replayed; the outputs equal those of
- * one vdi_composite call per request, bit for bit. */
+/* Composites every request of the table with the pooled schedule run over all
+ * of them at once: a persistent build launch in which warps take (request,
+ * 32-pixel batch) items from an atomic counter in the workspace and write
+ * every request's pieces to one pool, a search launch whose lanes take the
+ * listed pixels of every request, and a launch of the direct sweep for the
+ * pixels the stage cannot hold and the requests with a direct schedule (1-3,
+ * run as 2).  The (request, pixel) list is processed in chunks of at most
+ * 2^22 pixels whose pieces fit the pool.  Counters are reset with
+ * stream-ordered memsets; the memsets and the launches may be captured into a
+ * CUDA graph and replayed; the outputs equal those of one vdi_composite call
+ * per request, bit for bit. */
 vdi_status vdi_composite_batched(const void* dev_table, const void* host_table, const vdi_params* params,
                                  void* workspace, size_t ws_bytes, vdi_stream stream);
 /* Autotuner: for each request whose schedule is 0, times the applicable
