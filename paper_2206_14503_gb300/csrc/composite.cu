@@ -25,11 +25,13 @@
 // autotuner, vdi_composite_autotune; the default is the lane schedule for
 // K <= 8 and the staged one above):
 //   VDI_SCHED_LANE (5, K <= 8): composite_lane_kernel copies a warp's 32
-//     pixels' records into shared memory with asynchronous coalesced copies,
-//     sweeps each pixel there (a lane each; depth-disjoint lists, as every box
-//     decomposition gives, without the K-head merge), and emits the pixels
-//     whose gamma = 0 count is within n_s; the others' pieces go to a pool in
-//     the workspace and composite_flat_kernel searches and emits them;
+//     pixels' records into shared memory with asynchronous coalesced copies
+//     and sweeps each pixel there once (a lane each; depth-disjoint lists, as
+//     every box decomposition gives, without the K-head merge): the pixels
+//     whose gamma = 0 count is within n_s are emitted, the others' pieces go
+//     to a pool in the workspace; the list of those pixels is sorted by piece
+//     count (list_hist / list_offsets / list_scatter) and
+//     composite_flat_kernel searches and emits them;
 //   VDI_SCHED_STAGED (4): composite_build_kernel builds each pixel's pieces
 //     with the whole warp (coalesced span loads, merge-path sort of the bounds,
 //     exact prefix scan of the mixture terms) into the pool, and
@@ -43,8 +45,9 @@
 //     under a winner tree (2; 3 with three levels per march).
 // composite_flat_kernel runs the search and the emission as one loop whose
 // body handles one piece of a lane's current march, so lanes at different
-// marches or pixels execute the same instructions and a lane that finishes
-// takes the next pixel.
+// marches or pixels execute the same instructions; lanes at the end of a
+// march wait for others to end theirs together, and a lane that finishes its
+// pixel takes the next one.
 //
 // The batched path runs many requests (different sizes, K, N_S) as the pooled
 // staged schedule does: composite_batched_build_kernel pulls (request, 32-pixel
