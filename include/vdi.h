@@ -198,11 +198,11 @@ vdi_status vdi_brick_build(const void* volume, vdi_voltype type, const int32_t d
  * the current device: a status header, a work counter, the prefix sum's
  * partial sums (8 bytes per 4096 pixels per PE) and a sample cache (1024
  * entries of 8 bytes per resident thread: 152 SMs x 12 CTAs x 64 threads,
- * about 0.96 GB, on a GB300)
- * that lets the gamma search run over each ray's
+ * about 0.96 GB, on a GB300) that lets the gamma search run over each ray's
  * cached non-transparent samples instead of re-sampling the volume.  Any
- * workspace of at least 512 + 8 k ceil(w h / 4096) bytes is accepted; without
- * room for the cache the search re-marches the volume (same result, slower). */
+ * workspace of at least 512 bytes plus 8 k ceil(w h / 4096) rounded up to a
+ * multiple of 256 is accepted; without room for the cache the search
+ * re-marches the volume (same result, slower). */
 size_t vdi_generate_workspace(int32_t k, int32_t w, int32_t h);
 
 /* Chooses gamma and the resulting supersegment count for every (PE, ray)

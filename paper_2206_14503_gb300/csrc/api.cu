@@ -116,8 +116,21 @@ vdi_status vdi_last_error(char* buf, size_t n) {
     return g_last;
 }
 
+// true if p is device (or managed) memory of the current context: a host or stray pointer handed to a
+// device-to-host copy would otherwise be read as host memory
+static bool device_pointer(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 vdi_status vdi_workspace_status(const void* workspace, vdi_stream stream) {
     if (!workspace) return set_error(VDI_ERR_INVALID_ARG, "vdi_workspace_status: workspace is NULL");
+    if (!device_pointer(workspace))
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_workspace_status: workspace is not device memory");
     unsigned int s = 0;
     cudaStream_t st = (cudaStream_t)stream;
     vdi_status r = cuda_check(cudaMemcpyAsync(&s, workspace, sizeof s, cudaMemcpyDeviceToHost, st), "status read");
@@ -130,6 +143,8 @@ vdi_status vdi_workspace_status(const void* workspace, vdi_stream stream) {
 
 vdi_status vdi_workspace_counters(const void* workspace, uint64_t counters[8], vdi_stream stream) {
     if (!workspace || !counters) return set_error(VDI_ERR_INVALID_ARG, "vdi_workspace_counters: NULL argument");
+    if (!device_pointer(workspace))
+        return set_error(VDI_ERR_INVALID_ARG, "vdi_workspace_counters: workspace is not device memory");
     cudaStream_t st = (cudaStream_t)stream;
     const char* src = static_cast<const char*>(workspace) + offsetof(WsHeader, counters);
     vdi_status r = cuda_check(cudaMemcpyAsync(counters, src, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st),

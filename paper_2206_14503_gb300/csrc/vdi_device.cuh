@@ -375,6 +375,19 @@ __device__ __forceinline__ bool criterion(const float P[3], float A, float L2, f
     return D >= __fmul_rn(g2, __fmul_rn(A, A));
 }
 
+// The same decision for a transparent piece (Px = 0): each channel's term
+// fma(P, at, -(A * 0)) is the rounded product P * at (adding -0 changes no
+// rounded result), so this is criterion(P, A, L2, r, {0, 0, 0}, g2) bit for
+// bit with three multiplications fewer.
+__device__ __forceinline__ bool criterion_clear(const float P[3], float A, float L2, float r, float g2) {
+    float at = __fsub_rn(1.f, ex2_approx(__fmul_rn(L2, r)));
+    float e0 = __fmul_rn(P[0], at);
+    float e1 = __fmul_rn(P[1], at);
+    float e2 = __fmul_rn(P[2], at);
+    float D = __fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0)));
+    return D >= __fmul_rn(g2, __fmul_rn(A, A));
+}
+
 // The same decision, also returning the decision ratio q ~= D / A^2 (one
 // approximate reciprocal): every gamma with gamma^2 on the same side of q
 // takes the same decision at this step.

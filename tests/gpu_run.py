@@ -84,8 +84,9 @@ def composite(lists, w, h, n_s, prec_out=0, iters=16, schedule=0):
 
 
 def generate(vol, dims, boxes, lut, cam, n_s, gamma, step=0.5, ref_len=1.0, prec=0, capacity=None, iters=16,
-             given_gamma=None):
-    """Returns per-PE lists (counts, offsets, fb, rgba, prec) as numpy, plus gammas [k, npix]."""
+             given_gamma=None, ws_bytes=None):
+    """Returns per-PE lists (counts, offsets, fb, rgba, prec) as numpy, plus gammas [k, npix].
+    ws_bytes: the generation workspace's size (default: vdi_generate_workspace's)."""
     import paper_2206_14503_gb300 as vdi
 
     torch = _torch()
@@ -99,7 +100,7 @@ def generate(vol, dims, boxes, lut, cam, n_s, gamma, step=0.5, ref_len=1.0, prec
     if given_gamma is not None:
         for e in range(k):
             outs[e].gamma.copy_(torch.from_numpy(np.ascontiguousarray(given_gamma[e], dtype=np.float32)))
-    ws = vdi.Workspace(vdi.vdi_generate_workspace(k, W, H))
+    ws = vdi.Workspace(ws_bytes if ws_bytes is not None else vdi.vdi_generate_workspace(k, W, H))
     lut_d = to_dev(lut.astype(np.float32))
     vdi.check(vdi.vdi_generate(br.bricks, lut_d.data_ptr(), vdi.make_camera(cam), n_s, gamma,
                                [o.struct() for o in outs], vdi.make_params(step=step, ref_len=ref_len,

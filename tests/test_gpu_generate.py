@@ -61,6 +61,35 @@ def test_generate_search_tiny(tiny_workload, n_s):
     assert np.mean(gam[same] == ogam[same]) >= 0.999
 
 
+@pytest.mark.parametrize("gamma_mode", ["search", "given"])
+def test_search_paths_agree(tiny_workload, gamma_mode):
+    """The bisection runs over the sample cache when the workspace has room for it and re-marches the
+    volume when it has not: the same decisions either way, so the counts, gammas and records agree bit
+    for bit (with the search's own mode and with the given-gamma mode's fallback to it)."""
+    import paper_2206_14503_gb300 as vdi
+
+    w = tiny_workload
+    cam = w["cams"][5]
+    k, npix = len(w["boxes"]), cam.width * cam.height
+    full = vdi.vdi_generate_workspace(k, cam.width, cam.height)
+    no_cache = 512 + (8 * k * ((npix + 4095) // 4096) + 255) // 256 * 256  # the smallest workspace accepted
+    assert no_cache < full
+    given = None
+    gamma = -1.0
+    if gamma_mode == "given":
+        gamma = -2.0  # VDI_GAMMA_GIVEN: a ray over the budget at its given gamma falls back to the search
+        given = np.full((k, npix), 0.03, dtype=np.float32)
+    runs = [generate(w["vol"], w["dims"], w["boxes"], w["lut"], cam, w["n_s"], gamma, step=w["step"],
+                     given_gamma=given, ws_bytes=b) for b in (full, no_cache)]
+    (ref_lists, ref_gam), (lists, gam) = runs
+    searched = np.sum(ref_gam != np.float32(0.03)) if given is not None else np.sum(ref_gam > 0)
+    assert searched > 1000
+    assert np.array_equal(gam, ref_gam)
+    for (c, o, fb, rgba, _), (c0, o0, fb0, rgba0, _) in zip(lists, ref_lists):
+        assert np.array_equal(c, c0) and np.array_equal(o, o0)
+        assert np.array_equal(fb, fb0) and np.array_equal(rgba, rgba0)
+
+
 def test_end_to_end_equals_dvr_tiny(tiny_workload):
     # sec. 2.3: the composited VDI renders exactly from the generating view
     w = tiny_workload
