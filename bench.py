@@ -954,6 +954,8 @@ def main():
     gen_tops = gen_ops / args.steps / (mean["choose_gamma"] * 1e-3) / 1e12
     gen_tops_exec = gen_ops_exec / args.steps / (mean["choose_gamma"] * 1e-3) / 1e12
     comp_gbs = statistics.mean(comp_bytes) / (mean["composite"] * 1e-3) / 1e9
+    # the compositing search's issue rate: 24 ops per executed candidate step (census) over the stage's time
+    comp_tops = OPS_PER_STEP * comp_ctr[4] / args.steps / (mean["composite"] * 1e-3) / 1e12
     if dominant == "composite":
         roof = {"bound": "hbm", "achieved": comp_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": comp_gbs / hbm_peak, "traffic": None, "kernel": "composite_kernel",
@@ -1050,6 +1052,7 @@ def main():
                       "cached_marches_per_frame": cached // args.steps,
                       "volume_search_marches_per_frame": remarched // args.steps}
         comp_detail = {"gbs": comp_gbs, "frac_hbm": comp_gbs / hbm_peak, "peak_gbs": hbm_peak,
+                       "tops": comp_tops, "frac_alu": comp_tops / alu_peak_tops,
                        "peak_source": hbm_src, "records_in_per_frame": int(statistics.mean(n_in)),
                        "bytes_per_frame": int(statistics.mean(comp_bytes)),
                        "census": _comp_census(vdi, comp_ctr), "schedule": comp_schedule,
@@ -1063,6 +1066,7 @@ def main():
                 json.dump(detail, f, indent=1)
         # the line stays short: the driver keeps the tail of the output
         summary = {"composite_plain_frac_hbm": round(comp_gbs / hbm_peak, 4),
+                   "composite_plain_frac_alu": round(comp_tops / alu_peak_tops, 4),
                    "composite_plain_ms": round(mean["composite"], 3), "composite_schedule": comp_schedule,
                    "choose_gamma_ms": round(mean["choose_gamma"], 3)}
         for key, leg in (("scale_fp32", (scale or {}).get("fp32")), ("scale_fp16", (scale or {}).get("fp16")),
@@ -1070,6 +1074,12 @@ def main():
             if leg and "ms" in leg:
                 summary[f"composite_{key}_frac_hbm"] = round(leg["frac_hbm"], 4)
                 summary[f"composite_{key}_ms"] = round(leg["ms"], 1)
+                cen = leg.get("census")
+                if cen and key.startswith("scale"):
+                    # 24 ops per executed candidate step over the leg's pixels and time
+                    tops = OPS_PER_STEP * cen["cand_steps_per_pixel"] * args.scale_size ** 2 / (leg["ms"] * 1e-3) / 1e12
+                    leg["frac_alu"] = tops / alu_peak_tops
+                    summary[f"composite_{key}_frac_alu"] = round(leg["frac_alu"], 4)
         if gen_batched and "mrays_s" in gen_batched:
             summary["generate_batched_mrays_s"] = round(gen_batched["mrays_s"], 2)
         if learned:
