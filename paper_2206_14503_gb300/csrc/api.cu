@@ -223,7 +223,9 @@ size_t vdi_generate_workspace(int32_t k, int32_t w, int32_t h) {
     int ctas = 0;
     size_t cache = 0;
     if (gen_count_grid(ctas) == VDI_OK) cache = gen_cache_bytes(ctas);
-    return gen_min_workspace(k, w, h) + align_up(cache, 256);
+    size_t bytes = gen_min_workspace(k, w, h) + align_up(cache, 256);
+    if (cache > 0) bytes += align_up(gen_span_bytes(k, w, h), 256) + 256;  // the recorded spans and their tag
+    return bytes;
 }
 
 static vdi_status gen_check(const char* fn, const vdi_brick* bricks, int32_t k, const float* tf_lut,
@@ -350,7 +352,7 @@ static vdi_status generate_compact(const char* fn, const vdi_brick* bricks, int3
                                  (unsigned long long)tot[e], (unsigned long long)out[e].capacity);
     }
     return launch_gen_emit(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s,
-                           out[0].prec, od, status, st, false, own);
+                           out[0].prec, od, status, st, false, own, ws + fixed, ws_bytes - fixed);
 }
 
 vdi_status vdi_generate(const vdi_brick* bricks, int32_t k, const float* tf_lut, const vdi_camera* cam, int32_t n_s,
@@ -460,7 +462,7 @@ vdi_status vdi_generate_regular(const vdi_brick* bricks, int32_t k, const float*
                          reinterpret_cast<unsigned int*>(ws + kWsHeader), ws + fixed, ws_bytes - fixed, st);
     if (s != VDI_OK) return s;
     return launch_gen_emit(bd, k, tf_lut, cd, bricks[0].dims, scale255, params->step, params->ref_len, n_s,
-                           out[0].prec, od, status, st, true);
+                           out[0].prec, od, status, st, true, nullptr, ws + fixed, ws_bytes - fixed);
 }
 
 size_t vdi_composite_workspace(int32_t k, int32_t w, int32_t h, int32_t n_s) {

@@ -70,6 +70,12 @@ struct GenArgs {
     unsigned int* counter;  // work-item counter (persistent kernel)
     float2* cache;          // sample cache: [cap][slots] (table coordinate x, transparent samples before it)
     int cache_cap, slots;
+    // each (PE, ray)'s samples from its first to its last non-transparent one, [x, y) (PE-major), and the
+    // tag of the inputs they were recorded for: the count kernel records them, the emit kernel marches
+    // only that span when the tag matches its own inputs' (nullptr: neither)
+    uint2* ranges;
+    unsigned long long* range_tag;
+    unsigned long long tag;
 };
 
 // gen_count_kernel: CTAs of two warps on 16 x 4 tiles, VDI_COUNT_MIN_BLOCKS per SM (the register
@@ -292,17 +298,22 @@ struct CacheRef {
 template <int NC, bool OWNED = false>
 __device__ __forceinline__ int first_march(const Ray& r, int k0, int k1, const BrickDev& b, const float4* lut2,
                                            float scale255, const float* g2, int cap, const CacheRef* c, int* cnt,
-                                           Census& cs, const GenReq* ga = nullptr, int e = 0, int* runs = nullptr) {
+                                           Census& cs, const GenReq* ga = nullptr, int e = 0, int* runs = nullptr,
+                                           int* kspan = nullptr) {
     cs.evals += (unsigned long long)(k1 - k0);
     cs.steps += (unsigned long long)(k1 - k0) * NC;
     cs.passes += 1;
     GenCount st[NC > 0 ? NC : 1];
 #pragma unroll
     for (int q = 0; q < NC; ++q) gc_reset(st[q]);
-    int nt = 0, gap = 0, nruns = 0;
+    int nt = 0, gap = 0, nruns = 0, kf = 0, kl = 0;
     bool brk = false;
-    auto visit = [&](int, const Sample& s) {
+    auto visit = [&](int k, const Sample& s) {
         if (s.a > 0.f) {
+            if (kspan) {
+                kf = nt == 0 ? k : kf;
+                kl = k;
+            }
             if (c && nt < c->cap) c->e[c->at(nt)] = make_float2(s.x, (OWNED && brk) ? -1.f : (float)gap);
             if (OWNED && (nruns == 0 || brk)) ++nruns;
             brk = false;
@@ -327,6 +338,10 @@ __device__ __forceinline__ int first_march(const Ray& r, int k0, int k1, const B
     }
 #pragma unroll
     for (int q = 0; q < NC; ++q) cnt[q] = st[q].cnt;
+    if (kspan) {
+        kspan[0] = kf;
+        kspan[1] = kl + 1;
+    }
     return nt;
 }
 
@@ -565,7 +580,7 @@ __device__ __forceinline__ float bisect_gamma(const Ray& r, int k0, int k1, cons
 template <bool LEARNED, bool OWNED>
 __device__ __forceinline__ void count_ray(const GenReq& a, const BrickDev& b, const CompactDev& o, int e, int i, int j,
                                           const float4* __restrict__ lut2, const CacheRef& cref, Census& cs,
-                                          unsigned long long& rays) {
+                                          unsigned long long& rays, uint2* rng) {
     const int mode = LEARNED ? 3 : a.mode;
     const size_t p = (size_t)j * a.cam.W + i;
     Ray r;
@@ -574,13 +589,19 @@ __device__ __forceinline__ void count_ray(const GenReq& a, const BrickDev& b, co
     float gamma = mode == 0 ? a.gamma : (mode >= 2 ? fmaxf(o.gamma[p], 0.f) : 0.f);
     int count = 0;
     int runs = 1;
+    // the span from the first to the last non-transparent sample (box domains): samples outside it change
+    // no count and no record
+    int kspan[2] = {0, 0};
+    int* ks = OWNED ? nullptr : kspan;
     if (any) {
         rays += 1;
         if (mode == 0) {
             const float g2[1] = {__fmul_rn(a.gamma, a.gamma)};
             int c[1];
-            first_march<1, OWNED>(r, k0, k1, b, lut2, a.scale255, g2, a.n_s, nullptr, c, cs, &a, e, &runs);
+            const int nt = first_march<1, OWNED>(r, k0, k1, b, lut2, a.scale255, g2, a.n_s, nullptr, c, cs, &a, e,
+                                                 &runs, ks);
             count = c[0];
+            if (!OWNED && rng && nt > 0) *rng = make_uint2((unsigned)kspan[0], (unsigned)kspan[1]);
         } else {
             const bool use_cache = cref.e != nullptr;
             int nt;
@@ -591,7 +612,7 @@ __device__ __forceinline__ void count_ray(const GenReq& a, const BrickDev& b, co
                 const float g2[1] = {__fmul_rn(gamma, gamma)};
                 int c[1];
                 nt = first_march<1, OWNED>(r, k0, k1, b, lut2, a.scale255, g2, INT_MAX, use_cache ? &cref : nullptr,
-                                           c, cs, &a, e, &runs);
+                                           c, cs, &a, e, &runs, ks);
                 cp = c[0];
                 if (mode == 2) {
                     if (c[0] <= a.n_s) {
@@ -604,7 +625,13 @@ __device__ __forceinline__ void count_ray(const GenReq& a, const BrickDev& b, co
             } else {
                 int dummy[1];
                 nt = first_march<0, OWNED>(r, k0, k1, b, lut2, a.scale255, nullptr, INT_MAX,
-                                           use_cache ? &cref : nullptr, dummy, cs, &a, e, &runs);
+                                           use_cache ? &cref : nullptr, dummy, cs, &a, e, &runs, ks);
+            }
+            if (!OWNED && nt > 0) {
+                if (rng) *rng = make_uint2((unsigned)kspan[0], (unsigned)kspan[1]);
+                // a search that re-marches the volume marches the span only (same counts)
+                k0 = kspan[0];
+                k1 = kspan[1];
             }
             if (searched) {
                 if (nt <= a.n_s) {
@@ -648,6 +675,7 @@ __global__ void __launch_bounds__(kCountThreads, LEARNED ? VDI_LEARNED_MIN_BLOCK
     const __grid_constant__ GenArgs a) {
     __shared__ float4 lut2[2 * 257];
     __shared__ unsigned int s_item;
+    if (a.range_tag && blockIdx.x == 0 && threadIdx.x == 0) *a.range_tag = a.tag;
     load_lut(a.r, lut2);
     const unsigned tiles = (unsigned)(a.r.tiles_x * a.r.tiles_y);
     const unsigned total = tiles * (unsigned)a.r.k;
@@ -668,7 +696,10 @@ __global__ void __launch_bounds__(kCountThreads, LEARNED ? VDI_LEARNED_MIN_BLOCK
         int i, j;
         tile_pixel(a.r.tiles_x, (int)(item % tiles), kCountTileH, i, j);
         if (i >= a.r.cam.W || j >= a.r.cam.H) continue;
-        count_ray<LEARNED, OWNED>(a.r, a.b[e], a.out[e], e, i, j, lut2, cref, cs, rays);
+        count_ray<LEARNED, OWNED>(a.r, a.b[e], a.out[e], e, i, j, lut2, cref, cs, rays,
+                                  a.ranges ? a.ranges + (size_t)e * a.r.cam.W * a.r.cam.H +
+                                                 ((size_t)j * a.r.cam.W + i)
+                                           : nullptr);
     }
     if (CENSUS) census_flush_gen(cs, rays, a.status);
 }
@@ -697,7 +728,7 @@ __device__ __forceinline__ void store_record(unsigned int* status, int prec, con
 // the compact path carries none of it (as a run-time flag it cost the compact emission 70%).
 template <bool OWNED, bool REGULAR>
 __device__ __forceinline__ void emit_ray(const GenReq& a, const BrickDev& b, const CompactDev& o, int e, int i, int j,
-                                         bool inside, float4* lut2, unsigned int* status) {
+                                         bool inside, float4* lut2, unsigned int* status, const uint2* rng) {
     const size_t p = inside ? (size_t)j * a.cam.W + i : 0;
     const uint32_t want = inside ? o.counts[p] : 0u;
     // most (PE, tile) pairs hold no record (rays that miss the PE's box): such a CTA of the compact
@@ -741,6 +772,14 @@ __device__ __forceinline__ void emit_ray(const GenReq& a, const BrickDev& b, con
     if (!(ray_setup(a.cam, i, j, a.dims, a.step, r) && owned_range(r, a.step, b, a.dims, k0, k1))) {
         zero_tail();
         return;
+    }
+    if (!OWNED && rng) {
+        // the span the count kernel recorded: before its first non-transparent sample no supersegment is
+        // open, and after its last one transparent samples only absorb into or close the open one, whose
+        // values and back depth they leave unchanged
+        const uint2 g = rng[p];
+        k0 = max(k0, (int)g.x);
+        k1 = min(k1, (int)g.y);
     }
     const float gamma = o.gamma ? o.gamma[p] : a.gamma;
     const float g2 = __fmul_rn(gamma, gamma);
@@ -803,7 +842,9 @@ __global__ void __launch_bounds__(kEmitThreads, VDI_EMIT_MIN_BLOCKS) gen_emit_ke
     tile_pixel(a.r.tiles_x, blockIdx.x, kEmitTileH, i, j);
     const bool inside = i < a.r.cam.W && j < a.r.cam.H;
     const int e = blockIdx.y;
-    emit_ray<OWNED, REGULAR>(a.r, a.b[e], a.out[e], e, i, j, inside, lut2, a.status);
+    const bool spans = !OWNED && a.ranges && *a.range_tag == a.tag;
+    emit_ray<OWNED, REGULAR>(a.r, a.b[e], a.out[e], e, i, j, inside, lut2, a.status,
+                             spans ? a.ranges + (size_t)e * a.r.cam.W * a.r.cam.H : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -887,7 +928,7 @@ __global__ void __launch_bounds__(kCountThreads, VDI_COUNT_MIN_BLOCKS) gen_count
         tile_pixel(br.r.tiles_x, (int)(local % tiles), kCountTileH, i, j);
         if (i >= br.r.cam.W || j >= br.r.cam.H) continue;
         const GenBatchPe& pe = a.pes[br.pe_begin + e];
-        count_ray<false, false>(br.r, pe.b, pe.out, e, i, j, lut2, cref, cs, rays);
+        count_ray<false, false>(br.r, pe.b, pe.out, e, i, j, lut2, cref, cs, rays, nullptr);
     }
 }
 
@@ -903,7 +944,7 @@ __global__ void __launch_bounds__(kEmitThreads, VDI_EMIT_MIN_BLOCKS) gen_emit_ba
     tile_pixel(br.r.tiles_x, (int)(local % etiles), kEmitTileH, i, j);
     const bool inside = i < br.r.cam.W && j < br.r.cam.H;
     const GenBatchPe& pe = a.pes[br.pe_begin + e];
-    emit_ray<false, false>(br.r, pe.b, pe.out, e, i, j, inside, lut2, a.status);
+    emit_ray<false, false>(br.r, pe.b, pe.out, e, i, j, inside, lut2, a.status, nullptr);
 }
 
 static void fill_req(GenReq& r, int k, const float* lut, const CamDev& cam, const int dims[3], float scale255,
@@ -938,6 +979,47 @@ static void fill_args(GenArgs& a, const BrickDev* bricks, int k, const float* lu
     a.cache = nullptr;
     a.cache_cap = 0;
     a.slots = 0;
+    a.ranges = nullptr;
+    a.range_tag = nullptr;
+    a.tag = 0;
+}
+
+// The recorded spans in a generation workspace: after the sample cache, one uint2 per (PE, pixel) and
+// the 8-byte tag (nullptr when the workspace has no room for them).
+static void gen_span_refs(void* cache, size_t cache_bytes, int k, int w, int h, uint2*& ranges,
+                          unsigned long long*& tag) {
+    ranges = nullptr;
+    tag = nullptr;
+    int ctas = 0;
+    if (!cache || gen_count_grid(ctas) != VDI_OK) return;
+    const size_t cache_sz = align_up(gen_cache_bytes(ctas), 256);
+    const size_t span_sz = align_up(gen_span_bytes(k, w, h), 256);
+    if (cache_bytes < cache_sz + span_sz + 256) return;
+    char* b = static_cast<char*>(cache);
+    ranges = reinterpret_cast<uint2*>(b + cache_sz);
+    tag = reinterpret_cast<unsigned long long*>(b + cache_sz + span_sz);
+}
+
+// Tag of the inputs that decide which samples are non-transparent (bricks, table, camera, sampling): a
+// 64-bit FNV-1a hash of their values (pointers, not contents), never 0.
+static unsigned long long gen_span_tag(const GenArgs& a) {
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= c[i];
+            h *= 1099511628211ull;
+        }
+    };
+    mix(&a.r.k, sizeof a.r.k);
+    mix(&a.r.cam, sizeof a.r.cam);
+    mix(a.r.dims, sizeof a.r.dims);
+    mix(&a.r.lut, sizeof a.r.lut);
+    mix(&a.r.scale255, sizeof a.r.scale255);
+    mix(&a.r.step, sizeof a.r.step);
+    mix(&a.r.ref_len, sizeof a.r.ref_len);
+    mix(a.b, sizeof(BrickDev) * (size_t)a.r.k);
+    return h ? h : 1ull;
 }
 
 // count-kernel mode of a gamma argument
@@ -970,6 +1052,8 @@ vdi_status gen_count_grid(int& ctas) {
     return VDI_OK;
 }
 
+size_t gen_span_bytes(int k, int w, int h) { return (size_t)k * (size_t)w * (size_t)h * sizeof(uint2); }
+
 size_t gen_cache_bytes(int ctas) {
     return (size_t)ctas * kCountThreads * kCacheCap * sizeof(float2);
 }
@@ -998,6 +1082,18 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
     if ((unsigned)ctas > items) ctas = (int)items;
     const bool learned = a.r.mode == 3;
     if (a.r.own.map && learned) return set_error(VDI_ERR_UNSUPPORTED, "learned gamma with an ownership map");
+    // the spans: every count launch invalidates the recorded ones; box domains record their own
+    gen_span_refs(cache, cache_bytes, k, cam.W, cam.H, a.ranges, a.range_tag);
+    if (a.range_tag) {
+        s = cuda_check(cudaMemsetAsync(a.range_tag, 0, sizeof(unsigned long long), st), "span tag clear");
+        if (s != VDI_OK) return s;
+        if (a.r.own.map) {
+            a.ranges = nullptr;
+            a.range_tag = nullptr;
+        } else {
+            a.tag = gen_span_tag(a);
+        }
+    }
     if (a.r.own.map && census) gen_count_kernel<true, false, true><<<ctas, kCountThreads, 0, st>>>(a);
     else if (a.r.own.map) gen_count_kernel<false, false, true><<<ctas, kCountThreads, 0, st>>>(a);
     else if (census && learned) gen_count_kernel<true, true><<<ctas, kCountThreads, 0, st>>>(a);
@@ -1009,10 +1105,16 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
 
 vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                            float scale255, float step, float ref_len, int n_s, int prec, const CompactDev* out,
-                           unsigned int* status, cudaStream_t st, bool regular, const OwnerDev* own) {
+                           unsigned int* status, cudaStream_t st, bool regular, const OwnerDev* own, void* cache,
+                           size_t cache_bytes) {
     GenArgs a;
     fill_args(a, bricks, k, lut, cam, dims, scale255, step, ref_len, n_s, out, status);
     if (own) a.r.own = *own;
+    // the spans the last count launch on this workspace recorded, used when they are for these inputs
+    if (!a.r.own.map) {
+        gen_span_refs(cache, cache_bytes, k, cam.W, cam.H, a.ranges, a.range_tag);
+        if (a.range_tag) a.tag = gen_span_tag(a);
+    }
     a.r.prec = prec;
     a.r.tiles_y = (cam.H + kEmitTileH - 1) / kEmitTileH;
     dim3 grid((unsigned)(a.r.tiles_x * a.r.tiles_y), (unsigned)k);

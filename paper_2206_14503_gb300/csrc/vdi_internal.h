@@ -80,8 +80,10 @@ vdi_status launch_gen_count(const BrickDev* bricks, int k, const float* lut, con
                             void* cache, size_t cache_bytes, cudaStream_t st, const OwnerDev* own = nullptr);
 vdi_status gen_count_grid(int& ctas);
 size_t gen_cache_bytes(int ctas);
+size_t gen_span_bytes(int k, int w, int h);
 // generation workspace: [0, 256) header, [256, 512) work counter, then the
-// prefix sum's partial sums, then (optionally) the sample cache
+// prefix sum's partial sums, then (optionally) the sample cache, the recorded
+// spans (one uint2 per (PE, pixel)) and their 8-byte tag (a 256-byte slot)
 constexpr size_t kGenFixed = 512;
 // internal gamma mode of launch_gen_count: per-ray predicted gamma in out.gamma,
 // refined by a short bracketed search over the sample cache (learned path)
@@ -89,7 +91,7 @@ constexpr float kGammaLearnedBracket = -5.0f;
 vdi_status launch_gen_emit(const BrickDev* bricks, int k, const float* lut, const CamDev& cam, const int dims[3],
                            float scale255, float step, float ref_len, int n_s, int prec, const CompactDev* out,
                            unsigned int* status, cudaStream_t st, bool regular = false,
-                           const OwnerDev* own = nullptr);
+                           const OwnerDev* own = nullptr, void* cache = nullptr, size_t cache_bytes = 0);
 size_t scan_workspace(int k, int n);
 vdi_status launch_scan(int k, int n, uint32_t* const* counts, uint64_t* const* offsets, void* ws, cudaStream_t st);
 uint32_t scan_chunks(int n);

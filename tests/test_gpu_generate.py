@@ -90,6 +90,85 @@ def test_search_paths_agree(tiny_workload, gamma_mode):
         assert np.array_equal(fb, fb0) and np.array_equal(rgba, rgba0)
 
 
+def test_emission_spans(tiny_workload):
+    """Emission marches, for each ray with records, only the samples from its first to its last
+    non-transparent one, as the count pass recorded them: the same call's, or the last vdi_choose_gamma's
+    on the same workspace when it was for the same bricks, table and camera; with no such record it marches
+    every sample.  The records are the same bit for bit in every case."""
+    import torch
+
+    import paper_2206_14503_gb300 as vdi
+    from gpu_run import to_dev
+
+    w = tiny_workload
+    cam_a, cam_b = vdi.make_camera(w["cams"][6]), vdi.make_camera(w["cams"][7])
+    npix = w["cams"][6].width * w["cams"][6].height
+    n_s = w["n_s"]
+    vb = [vdi.vdi_box(tuple(lo), tuple(hi)) for lo, hi in w["boxes"]]
+    k = len(vb)
+    br = vdi.Bricks(to_dev(w["vol"]), w["dims"], vb)
+    lut = to_dev(w["lut"].astype(np.float32))
+    params = vdi.make_params(step=w["step"])
+    wsz = vdi.vdi_generate_workspace(k, w["cams"][6].width, w["cams"][6].height)
+
+    def outs():
+        return [vdi.Compact(npix, npix * n_s) for _ in vb]
+
+    def structs(o):
+        return [c.struct() for c in o]
+
+    def records(o):
+        torch.cuda.synchronize()
+        res = []
+        for c in o:
+            fb, rgba = vdi.compact_records_f32(c)
+            n = int(c.offsets[-1].item())
+            res.append((c.counts.cpu().numpy(), c.offsets.cpu().numpy(), c.gamma.cpu().numpy(),
+                        fb[:n].cpu().numpy(), rgba[:n].cpu().numpy()))
+        return res
+
+    # one call: the count pass records the spans, the emission of the same call uses them
+    ws1 = vdi.Workspace(wsz)
+    ref = outs()
+    vdi.check(vdi.vdi_generate(br.bricks, lut.data_ptr(), cam_a, n_s, -1.0, structs(ref), params, ws1.ptr, ws1.nbytes),
+              "one call")
+    vdi.check(ws1.status(), "one call status")
+    # the choice, then the emission on the same workspace: the choice's spans
+    ws2 = vdi.Workspace(wsz)
+    o2 = outs()
+    vdi.check(vdi.vdi_choose_gamma(br.bricks, lut.data_ptr(), cam_a, n_s, -1.0, structs(o2), params, ws2.ptr,
+                                   ws2.nbytes), "choice")
+    vdi.check(vdi.vdi_generate(br.bricks, lut.data_ptr(), cam_a, n_s, vdi.VDI_GAMMA_CHOSEN, structs(o2), params,
+                               ws2.ptr, ws2.nbytes), "chosen")
+    vdi.check(ws2.status(), "chosen status")
+    # the workspace's last choice was for another camera: every sample is marched
+    ws3 = vdi.Workspace(wsz)
+    o3, o3b = outs(), outs()
+    vdi.check(vdi.vdi_choose_gamma(br.bricks, lut.data_ptr(), cam_a, n_s, -1.0, structs(o3), params, ws3.ptr,
+                                   ws3.nbytes), "choice a")
+    vdi.check(vdi.vdi_choose_gamma(br.bricks, lut.data_ptr(), cam_b, n_s, -1.0, structs(o3b), params, ws3.ptr,
+                                   ws3.nbytes), "choice b")
+    vdi.check(vdi.vdi_generate(br.bricks, lut.data_ptr(), cam_a, n_s, vdi.VDI_GAMMA_CHOSEN, structs(o3), params,
+                               ws3.ptr, ws3.nbytes), "chosen, other record")
+    vdi.check(ws3.status(), "chosen status")
+    # a workspace without room for the spans
+    small = 512 + (8 * k * ((npix + 4095) // 4096) + 255) // 256 * 256
+    ws4 = vdi.Workspace(small)
+    o4 = [vdi.Compact(npix, npix * n_s) for _ in vb]
+    for c, r in zip(o4, o2):
+        c.gamma.copy_(r.gamma)
+        c.counts.copy_(r.counts)
+    vdi.check(vdi.vdi_generate(br.bricks, lut.data_ptr(), cam_a, n_s, vdi.VDI_GAMMA_CHOSEN, structs(o4), params,
+                               ws4.ptr, ws4.nbytes), "chosen, no spans")
+    vdi.check(ws4.status(), "chosen status")
+    r_ref = records(ref)
+    assert sum(int(c[0].sum()) for c in r_ref) > 1000
+    for o in (o2, o3, o4):
+        for got, want in zip(records(o), r_ref):
+            for g, x in zip(got, want):
+                assert np.array_equal(g, x)
+
+
 def test_end_to_end_equals_dvr_tiny(tiny_workload):
     # sec. 2.3: the composited VDI renders exactly from the generating view
     w = tiny_workload
