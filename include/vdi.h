@@ -196,13 +196,17 @@ vdi_status vdi_brick_build(const void* volume, vdi_voltype type, const int32_t d
 /* ------------------------------------------------------------------------ */
 /* Workspace bytes for vdi_generate / vdi_choose_gamma with k PEs of w x h on
  * the current device: a status header, a work counter, the prefix sum's
- * partial sums (8 bytes per 4096 pixels per PE) and a sample cache (1024
+ * partial sums (8 bytes per 4096 pixels per PE), a sample cache (1024
  * entries of 8 bytes per resident thread: 152 SMs x 12 CTAs x 64 threads,
  * about 0.96 GB, on a GB300) that lets the gamma search run over each ray's
- * cached non-transparent samples instead of re-sampling the volume.  Any
- * workspace of at least 512 bytes plus 8 k ceil(w h / 4096) rounded up to a
- * multiple of 256 is accepted; without room for the cache the search
- * re-marches the volume (same result, slower). */
+ * cached non-transparent samples instead of re-sampling the volume, and each
+ * (PE, ray)'s recorded span (8 bytes per PE and pixel, plus 256): the samples
+ * from its first to its last non-transparent one, which emission marches
+ * instead of all of the ray's samples in the PE's box.  Any workspace of at
+ * least 512 bytes plus 8 k ceil(w h / 4096) rounded up to a multiple of 256
+ * is accepted, with the same results: without room for the cache the search
+ * re-marches the volume, without room for the spans emission marches every
+ * sample (slower). */
 size_t vdi_generate_workspace(int32_t k, int32_t w, int32_t h);
 
 /* Chooses gamma and the resulting supersegment count for every (PE, ray)
@@ -223,7 +227,12 @@ vdi_status vdi_choose_gamma(const vdi_brick* bricks, int32_t k, const float* tf_
  * gamma as in vdi_choose_gamma, or VDI_GAMMA_CHOSEN to skip choosing: out[e].counts
  * and out[e].gamma then hold the result of an earlier vdi_choose_gamma call
  * with the same bricks, camera, n_s and params (only the prefix sum and the
- * emission run).
+ * emission run).  Emission marches the spans the last choice on this
+ * workspace recorded when that choice had the same bricks, table, camera and
+ * sampling parameters (compared as values: pointers, boxes, camera, step),
+ * and every sample otherwise.  A caller that rewrites the bricks' or the
+ * table's contents in place between vdi_choose_gamma and this call must
+ * choose again, or pass another workspace.
  * Records of a list are in depth order, at most n_s per list for box-shaped
  * domains.  If a PE's total exceeds out[e].capacity, no record past the
  * capacity is written and VDI_ERR_CAPACITY is reported through the workspace
