@@ -226,3 +226,35 @@ def test_records_lie_in_owning_brick():
                 assert np.all(c >= lo) and np.all(c < hi)
                 checked += 1
     assert checked > 1000
+
+
+def test_transparent_ends_change_no_record():
+    """Transparent samples before a ray's first non-transparent one and after its last one change no
+    supersegment (sec. 2.4, Eq. 1 with readings G5 and G6): before the first, no supersegment is open;
+    after the last, each is absorbed into the open supersegment or closes it, and neither moves its
+    colour, opacity or back depth.  So the lists, and the searched gamma, of a ray equal those of the
+    span between its first and last non-transparent sample -- the span the generation kernels record
+    and emission marches."""
+    rng = np.random.default_rng(29)
+    for trial in range(60):
+        n = int(rng.integers(8, 80))
+        a = rng.uniform(0.0, 0.6, n) * (rng.uniform(size=n) < 0.6)
+        lead, trail = int(rng.integers(0, 12)), int(rng.integers(0, 12))
+        a[:lead] = 0.0
+        a[n - trail:] = 0.0
+        nz = np.nonzero(a)[0]
+        if len(nz) == 0:
+            continue
+        first, last = nz[0], nz[-1]
+        col = rng.uniform(size=(n, 3))
+        k = np.arange(n, dtype=np.float64)
+        pcs = np.column_stack([0.5 * k, 0.5 * (k + 1), col * a[:, None], a])
+        span = pcs[first:last + 1]
+        for gamma in (0.0, 0.05, 0.3, 1.0, 2.0):
+            for cap in (2, 6, 1 << 30):
+                c_full, r_full = oracle.segment(pcs, gamma, cap)
+                c_span, r_span = oracle.segment(span, gamma, cap)
+                assert c_full == c_span, (trial, gamma, cap)
+                assert np.array_equal(r_full, r_span), (trial, gamma, cap)
+        for n_s in (1, 3, 8):
+            assert oracle.search(pcs, n_s)[0] == oracle.search(span, n_s)[0], (trial, n_s)
