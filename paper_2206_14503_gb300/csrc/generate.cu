@@ -30,7 +30,10 @@
 // so cached, re-marched and emitting marches take identical decisions.
 //
 // gen_emit_kernel re-marches with the chosen gamma and writes the records at
-// the prefix-sum offsets (compact layout, sec. 4).
+// the prefix-sum offsets (compact layout, sec. 4).  The count kernel's first
+// march records, per (PE, ray), the span from the first to the last
+// non-transparent sample; emission marches only that span when the record is
+// for its own inputs (samples outside it change no record).
 //
 // Non-convex ownership (sec. 5.3; the OWNED instantiations): a PE marches the
 // samples of its bounding box and keeps those whose cell lies in one of its
